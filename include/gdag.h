@@ -1,0 +1,334 @@
+/*
+ * gdag.h -- run-time DAG scheduling of GPU kernel launches (C ABI).
+ *
+ * A program issues a plain sequence of kernel launches, host writes and host
+ * reads on registered arrays.  The library infers the dependency DAG from each
+ * element's per-argument access modes as the elements arrive (Section III-A,
+ * "Computation DAG and Dependency Sets"), runs independent elements on
+ * separate CUDA streams with event waits only along DAG edges, and issues
+ * host-to-device copies as DAG nodes so they overlap computation (Section
+ * III-B "System Architecture", Section III-C "Scheduling Policies and Stream
+ * Management").  Argument annotations follow Section III-D ("Language Design
+ * and Integration").
+ *
+ * Conventions for every call:
+ *   - returns GDAG_OK (0) or a negative GDAG_ERR_* code; gdag_last_error()
+ *     gives a message for the last failing call on that context;
+ *   - pointers named dev* are CUDA device pointers, host* are host pointers;
+ *   - a context belongs to one host thread and is not thread-safe;
+ *   - after a CUDA error that poisons the device context (a sticky error) the
+ *     gdag context is poisoned and every later call returns
+ *     GDAG_ERR_POISONED; gdag_destroy() still releases host resources;
+ *   - host waits poll for completion against options.timeout_ms and return
+ *     GDAG_ERR_TIMEOUT instead of blocking forever.
+ */
+#ifndef GDAG_H
+#define GDAG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------- status */
+#define GDAG_OK             0
+#define GDAG_ERR_INVALID   -1  /* bad argument, unknown handle, size error   */
+#define GDAG_ERR_CUDA      -2  /* a CUDA runtime call failed (not sticky)    */
+#define GDAG_ERR_TIMEOUT   -3  /* a host wait passed options.timeout_ms      */
+#define GDAG_ERR_OOM       -4  /* host or pinned allocation failed           */
+#define GDAG_ERR_POISONED  -5  /* an earlier sticky CUDA error               */
+#define GDAG_ERR_BUSY      -6  /* array still referenced by active nodes     */
+#define GDAG_ERR_NOT_FOUND -7  /* no built-in kernel of that name            */
+
+/* ------------------------------------------------------------- policies
+ * Section III-C: a serial scheduler runs elements one after the other with
+ * no overlap; a parallel one lets dependencies alone order them.  A
+ * synchronous one makes the host wait for every GPU element; an asynchronous
+ * one does not.  The paper's baseline is serial+synchronous, its method
+ * parallel+asynchronous.                                                   */
+#define GDAG_POLICY_SERIAL_SYNC  0  /* one stream, host waits after each op  */
+#define GDAG_POLICY_SERIAL_ASYNC 1  /* one stream, no host waits             */
+#define GDAG_POLICY_PARALLEL     2  /* DAG-driven multi-stream (default)     */
+
+#define GDAG_BACKEND_CUDA 0  /* real device                                  */
+#define GDAG_BACKEND_FAKE 1  /* records operations only; runs and computes
+                                nothing (scheduler tests without a GPU)      */
+
+/* ------------------------------------------------------- access modes
+ * Section III-D: "input" and "const" arguments are read-only; "output" and
+ * unannotated arguments are treated as modified.  OUT is write-only for edge
+ * labelling; INOUT and DEFAULT read and write.                             */
+#define GDAG_MODE_DEFAULT 0
+#define GDAG_MODE_IN      1
+#define GDAG_MODE_CONST   2
+#define GDAG_MODE_OUT     3
+#define GDAG_MODE_INOUT   4
+#define GDAG_MODE_SIGNATURE -1  /* gdag_arg.mode: keep the signature's mode */
+
+/* ----------------------------------------------------------- edge kinds */
+#define GDAG_EDGE_RAW 0
+#define GDAG_EDGE_WAR 1
+#define GDAG_EDGE_WAW 2
+
+/* ----------------------------------------------------------- node kinds */
+#define GDAG_NODE_KERNEL     0
+#define GDAG_NODE_HOST_WRITE 1  /* host-to-device copy of a host write      */
+#define GDAG_NODE_HOST_READ  2  /* host read (device-to-host copy if needed) */
+#define GDAG_NODE_EXTERNAL   3  /* library call given the chosen stream     */
+
+typedef struct gdag_ctx gdag_ctx;
+typedef int32_t gdag_array;   /* array handle, >= 0                          */
+typedef int32_t gdag_kernel;  /* kernel handle, >= 0                         */
+
+typedef struct {
+    uint32_t x, y, z;
+} gdag_dim3;
+
+typedef struct {
+    int32_t policy;          /* GDAG_POLICY_*; default PARALLEL              */
+    int32_t backend;         /* GDAG_BACKEND_*; default CUDA                 */
+    int32_t device;          /* CUDA device ordinal; default 0               */
+    int32_t max_streams;     /* stream pool cap; default 16                  */
+    int32_t prefetch;        /* 1: host writes become asynchronous copy
+                                nodes that overlap compute; 0: each host
+                                write's copy completes before the call
+                                returns; default 1                           */
+    int32_t retire_by_query; /* 1: at each new element, parents whose event
+                                has completed are retired without a host
+                                wait; default 0 (the paper retires on host
+                                access only)                                  */
+    int32_t record_log;      /* 1: keep element, edge and op logs for the
+                                export calls; default 0                      */
+    int32_t trace;           /* 1: timing events around every node for
+                                gdag_trace_export; default 0                 */
+    int32_t timeout_ms;      /* host-wait deadline; default 60000            */
+    int32_t fake_complete;   /* FAKE backend: 1 = an event reports complete
+                                when queried; 0 = only after a host wait;
+                                2 = never (host waits time out)              */
+    int32_t fake_fail_sticky;/* FAKE backend: 1 = the injected failure is a
+                                sticky (context-losing) error                */
+    int64_t fake_fail_op;    /* FAKE backend: index of the backend operation
+                                (launch, copy, record, wait, external) that
+                                fails, -1 = none                              */
+} gdag_options;
+
+/* Array argument or scalar argument of a launch. */
+#define GDAG_ARG_ARRAY  0
+#define GDAG_ARG_SCALAR 1
+
+typedef struct {
+    int32_t kind;    /* GDAG_ARG_ARRAY or GDAG_ARG_SCALAR                    */
+    int32_t mode;    /* arrays: GDAG_MODE_SIGNATURE or a GDAG_MODE_* override */
+    int32_t array;   /* arrays: handle                                       */
+    int32_t size;    /* scalars: bytes, 1..8 (must match the signature)      */
+    uint64_t value;  /* scalars: the value's bytes, little-endian            */
+} gdag_arg;
+
+typedef struct {
+    int32_t kind;    /* GDAG_ARG_ARRAY or GDAG_ARG_SCALAR                    */
+    int32_t mode;    /* arrays: GDAG_MODE_*                                  */
+    int32_t size;    /* scalars: bytes                                       */
+    int32_t reserved;
+} gdag_argspec;
+
+/* One logical DAG edge src -> dst caused by `array`. */
+typedef struct {
+    int64_t src, dst;
+    int32_t array;
+    int32_t kind;    /* GDAG_EDGE_*                                          */
+} gdag_edge;
+
+/* One element of the program, in issue order (node ids are consecutive). */
+typedef struct {
+    int64_t id;
+    int32_t kind;    /* GDAG_NODE_*                                          */
+    int32_t stream;  /* pool index of the stream it ran on, -1 = host only   */
+} gdag_node_info;
+
+/* One recorded runtime operation (issue order). */
+#define GDAG_OP_LAUNCH      0
+#define GDAG_OP_COPY_H2D    1
+#define GDAG_OP_COPY_D2H    2
+#define GDAG_OP_EXTERNAL    3
+#define GDAG_OP_RECORD      4
+#define GDAG_OP_WAIT        5
+#define GDAG_OP_HOST_WAIT   6
+#define GDAG_OP_STREAM_SYNC 7
+#define GDAG_OP_HOST_NODE   8  /* host-only element (read from the view)  */
+#define GDAG_OP_QUERY_DONE  9  /* an event query found the node complete  */
+typedef struct {
+    int32_t type;    /* GDAG_OP_*                                            */
+    int32_t stream;  /* pool index, -1 for host ops                          */
+    int32_t event;   /* event slot for RECORD/WAIT/HOST_WAIT, else -1        */
+    int32_t reserved;
+    int64_t node;    /* node the op belongs to, -1 if none                   */
+} gdag_op;
+
+/* Timing of one node when options.trace = 1 (ms from context creation). */
+typedef struct {
+    int64_t node;
+    int32_t kind;
+    int32_t stream;
+    double start_ms, end_ms;
+} gdag_trace_rec;
+
+typedef struct {
+    int64_t nodes;          /* elements issued                               */
+    int64_t edges;          /* logical edges inferred                        */
+    int64_t waits;          /* cudaStreamWaitEvent calls issued              */
+    int64_t launches;       /* kernel launches issued (all nodes)            */
+    int64_t copies;         /* host<->device copies issued                   */
+    int64_t host_waits;     /* host blocking waits                           */
+    int32_t streams;        /* streams in the pool                           */
+    int32_t active;         /* nodes currently active                        */
+} gdag_stats;
+
+/* ------------------------------------------------------------ lifetime */
+
+/* Fill *o with the defaults listed in gdag_options. */
+void gdag_options_default(gdag_options *o);
+
+/* Create a context.  opts may be NULL (defaults).  With the CUDA backend the
+ * device is made current; streams are created lazily (non-blocking streams,
+ * owned by the library).  Errors: INVALID, CUDA, OOM. */
+int gdag_create(gdag_ctx **out, const gdag_options *opts);
+
+/* Wait for all work (bounded by timeout_ms), then free every library-owned
+ * stream, event and pinned buffer.  Caller-owned memory is not touched. */
+int gdag_destroy(gdag_ctx *ctx);
+
+/* Message of the last failing call on ctx ("" if none).  Owned by ctx. */
+const char *gdag_last_error(gdag_ctx *ctx);
+
+/* Add a caller-owned CUDA stream (cudaStream_t) to the pool; the library
+ * uses it like its own but never destroys it.  INVALID past max_streams. */
+int gdag_add_stream(gdag_ctx *ctx, void *stream);
+
+/* --------------------------------------------------------------- arrays
+ * Section III-A: arrays are managed objects, so dependency identity is array
+ * identity (no aliasing between distinct handles).
+ *
+ * Register `bytes` of device memory at dev (non-owning; the caller keeps it
+ * alive until unregister).  host is an optional caller-owned pinned host
+ * buffer of the same size used as the array's host view; if NULL, the library
+ * allocates one (cudaHostAlloc) on the first host access.  Errors: INVALID
+ * (dev NULL with bytes > 0). */
+int gdag_array_register(gdag_ctx *ctx, void *dev, size_t bytes, void *host,
+                        gdag_array *out);
+
+/* Wait (bounded) for every active element that uses the array, then forget
+ * it; frees the library-owned host view. */
+int gdag_array_unregister(gdag_ctx *ctx, gdag_array a);
+
+/* Host view of the array (allocating it if needed).  mode GDAG_MODE_IN:
+ * waits until the view holds the array's current contents (a host read of
+ * the whole array).  mode GDAG_MODE_OUT: waits until no copy in flight reads
+ * the view, so the caller may overwrite it and then call gdag_array_write
+ * with src = NULL.  Section III-A: a host access that conflicts with active
+ * GPU work waits for it. */
+int gdag_array_host(gdag_ctx *ctx, gdag_array a, int32_t mode, void **out);
+
+/* Host write of [off, off+bytes) (Sections III-A and III-C).  src == NULL, or
+ * src equal to the host view + off: the caller already wrote the view.
+ * Otherwise src is copied into the view first (after any copy in flight from
+ * that region completes); src may be reused when the call returns.  The
+ * device copy is a DAG node that writes the array: it waits on the GPU for
+ * the array's active readers (WAR) or writer (WAW), never on the host.
+ * Errors: INVALID (range), TIMEOUT, CUDA. */
+int gdag_array_write(gdag_ctx *ctx, gdag_array a, const void *src, size_t off,
+                     size_t bytes);
+
+/* Host read of [off, off+bytes) into dst (dst == NULL or equal to host view
+ * + off: leave it in the view).  If the device holds newer data than the
+ * view, a device-to-host copy runs after the array's last writer and the
+ * host waits for it; that node and all its ancestors become inactive
+ * (Section III-B: computations stay active until the host needs their result
+ * or a child's).  Errors: INVALID, TIMEOUT, CUDA. */
+int gdag_array_read(gdag_ctx *ctx, gdag_array a, void *dst, size_t off,
+                    size_t bytes);
+
+/* -------------------------------------------------------------- kernels
+ * Built-in sm_103a kernels with their signatures (argument order and modes
+ * in the kernel table, README of the package).  Errors: NOT_FOUND. */
+int gdag_kernel_lookup(gdag_ctx *ctx, const char *name, gdag_kernel *out);
+
+/* Number of arguments of kernel k and its signature (spec may be NULL). */
+int gdag_kernel_signature(gdag_ctx *ctx, gdag_kernel k, int32_t *nargs,
+                          gdag_argspec *spec, int32_t cap);
+
+/* Register a user kernel: fn is a __global__ function's host handle usable
+ * with cudaLaunchKernel; spec gives each argument's kind, access mode
+ * (Section III-D annotations) and scalar size.  nargs <= 16. */
+int gdag_kernel_register(gdag_ctx *ctx, const char *name, const void *fn,
+                         int32_t nargs, const gdag_argspec *spec,
+                         gdag_kernel *out);
+
+/* Launch kernel k as a DAG element (Section III-A, III-B).  grid = {0,0,0}
+ * lets a built-in kernel pick its own launch shape (block and smem are then
+ * ignored).  For every array argument the dependency sets are updated and
+ * edges inferred; the stream is chosen by the policy (first child on its
+ * parent's stream, else the oldest empty stream, else a new one up to
+ * max_streams, else the least recently used); the stream waits on the events
+ * of active parents on other streams; the node records its own event.
+ * Never blocks the host except under GDAG_POLICY_SERIAL_SYNC.  *node_out
+ * (may be NULL) receives the node id.  Errors: INVALID (unknown array or
+ * kernel, argument count or kind mismatch), CUDA. */
+int gdag_launch(gdag_ctx *ctx, gdag_kernel k, gdag_dim3 grid, gdag_dim3 block,
+                size_t smem, const gdag_arg *args, int32_t nargs,
+                int64_t *node_out);
+
+/* Launch kernel k on the caller's CUDA stream with no dependency tracking
+ * (hand-scheduled baselines and graph capture).  Arrays are resolved to their
+ * device pointers only. */
+int gdag_launch_raw(gdag_ctx *ctx, gdag_kernel k, gdag_dim3 grid,
+                    gdag_dim3 block, size_t smem, const gdag_arg *args,
+                    int32_t nargs, void *stream);
+
+/* A library call as a DAG element (Section III-A: pre-registered library
+ * functions are scheduled asynchronously when they take a stream).  fn is
+ * called on the host with the chosen cudaStream_t and user; it must only
+ * enqueue work on that stream.  arrays/modes give its accesses. */
+int gdag_launch_external(gdag_ctx *ctx, void (*fn)(void *stream, void *user),
+                         void *user, const gdag_array *arrays,
+                         const int32_t *modes, int32_t n, int64_t *node_out);
+
+/* ----------------------------------------------------------------- sync */
+
+/* Wait for every stream (bounded) and retire every node. */
+int gdag_sync(gdag_ctx *ctx);
+
+/* Make the caller's CUDA stream wait for all work issued so far, without
+ * blocking the host (a join for timing events or stream capture). */
+int gdag_stream_wait_all(gdag_ctx *ctx, void *stream);
+
+/* Make every pool stream wait for the caller's stream's work issued so far
+ * (a fork: later nodes run after it). */
+int gdag_stream_fork(gdag_ctx *ctx, void *stream);
+
+/* ---------------------------------------------------------- inspection */
+
+/* Copy up to cap records; *n receives the total available.  These need
+ * options.record_log = 1 (INVALID otherwise). */
+int gdag_dag_export(gdag_ctx *ctx, gdag_edge *buf, size_t cap, size_t *n);
+int gdag_nodes_export(gdag_ctx *ctx, gdag_node_info *buf, size_t cap,
+                      size_t *n);
+int gdag_ops_export(gdag_ctx *ctx, gdag_op *buf, size_t cap, size_t *n);
+
+/* Timing records (options.trace = 1); waits for completion first. */
+int gdag_trace_export(gdag_ctx *ctx, gdag_trace_rec *buf, size_t cap,
+                      size_t *n);
+
+int gdag_stats_get(gdag_ctx *ctx, gdag_stats *out);
+
+/* Bytes of scratch the built-in reductions (vec_reduce_diff, minmax, l2norm)
+ * and spmv_csr need for `n` elements; the scratch array must be zeroed once
+ * before its first use and is left zeroed-counter by every launch. */
+size_t gdag_scratch_bytes(const char *kernel, int64_t n);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GDAG_H */

@@ -86,7 +86,7 @@ def closure(pairs, L):
 # Op types (numbering of the C ABI's gdag_op.type):
 OP_LAUNCH, OP_COPY_H2D, OP_COPY_D2H, OP_EXTERNAL = 0, 1, 2, 3
 OP_RECORD, OP_WAIT = 4, 5
-OP_HOST_WAIT, OP_STREAM_SYNC, OP_HOST_NODE = 6, 7, 8
+OP_HOST_WAIT, OP_STREAM_SYNC, OP_HOST_NODE, OP_QUERY_DONE = 6, 7, 8, 9
 WORK_OPS = (OP_LAUNCH, OP_COPY_H2D, OP_COPY_D2H, OP_EXTERNAL)
 
 
@@ -98,7 +98,9 @@ def happens_before(ops):
       before the WAIT ahead of everything after the WAIT on its stream;
     * a HOST_WAIT on e (or a STREAM_SYNC of s) returns only after the latest
       RECORD of e (the last op on s) completed; the host issues everything
-      after it later, and host-only elements (HOST_NODE) run at issue time.
+      after it later, and host-only elements (HOST_NODE) run at issue time;
+    * a QUERY_DONE on e is a non-blocking query that found the latest RECORD
+      of e complete: for ordering it is a host wait that did not block.
 
     ``ops`` is a list of tuples (type, stream, event, node) in issue order.
     Returns ``anc`` with bit p of anc[q] set iff op p happens before op q."""
@@ -115,7 +117,7 @@ def happens_before(ops):
                 preds.append(last_on_stream[s])
             if t == OP_WAIT and e in last_record:
                 preds.append(last_record[e])
-        elif t == OP_HOST_WAIT:
+        elif t in (OP_HOST_WAIT, OP_QUERY_DONE):
             if e in last_record:
                 preds.append(last_record[e])
         elif t == OP_STREAM_SYNC:
@@ -129,7 +131,7 @@ def happens_before(ops):
             last_on_stream[s] = q
         if t == OP_RECORD:
             last_record[e] = q
-        if t in (OP_HOST_WAIT, OP_STREAM_SYNC, OP_HOST_NODE):
+        if t in (OP_HOST_WAIT, OP_STREAM_SYNC, OP_HOST_NODE, OP_QUERY_DONE):
             host_frontier = q
     return anc
 
@@ -144,7 +146,12 @@ def node_ops(ops):
 
 
 def check_hb(ops, edges):
-    """Edges (i, j, ...) whose work ops are not ordered i before j."""
+    """Edges (i, j, ...) whose work ops are not ordered i before j.
+
+    A host write fills the array's host view on the host when it is issued
+    (its COPY_H2D then moves the view to the device), so a host read served
+    from the view (a HOST_NODE) is ordered after an earlier host write by
+    program order alone."""
     anc = happens_before(ops)
     where = node_ops(ops)
     bad = []
@@ -152,6 +159,8 @@ def check_hb(ops, edges):
         i, j = e[0], e[1]
         if i not in where or j not in where:
             bad.append(e)
+            continue
+        if ops[where[i]][0] == OP_COPY_H2D and ops[where[j]][0] == OP_HOST_NODE and where[i] < where[j]:
             continue
         if not (anc[where[j]] >> where[i]) & 1:
             bad.append(e)

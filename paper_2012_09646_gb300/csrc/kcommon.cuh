@@ -1,0 +1,123 @@
+// Helpers shared by the built-in kernels: launch sizing for 152-SM GB300,
+// deterministic block reductions, the last-block-done combine.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+namespace gdag {
+
+// Multiprocessor count of the current device (queried once per process).
+inline int sm_count()
+{
+    static int n = 0;
+    if (!n) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 152;
+    }
+    return n;
+}
+
+inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+// Streaming kernels: each block handles tiles of kThreads x kUnroll float4,
+// grid-stride over tiles, at most kBlocksPerSm resident blocks per SM.
+constexpr int kThreads = 256;
+constexpr int kUnroll = 4;
+constexpr int kBlocksPerSm = 8;
+
+inline unsigned stream_grid(int64_t n_vec4)
+{
+    int64_t tiles = ceil_div(n_vec4 > 0 ? n_vec4 : 1, (int64_t)kThreads * kUnroll);
+    int64_t cap = (int64_t)sm_count() * kBlocksPerSm;
+    return (unsigned)(tiles < cap ? tiles : cap);
+}
+
+// Reductions: a fixed grid that depends only on n and the SM count, so the
+// summation order (and the result) is the same on every run.
+constexpr int kReduceMaxBlocks = 1024;
+
+inline unsigned reduce_grid(int64_t n_vec4)
+{
+    int64_t tiles = ceil_div(n_vec4 > 0 ? n_vec4 : 1, (int64_t)kThreads * kUnroll);
+    int64_t cap = (int64_t)sm_count() * 2;
+    if (cap > kReduceMaxBlocks) cap = kReduceMaxBlocks;
+    return (unsigned)(tiles < cap ? tiles : cap);
+}
+
+// Scratch of one reduction: kReduceMaxBlocks partials of `Width` doubles,
+// then a 32-bit arrival counter (zero between launches).
+template <int Width> constexpr size_t reduce_scratch_bytes()
+{
+    return sizeof(double) * Width * kReduceMaxBlocks + 16;
+}
+
+#ifdef __CUDACC__
+__device__ __forceinline__ double warp_sum(double v)
+{
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ float warp_min(float v)
+{
+    for (int o = 16; o > 0; o >>= 1) v = fminf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+__device__ __forceinline__ float warp_max(float v)
+{
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// Sum of v over the block (blockDim.x == kThreads), fixed order; valid in
+// thread 0.  `sh` holds kThreads/32 doubles.
+__device__ __forceinline__ double block_sum(double v, double *sh)
+{
+    v = warp_sum(v);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) sh[warp] = v;
+    __syncthreads();
+    double s = 0.0;
+    if (threadIdx.x < 32) {
+        s = (lane < kThreads / 32) ? sh[lane] : 0.0;
+        s = warp_sum(s);
+    }
+    __syncthreads();
+    return s;
+}
+
+// Last-block-done: each block publishes its partial(s), then one arrival
+// counter tells the last block to combine all partials in block order.
+// Returns true in the block that arrived last (all threads).
+__device__ __forceinline__ bool arrive_last(unsigned *counter)
+{
+    __shared__ bool last;
+    __threadfence();  // partials visible device-wide before arrival
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned prev = atomicAdd(counter, 1u);
+        last = (prev == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (last) __threadfence();  // see every other block's partials
+    return last;
+}
+
+// Kahan-compensated fp32 accumulation: per-thread sums stay accurate to a
+// few ulp however many elements a thread visits.
+struct Kahan {
+    float s = 0.f, c = 0.f;
+    __device__ __forceinline__ void add(float v)
+    {
+        float y = v - c;
+        float t = s + y;
+        c = (t - s) - y;
+        s = t;
+    }
+    __device__ __forceinline__ double value() const { return (double)s - (double)c; }
+};
+#endif
+
+}  // namespace gdag

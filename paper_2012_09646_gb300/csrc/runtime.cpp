@@ -1,0 +1,1047 @@
+// Dependency tracker, stream manager and C ABI of libgdag.
+//
+// Section III-A (Computation DAG and dependency sets): every kernel launch,
+// host array access and library call is a computational element.  For each
+// array the tracker keeps the last writer W and the readers R since W; a
+// reader gets an edge from W; a writer gets edges from every reader in R, or
+// from W when R is empty, and then becomes the new W with R emptied.  This is
+// the paper's dependency-set rule (a read-only use adds an edge but does not
+// remove the argument from the parent's set; a later writer depends on all
+// readers, not on the writer).
+//
+// Section III-B (System Architecture): elements stay active until the host
+// needs their result or a child's; only active parents cause waits.
+//
+// Section III-C (Scheduling Policies and Stream Management): the first child
+// of a parent runs on the parent's stream; otherwise the oldest empty stream
+// is reused (FIFO), a new stream is created only if none is empty, and one
+// event per element provides the cross-stream synchronization.
+#include <algorithm>
+#include <chrono>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <deque>
+#include <memory>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "backend.h"
+#include "catalog.h"
+#include "gdag.h"
+
+namespace gdag {
+namespace {
+
+constexpr int R_BIT = 1, W_BIT = 2;
+
+int mode_bits(int mode)
+{
+    switch (mode) {
+    case GDAG_MODE_IN:
+    case GDAG_MODE_CONST:
+        return R_BIT;
+    case GDAG_MODE_OUT:
+        return W_BIT;
+    default:  // INOUT and unannotated: read and modified
+        return R_BIT | W_BIT;
+    }
+}
+
+struct Node {
+    int32_t kind = 0;
+    int32_t stream = -1;
+    int32_t event = -1;       // pooled event slot (active nodes only)
+    int32_t tev0 = -1, tev1 = -1;  // timing events (trace)
+    bool active = false;
+    bool first_child_taken = false;
+    uint32_t parent_off = 0, parent_cnt = 0;
+};
+
+struct ArrayState {
+    void *dev = nullptr;
+    size_t bytes = 0;
+    void *host = nullptr;
+    bool host_owned = false;
+    bool live = false;
+    bool host_valid = false;  // host view holds the current contents
+    int64_t writer = -1;
+    std::vector<int64_t> readers;
+    int64_t host_copy = -1;   // last host-to-device copy reading the view
+};
+
+struct StreamState {
+    void *handle = nullptr;
+    bool owned = true;
+    int64_t tail = -1;
+    int32_t active = 0;
+    uint64_t last_use = 0;
+    bool queued = false;
+};
+
+struct Access {
+    int32_t array;
+    int32_t bits;
+};
+
+}  // namespace
+
+struct Ctx {
+    gdag_options opt;
+    std::unique_ptr<Backend> be;
+    std::string last_error;
+    bool poisoned = false;
+
+    std::vector<KernelEntry> kernels;
+    std::vector<ArrayState> arrays;
+    std::vector<int32_t> free_arrays;
+
+    // node table: ids [base, base + nodes.size())
+    int64_t base = 0;
+    std::deque<Node> nodes;
+    std::vector<int64_t> parent_arena;
+    int64_t active_count = 0;
+
+    std::vector<StreamState> streams;
+    std::deque<int32_t> free_streams;  // empty streams, oldest first
+    uint64_t tick = 0;
+
+    std::vector<void *> events;      // pooled (non-timing)
+    std::vector<int32_t> free_events;
+    std::vector<void *> tevents;     // timing events (trace), never reused
+    void *t0 = nullptr;              // trace time base
+
+    // logs
+    std::vector<gdag_edge> edge_log;
+    std::vector<gdag_node_info> node_log;
+    std::vector<gdag_op> op_log;
+    gdag_stats st{};
+
+    // scratch for one element
+    std::vector<int64_t> par;
+
+    // ------------------------------------------------------------- errors
+    int fail(int code, const char *fmt, ...)
+    {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof buf, fmt, ap);
+        va_end(ap);
+        last_error = buf;
+        return code;
+    }
+    int be_fail(int r, const char *what)
+    {
+        if (r == BE_STICKY) poisoned = true;
+        return fail(r == BE_STICKY ? GDAG_ERR_POISONED : GDAG_ERR_CUDA, "%s: %s", what, be->err.c_str());
+    }
+
+    void log_op(int type, int stream, int event, int64_t node)
+    {
+        if (opt.record_log) op_log.push_back(gdag_op{type, stream, event, 0, node});
+    }
+
+    // ------------------------------------------------------------- nodes
+    Node *node(int64_t id)
+    {
+        if (id < base || id >= base + (int64_t)nodes.size()) return nullptr;
+        return &nodes[(size_t)(id - base)];
+    }
+    int64_t next_id() const { return base + (int64_t)nodes.size(); }
+
+    int acquire_event(int32_t *slot)
+    {
+        if (!free_events.empty()) {
+            *slot = free_events.back();
+            free_events.pop_back();
+            return GDAG_OK;
+        }
+        void *e;
+        int r = be->event_create(&e, false);
+        if (r) return be_fail(r, "event create");
+        events.push_back(e);
+        *slot = (int32_t)events.size() - 1;
+        return GDAG_OK;
+    }
+
+    // Retire node id and all its active ancestors (their results are
+    // complete once the host has observed id's completion).
+    void retire(int64_t id)
+    {
+        std::vector<int64_t> stack{id};
+        while (!stack.empty()) {
+            int64_t v = stack.back();
+            stack.pop_back();
+            Node *n = node(v);
+            if (!n || !n->active) continue;
+            n->active = false;
+            --active_count;
+            if (n->event >= 0) {
+                free_events.push_back(n->event);
+                n->event = -1;
+            }
+            if (n->stream >= 0) {
+                StreamState &s = streams[(size_t)n->stream];
+                if (--s.active == 0 && !s.queued) {
+                    s.queued = true;
+                    free_streams.push_back(n->stream);
+                }
+            }
+            for (uint32_t k = 0; k < n->parent_cnt; ++k) stack.push_back(parent_arena[n->parent_off + k]);
+        }
+    }
+
+    void retire_all()
+    {
+        for (size_t i = 0; i < nodes.size(); ++i)
+            if (nodes[i].active) retire(base + (int64_t)i);
+    }
+
+    // Host wait for node id (bounded); retires it and its ancestors.
+    int host_wait(int64_t id)
+    {
+        Node *n = node(id);
+        if (!n || !n->active) return GDAG_OK;
+        if (n->event < 0) {
+            retire(id);
+            return GDAG_OK;
+        }
+        log_op(GDAG_OP_HOST_WAIT, n->stream, n->event, id);
+        ++st.host_waits;
+        int r = poll_event(events[(size_t)n->event]);
+        if (r) return r;
+        retire(id);
+        return GDAG_OK;
+    }
+
+    int poll_event(void *ev)
+    {
+        auto t_end = std::chrono::steady_clock::now() + std::chrono::milliseconds(opt.timeout_ms);
+        unsigned spins = 0;
+        for (;;) {
+            int q = be->wait_query_event(ev);
+            if (q == BE_OK) return GDAG_OK;
+            if (q != BE_NOT_READY) return be_fail(q, "event query");
+            if (++spins > 64) {
+                if (std::chrono::steady_clock::now() > t_end)
+                    return fail(GDAG_ERR_TIMEOUT, "host wait exceeded %d ms", opt.timeout_ms);
+                std::this_thread::yield();
+            }
+        }
+    }
+
+    int poll_stream(int32_t s)
+    {
+        auto t_end = std::chrono::steady_clock::now() + std::chrono::milliseconds(opt.timeout_ms);
+        unsigned spins = 0;
+        for (;;) {
+            int q = be->wait_query_stream(streams[(size_t)s].handle);
+            if (q == BE_OK) return GDAG_OK;
+            if (q != BE_NOT_READY) return be_fail(q, "stream query");
+            if (++spins > 64) {
+                if (std::chrono::steady_clock::now() > t_end)
+                    return fail(GDAG_ERR_TIMEOUT, "stream sync exceeded %d ms", opt.timeout_ms);
+                std::this_thread::yield();
+            }
+        }
+    }
+
+    // ------------------------------------------------------------ streams
+    int new_stream(int32_t *out)
+    {
+        void *h;
+        int r = be->stream_create(&h);
+        if (r) return be_fail(r, "stream create");
+        StreamState s;
+        s.handle = h;
+        streams.push_back(s);
+        *out = (int32_t)streams.size() - 1;
+        if (opt.trace && !t0) {
+            int rr = be->event_create(&t0, true);
+            if (rr) return be_fail(rr, "event create");
+            rr = be->event_record(t0, h);
+            if (rr) return be_fail(rr, "event record");
+        }
+        return GDAG_OK;
+    }
+
+    // Section III-C stream choice for a new element with parents `par`.
+    int pick_stream(int32_t *out)
+    {
+        if (opt.policy != GDAG_POLICY_PARALLEL) {
+            if (streams.empty()) {
+                int r = new_stream(out);
+                if (r) return r;
+            }
+            *out = 0;
+            return GDAG_OK;
+        }
+        // first child on a parent's stream: the parent must be active, be
+        // the last work issued on its stream, and have no child there yet
+        for (int64_t p : par) {
+            Node *n = node(p);
+            if (!n || !n->active || n->stream < 0) continue;
+            if (streams[(size_t)n->stream].tail == p && !n->first_child_taken) {
+                n->first_child_taken = true;
+                *out = n->stream;
+                return GDAG_OK;
+            }
+        }
+        // oldest empty stream
+        while (!free_streams.empty()) {
+            int32_t s = free_streams.front();
+            free_streams.pop_front();
+            streams[(size_t)s].queued = false;
+            if (streams[(size_t)s].active == 0) {
+                *out = s;
+                return GDAG_OK;
+            }
+        }
+        if ((int)streams.size() < opt.max_streams) return new_stream(out);
+        // cap reached: least recently used stream
+        int32_t best = 0;
+        for (size_t i = 1; i < streams.size(); ++i)
+            if (streams[i].last_use < streams[(size_t)best].last_use) best = (int32_t)i;
+        *out = best;
+        return GDAG_OK;
+    }
+
+    // --------------------------------------------------------- tracking
+    void add_edge(int64_t src, int64_t dst, int32_t a, int32_t kind)
+    {
+        ++st.edges;
+        if (opt.record_log) edge_log.push_back(gdag_edge{src, dst, a, kind});
+        if (std::find(par.begin(), par.end(), src) == par.end()) par.push_back(src);
+    }
+
+    // Section III-A dependency rule for element `id` with accesses acc.
+    void infer(int64_t id, const Access *acc, int n)
+    {
+        par.clear();
+        for (int i = 0; i < n; ++i) {
+            ArrayState &s = arrays[(size_t)acc[i].array];
+            int bits = acc[i].bits;
+            if (!(bits & W_BIT)) {
+                if (s.writer >= 0) add_edge(s.writer, id, acc[i].array, GDAG_EDGE_RAW);
+                s.readers.push_back(id);
+            } else {
+                if (!s.readers.empty()) {
+                    for (int64_t r : s.readers) add_edge(r, id, acc[i].array, GDAG_EDGE_WAR);
+                } else if (s.writer >= 0) {
+                    add_edge(s.writer, id, acc[i].array, (bits & R_BIT) ? GDAG_EDGE_RAW : GDAG_EDGE_WAW);
+                }
+                s.writer = id;
+                s.readers.clear();
+            }
+        }
+        std::sort(par.begin(), par.end());
+    }
+
+    // Append the node for element `id` (after infer()).
+    void push_node(int32_t kind)
+    {
+        Node nd;
+        nd.kind = kind;
+        nd.parent_off = (uint32_t)parent_arena.size();
+        nd.parent_cnt = (uint32_t)par.size();
+        parent_arena.insert(parent_arena.end(), par.begin(), par.end());
+        nodes.push_back(nd);
+        ++st.nodes;
+        if (opt.record_log) node_log.push_back(gdag_node_info{next_id() - 1, kind, -1});
+    }
+
+    // Optionally retire completed parents without a host wait.
+    int retire_done_parents()
+    {
+        if (!opt.retire_by_query) return GDAG_OK;
+        for (int64_t p : par) {
+            Node *n = node(p);
+            if (!n || !n->active || n->event < 0) continue;
+            int q = be->event_query(events[(size_t)n->event]);
+            if (q == BE_OK) {
+                log_op(GDAG_OP_QUERY_DONE, n->stream, n->event, p);
+                retire(p);
+            }
+            else if (q != BE_NOT_READY)
+                return be_fail(q, "event query");
+        }
+        return GDAG_OK;
+    }
+
+    // Choose the stream, issue waits on active parents of other streams
+    // (only the latest parent per stream), mark the node active there.
+    int place(int64_t id, int32_t *stream_out)
+    {
+        int r = retire_done_parents();
+        if (r) return r;
+        int32_t s;
+        r = pick_stream(&s);
+        if (r) return r;
+        // waits: latest active parent per other stream
+        int64_t latest[64];
+        int nl = 0;
+        int32_t lstream[64];
+        for (int64_t p : par) {
+            Node *n = node(p);
+            if (!n || !n->active || n->stream < 0 || n->stream == s || n->event < 0) continue;
+            int k = 0;
+            while (k < nl && lstream[k] != n->stream) ++k;
+            if (k == nl) {
+                if (nl == 64) {  // more streams than the table: wait directly
+                    int rr = wait_on(s, p);
+                    if (rr) return rr;
+                    continue;
+                }
+                lstream[nl] = n->stream;
+                latest[nl++] = p;
+            } else if (p > latest[k]) {
+                latest[k] = p;
+            }
+        }
+        for (int k = 0; k < nl; ++k) {
+            r = wait_on(s, latest[k]);
+            if (r) return r;
+        }
+        Node *me = node(id);
+        me->stream = s;
+        me->active = true;
+        ++active_count;
+        StreamState &ss = streams[(size_t)s];
+        if (ss.queued) {  // taken from the FIFO by the LRU path: drop it
+            ss.queued = false;
+            free_streams.erase(std::find(free_streams.begin(), free_streams.end(), s));
+        }
+        ss.active++;
+        ss.tail = id;
+        ss.last_use = ++tick;
+        if (opt.record_log) node_log.back().stream = s;
+        *stream_out = s;
+        if (opt.trace) {
+            void *e;
+            r = be->event_create(&e, true);
+            if (r) return be_fail(r, "event create");
+            tevents.push_back(e);
+            me->tev0 = (int32_t)tevents.size() - 1;
+            r = be->event_record(e, ss.handle);
+            if (r) return be_fail(r, "event record");
+        }
+        return GDAG_OK;
+    }
+
+    int wait_on(int32_t s, int64_t p)
+    {
+        Node *n = node(p);
+        log_op(GDAG_OP_WAIT, s, n->event, p);
+        ++st.waits;
+        int r = be->stream_wait(streams[(size_t)s].handle, events[(size_t)n->event]);
+        if (r) return be_fail(r, "stream wait");
+        return GDAG_OK;
+    }
+
+    // After the node's work op: record its event; under SERIAL_SYNC wait.
+    int finish(int64_t id, int32_t s)
+    {
+        Node *me = node(id);
+        int r;
+        if (opt.trace) {
+            void *e;
+            r = be->event_create(&e, true);
+            if (r) return be_fail(r, "event create");
+            tevents.push_back(e);
+            me = node(id);
+            me->tev1 = (int32_t)tevents.size() - 1;
+            r = be->event_record(e, streams[(size_t)s].handle);
+            if (r) return be_fail(r, "event record");
+        }
+        int32_t slot;
+        r = acquire_event(&slot);
+        if (r) return r;
+        me = node(id);
+        me->event = slot;
+        log_op(GDAG_OP_RECORD, s, slot, id);
+        r = be->event_record(events[(size_t)slot], streams[(size_t)s].handle);
+        if (r) return be_fail(r, "event record");
+        if (opt.policy == GDAG_POLICY_SERIAL_SYNC) return host_wait(id);
+        return GDAG_OK;
+    }
+
+    // A failed work op: the node stays in the DAG as a retired element.
+    int abort_node(int64_t id, int r, const char *what)
+    {
+        retire(id);
+        return be_fail(r, what);
+    }
+
+    // ------------------------------------------------------------ arrays
+    ArrayState *arr(int32_t a)
+    {
+        if (a < 0 || (size_t)a >= arrays.size() || !arrays[(size_t)a].live) return nullptr;
+        return &arrays[(size_t)a];
+    }
+
+    int ensure_host(ArrayState &s)
+    {
+        if (s.host) return GDAG_OK;
+        int r = be->host_alloc(&s.host, s.bytes);
+        if (r) return fail(GDAG_ERR_OOM, "pinned host allocation of %zu bytes failed: %s", s.bytes, be->err.c_str());
+        s.host_owned = true;
+        return GDAG_OK;
+    }
+
+    // Wait until no host-to-device copy in flight reads the host view.
+    int release_view(ArrayState &s)
+    {
+        if (s.host_copy >= 0) {
+            Node *n = node(s.host_copy);
+            if (n && n->active) {
+                int r = host_wait(s.host_copy);
+                if (r) return r;
+            }
+            s.host_copy = -1;
+        }
+        return GDAG_OK;
+    }
+
+    int guard()
+    {
+        if (poisoned) return fail(GDAG_ERR_POISONED, "context poisoned by an earlier sticky CUDA error");
+        return GDAG_OK;
+    }
+};
+
+}  // namespace gdag
+
+using gdag::Access;
+using gdag::ArrayState;
+using gdag::Ctx;
+using gdag::KernelEntry;
+using gdag::LaunchArgs;
+
+struct gdag_ctx : Ctx {};
+
+template <class T>
+static int export_vec(gdag_ctx *c, const std::vector<T> &v, T *buf, size_t cap, size_t *n)
+{
+    if (!c || !n) return GDAG_ERR_INVALID;
+    if (!c->opt.record_log) return c->fail(GDAG_ERR_INVALID, "logs need options.record_log = 1");
+    *n = v.size();
+    if (buf)
+        for (size_t i = 0; i < v.size() && i < cap; ++i) buf[i] = v[i];
+    return GDAG_OK;
+}
+
+extern "C" {
+
+void gdag_options_default(gdag_options *o)
+{
+    std::memset(o, 0, sizeof *o);
+    o->policy = GDAG_POLICY_PARALLEL;
+    o->backend = GDAG_BACKEND_CUDA;
+    o->device = 0;
+    o->max_streams = 16;
+    o->prefetch = 1;
+    o->retire_by_query = 0;
+    o->record_log = 0;
+    o->trace = 0;
+    o->timeout_ms = 60000;
+    o->fake_complete = 0;
+    o->fake_fail_sticky = 0;
+    o->fake_fail_op = -1;
+}
+
+int gdag_create(gdag_ctx **out, const gdag_options *opts)
+{
+    if (!out) return GDAG_ERR_INVALID;
+    *out = nullptr;
+    gdag_options o;
+    if (opts)
+        o = *opts;
+    else
+        gdag_options_default(&o);
+    if (o.policy < 0 || o.policy > 2 || o.max_streams < 1 || o.max_streams > 1024 || o.timeout_ms <= 0 ||
+        (o.backend != GDAG_BACKEND_CUDA && o.backend != GDAG_BACKEND_FAKE))
+        return GDAG_ERR_INVALID;
+    gdag_ctx *c = new (std::nothrow) gdag_ctx();
+    if (!c) return GDAG_ERR_OOM;
+    c->opt = o;
+    c->be.reset(o.backend == GDAG_BACKEND_FAKE
+                    ? gdag::make_fake_backend(o.fake_complete, o.fake_fail_op, o.fake_fail_sticky)
+                    : gdag::make_cuda_backend());
+    int r = c->be->init(o.device);
+    if (r) {
+        delete c;
+        return r == gdag::BE_STICKY ? GDAG_ERR_POISONED : GDAG_ERR_CUDA;
+    }
+    for (int i = 0; i < gdag::builtin_count(); ++i) c->kernels.push_back(gdag::builtin(i));
+    *out = c;
+    return GDAG_OK;
+}
+
+int gdag_destroy(gdag_ctx *c)
+{
+    if (!c) return GDAG_ERR_INVALID;
+    int rc = GDAG_OK;
+    if (!c->poisoned) {
+        for (size_t s = 0; s < c->streams.size(); ++s) {
+            int r = c->poll_stream((int32_t)s);
+            if (r && !rc) rc = r;
+        }
+    }
+    for (auto &a : c->arrays)
+        if (a.live && a.host_owned) c->be->host_free(a.host);
+    for (void *e : c->events) c->be->event_destroy(e);
+    for (void *e : c->tevents) c->be->event_destroy(e);
+    if (c->t0) c->be->event_destroy(c->t0);
+    for (auto &s : c->streams)
+        if (s.owned) c->be->stream_destroy(s.handle);
+    delete c;
+    return rc;
+}
+
+const char *gdag_last_error(gdag_ctx *c) { return c ? c->last_error.c_str() : "null context"; }
+
+int gdag_add_stream(gdag_ctx *c, void *stream)
+{
+    if (!c) return GDAG_ERR_INVALID;
+    if ((int)c->streams.size() >= c->opt.max_streams) return c->fail(GDAG_ERR_INVALID, "stream pool full");
+    gdag::StreamState s;
+    s.handle = stream;
+    s.owned = false;
+    s.queued = true;
+    c->streams.push_back(s);
+    c->free_streams.push_back((int32_t)c->streams.size() - 1);
+    return GDAG_OK;
+}
+
+int gdag_array_register(gdag_ctx *c, void *dev, size_t bytes, void *host, gdag_array *out)
+{
+    if (!c || !out) return GDAG_ERR_INVALID;
+    if (!dev && bytes) return c->fail(GDAG_ERR_INVALID, "null device pointer");
+    int32_t id;
+    if (!c->free_arrays.empty()) {
+        id = c->free_arrays.back();
+        c->free_arrays.pop_back();
+    } else {
+        c->arrays.emplace_back();
+        id = (int32_t)c->arrays.size() - 1;
+    }
+    ArrayState &s = c->arrays[(size_t)id];
+    s = ArrayState();
+    s.dev = dev;
+    s.bytes = bytes;
+    s.host = host;
+    s.live = true;
+    *out = id;
+    return GDAG_OK;
+}
+
+int gdag_array_unregister(gdag_ctx *c, gdag_array a)
+{
+    if (!c) return GDAG_ERR_INVALID;
+    ArrayState *s = c->arr(a);
+    if (!s) return c->fail(GDAG_ERR_INVALID, "unknown array %d", a);
+    if (!c->poisoned) {
+        std::vector<int64_t> users = s->readers;
+        if (s->writer >= 0) users.push_back(s->writer);
+        for (int64_t u : users) {
+            int r = c->host_wait(u);
+            if (r) return r;
+        }
+        int r = c->release_view(*s);
+        if (r) return r;
+    }
+    if (s->host_owned) c->be->host_free(s->host);
+    *s = ArrayState();
+    c->free_arrays.push_back(a);
+    return GDAG_OK;
+}
+
+int gdag_kernel_lookup(gdag_ctx *c, const char *name, gdag_kernel *out)
+{
+    if (!c || !name || !out) return GDAG_ERR_INVALID;
+    for (size_t i = 0; i < c->kernels.size(); ++i)
+        if (c->kernels[i].name == name) {
+            *out = (gdag_kernel)i;
+            return GDAG_OK;
+        }
+    return c->fail(GDAG_ERR_NOT_FOUND, "no kernel named '%s'", name);
+}
+
+int gdag_kernel_signature(gdag_ctx *c, gdag_kernel k, int32_t *nargs, gdag_argspec *spec, int32_t cap)
+{
+    if (!c || k < 0 || (size_t)k >= c->kernels.size() || !nargs) return GDAG_ERR_INVALID;
+    const KernelEntry &e = c->kernels[(size_t)k];
+    *nargs = e.nargs;
+    if (spec)
+        for (int i = 0; i < e.nargs && i < cap; ++i) spec[i] = e.spec[i];
+    return GDAG_OK;
+}
+
+int gdag_kernel_register(gdag_ctx *c, const char *name, const void *fn, int32_t nargs, const gdag_argspec *spec,
+                         gdag_kernel *out)
+{
+    if (!c || !name || !out || (!fn && c->opt.backend == GDAG_BACKEND_CUDA)) return GDAG_ERR_INVALID;
+    if (nargs < 0 || nargs > gdag::kMaxArgs || (nargs && !spec))
+        return c->fail(GDAG_ERR_INVALID, "bad argument count %d", nargs);
+    KernelEntry e;
+    e.name = name;
+    e.fn = fn;
+    e.nargs = nargs;
+    for (int i = 0; i < nargs; ++i) {
+        if (spec[i].kind == GDAG_ARG_SCALAR && (spec[i].size < 1 || spec[i].size > 8))
+            return c->fail(GDAG_ERR_INVALID, "scalar argument %d: size %d not in 1..8", i, spec[i].size);
+        if (spec[i].kind != GDAG_ARG_SCALAR && spec[i].kind != GDAG_ARG_ARRAY)
+            return c->fail(GDAG_ERR_INVALID, "argument %d: bad kind", i);
+        e.spec[i] = spec[i];
+    }
+    c->kernels.push_back(e);
+    *out = (gdag_kernel)c->kernels.size() - 1;
+    return GDAG_OK;
+}
+
+// Resolve and validate arguments; fills acc (merged per array) and la.
+static int resolve(gdag_ctx *c, gdag_kernel k, gdag_dim3 grid, gdag_dim3 block, size_t smem, const gdag_arg *args,
+                   int32_t nargs, LaunchArgs &la, Access *acc, int *nacc)
+{
+    if (k < 0 || (size_t)k >= c->kernels.size()) return c->fail(GDAG_ERR_INVALID, "unknown kernel %d", k);
+    const KernelEntry &e = c->kernels[(size_t)k];
+    if (nargs != e.nargs)
+        return c->fail(GDAG_ERR_INVALID, "%s takes %d arguments, got %d", e.name.c_str(), e.nargs, nargs);
+    if (nargs && !args) return c->fail(GDAG_ERR_INVALID, "null argument list");
+    la.nargs = nargs;
+    *nacc = 0;
+    for (int i = 0; i < nargs; ++i) {
+        const gdag_arg &a = args[i];
+        if (a.kind != e.spec[i].kind)
+            return c->fail(GDAG_ERR_INVALID, "%s argument %d: expected %s", e.name.c_str(), i,
+                           e.spec[i].kind == GDAG_ARG_ARRAY ? "an array" : "a scalar");
+        la.ptr[i] = nullptr;
+        la.bytes[i] = 0;
+        la.val[i] = 0;
+        if (a.kind == GDAG_ARG_SCALAR) {
+            if (a.size != e.spec[i].size)
+                return c->fail(GDAG_ERR_INVALID, "%s argument %d: scalar of %d bytes, expected %d", e.name.c_str(), i,
+                               a.size, e.spec[i].size);
+            la.val[i] = a.value;
+            continue;
+        }
+        ArrayState *s = c->arr(a.array);
+        if (!s) return c->fail(GDAG_ERR_INVALID, "%s argument %d: unknown array %d", e.name.c_str(), i, a.array);
+        la.ptr[i] = s->dev;
+        la.bytes[i] = s->bytes;
+        int mode = a.mode == GDAG_MODE_SIGNATURE ? e.spec[i].mode : a.mode;
+        if (mode < GDAG_MODE_DEFAULT || mode > GDAG_MODE_INOUT)
+            return c->fail(GDAG_ERR_INVALID, "%s argument %d: bad mode %d", e.name.c_str(), i, mode);
+        int bits = gdag::mode_bits(mode);
+        int j = 0;
+        while (j < *nacc && acc[j].array != a.array) ++j;
+        if (j == *nacc) acc[(*nacc)++] = Access{a.array, bits};
+        else acc[j].bits |= bits;  // the same array twice: write dominates
+    }
+    bool autocfg = grid.x == 0 && grid.y == 0 && grid.z == 0;
+    if (autocfg && !e.launcher)
+        return c->fail(GDAG_ERR_INVALID, "%s: user kernels need an explicit grid", e.name.c_str());
+    if (!autocfg && (grid.x == 0 || grid.y == 0 || grid.z == 0 || block.x == 0 || block.y == 0 || block.z == 0))
+        return c->fail(GDAG_ERR_INVALID, "%s: zero grid or block dimension", e.name.c_str());
+    la.auto_cfg = autocfg;
+    la.grid[0] = grid.x; la.grid[1] = grid.y; la.grid[2] = grid.z;
+    la.block[0] = block.x; la.block[1] = block.y; la.block[2] = block.z;
+    la.smem = smem;
+    if (e.validate) {
+        const char *msg = e.validate(la);
+        if (msg) return c->fail(GDAG_ERR_INVALID, "%s: %s", e.name.c_str(), msg);
+    }
+    return GDAG_OK;
+}
+
+int gdag_launch(gdag_ctx *c, gdag_kernel k, gdag_dim3 grid, gdag_dim3 block, size_t smem, const gdag_arg *args,
+                int32_t nargs, int64_t *node_out)
+{
+    if (!c) return GDAG_ERR_INVALID;
+    int r = c->guard();
+    if (r) return r;
+    LaunchArgs la;
+    Access acc[gdag::kMaxArgs];
+    int nacc;
+    r = resolve(c, k, grid, block, smem, args, nargs, la, acc, &nacc);
+    if (r) return r;
+    int64_t id = c->next_id();
+    c->infer(id, acc, nacc);
+    for (int i = 0; i < nacc; ++i)
+        if (acc[i].bits & gdag::W_BIT) c->arrays[(size_t)acc[i].array].host_valid = false;
+    c->push_node(GDAG_NODE_KERNEL);
+    if (node_out) *node_out = id;
+    int32_t s;
+    r = c->place(id, &s);
+    if (r) {
+        c->retire(id);
+        return r;
+    }
+    c->log_op(GDAG_OP_LAUNCH, s, -1, id);
+    ++c->st.launches;
+    r = c->be->launch(c->kernels[(size_t)k], la, c->streams[(size_t)s].handle);
+    if (r) return c->abort_node(id, r, "launch");
+    return c->finish(id, s);
+}
+
+int gdag_launch_raw(gdag_ctx *c, gdag_kernel k, gdag_dim3 grid, gdag_dim3 block, size_t smem, const gdag_arg *args,
+                    int32_t nargs, void *stream)
+{
+    if (!c) return GDAG_ERR_INVALID;
+    int r = c->guard();
+    if (r) return r;
+    LaunchArgs la;
+    Access acc[gdag::kMaxArgs];
+    int nacc;
+    r = resolve(c, k, grid, block, smem, args, nargs, la, acc, &nacc);
+    if (r) return r;
+    ++c->st.launches;
+    r = c->be->launch(c->kernels[(size_t)k], la, stream);
+    if (r) return c->be_fail(r, "raw launch");
+    return GDAG_OK;
+}
+
+int gdag_launch_external(gdag_ctx *c, void (*fn)(void *, void *), void *user, const gdag_array *arrays,
+                         const int32_t *modes, int32_t n, int64_t *node_out)
+{
+    if (!c || !fn || n < 0 || n > gdag::kMaxArgs || (n && (!arrays || !modes))) return GDAG_ERR_INVALID;
+    int r = c->guard();
+    if (r) return r;
+    Access acc[gdag::kMaxArgs];
+    int nacc = 0;
+    for (int i = 0; i < n; ++i) {
+        if (!c->arr(arrays[i])) return c->fail(GDAG_ERR_INVALID, "unknown array %d", arrays[i]);
+        if (modes[i] < GDAG_MODE_DEFAULT || modes[i] > GDAG_MODE_INOUT)
+            return c->fail(GDAG_ERR_INVALID, "bad mode %d", modes[i]);
+        int bits = gdag::mode_bits(modes[i]);
+        int j = 0;
+        while (j < nacc && acc[j].array != arrays[i]) ++j;
+        if (j == nacc) acc[nacc++] = Access{arrays[i], bits};
+        else acc[j].bits |= bits;
+    }
+    int64_t id = c->next_id();
+    c->infer(id, acc, nacc);
+    for (int i = 0; i < nacc; ++i)
+        if (acc[i].bits & gdag::W_BIT) c->arrays[(size_t)acc[i].array].host_valid = false;
+    c->push_node(GDAG_NODE_EXTERNAL);
+    if (node_out) *node_out = id;
+    int32_t s;
+    r = c->place(id, &s);
+    if (r) {
+        c->retire(id);
+        return r;
+    }
+    c->log_op(GDAG_OP_EXTERNAL, s, -1, id);
+    r = c->be->external(fn, user, c->streams[(size_t)s].handle);
+    if (r) return c->abort_node(id, r, "external call");
+    return c->finish(id, s);
+}
+
+int gdag_array_host(gdag_ctx *c, gdag_array a, int32_t mode, void **out)
+{
+    if (!c || !out) return GDAG_ERR_INVALID;
+    int r = c->guard();
+    if (r) return r;
+    ArrayState *s = c->arr(a);
+    if (!s) return c->fail(GDAG_ERR_INVALID, "unknown array %d", a);
+    r = c->ensure_host(*s);
+    if (r) return r;
+    if (mode == GDAG_MODE_IN) {
+        r = gdag_array_read(c, a, nullptr, 0, s->bytes);
+        if (r) return r;
+    } else if (mode == GDAG_MODE_OUT) {
+        r = c->release_view(*s);
+        if (r) return r;
+    } else {
+        return c->fail(GDAG_ERR_INVALID, "mode must be GDAG_MODE_IN or GDAG_MODE_OUT");
+    }
+    *out = s->host;
+    return GDAG_OK;
+}
+
+int gdag_array_write(gdag_ctx *c, gdag_array a, const void *src, size_t off, size_t bytes)
+{
+    if (!c) return GDAG_ERR_INVALID;
+    int r = c->guard();
+    if (r) return r;
+    ArrayState *s = c->arr(a);
+    if (!s) return c->fail(GDAG_ERR_INVALID, "unknown array %d", a);
+    if (off > s->bytes || bytes > s->bytes - off)
+        return c->fail(GDAG_ERR_INVALID, "write of [%zu, %zu) outside %zu bytes", off, off + bytes, s->bytes);
+    r = c->ensure_host(*s);
+    if (r) return r;
+    char *view = static_cast<char *>(s->host) + off;
+    if (src && src != view) {
+        r = c->release_view(*s);
+        if (r) return r;
+        std::memcpy(view, src, bytes);
+    }
+    Access acc{a, gdag::W_BIT};
+    int64_t id = c->next_id();
+    c->infer(id, &acc, 1);
+    bool full = off == 0 && bytes == s->bytes;
+    s->host_valid = s->host_valid || full;
+    c->push_node(GDAG_NODE_HOST_WRITE);
+    int32_t st;
+    r = c->place(id, &st);
+    if (r) {
+        c->retire(id);
+        return r;
+    }
+    c->log_op(GDAG_OP_COPY_H2D, st, -1, id);
+    ++c->st.copies;
+    r = c->be->copy_h2d(static_cast<char *>(s->dev) + off, view, bytes, c->streams[(size_t)st].handle);
+    if (r) return c->abort_node(id, r, "host-to-device copy");
+    s->host_copy = id;
+    r = c->finish(id, st);
+    if (r) return r;
+    if (!c->opt.prefetch) return c->host_wait(id);
+    return GDAG_OK;
+}
+
+int gdag_array_read(gdag_ctx *c, gdag_array a, void *dst, size_t off, size_t bytes)
+{
+    if (!c) return GDAG_ERR_INVALID;
+    int r = c->guard();
+    if (r) return r;
+    ArrayState *s = c->arr(a);
+    if (!s) return c->fail(GDAG_ERR_INVALID, "unknown array %d", a);
+    if (off > s->bytes || bytes > s->bytes - off)
+        return c->fail(GDAG_ERR_INVALID, "read of [%zu, %zu) outside %zu bytes", off, off + bytes, s->bytes);
+    r = c->ensure_host(*s);
+    if (r) return r;
+    char *view = static_cast<char *>(s->host) + off;
+    Access acc{a, gdag::R_BIT};
+    int64_t id = c->next_id();
+    c->infer(id, &acc, 1);
+    c->push_node(GDAG_NODE_HOST_READ);
+    if (!s->host_valid) {
+        int32_t st;
+        r = c->place(id, &st);
+        if (r) {
+            c->retire(id);
+            return r;
+        }
+        c->log_op(GDAG_OP_COPY_D2H, st, -1, id);
+        ++c->st.copies;
+        r = c->be->copy_d2h(view, static_cast<char *>(s->dev) + off, bytes, c->streams[(size_t)st].handle);
+        if (r) return c->abort_node(id, r, "device-to-host copy");
+        r = c->finish(id, st);
+        if (r) return r;
+        r = c->host_wait(id);
+        if (r) return r;
+        if (off == 0 && bytes == s->bytes) s->host_valid = true;
+    } else {
+        // the view already holds the data: a host-only element
+        c->log_op(GDAG_OP_HOST_NODE, -1, -1, id);
+    }
+    if (dst && dst != view) std::memcpy(dst, view, bytes);
+    return GDAG_OK;
+}
+
+int gdag_sync(gdag_ctx *c)
+{
+    if (!c) return GDAG_ERR_INVALID;
+    int r = c->guard();
+    if (r) return r;
+    for (size_t s = 0; s < c->streams.size(); ++s) {
+        if (c->streams[s].active == 0) continue;
+        c->log_op(GDAG_OP_STREAM_SYNC, (int)s, -1, -1);
+        ++c->st.host_waits;
+        r = c->poll_stream((int32_t)s);
+        if (r) return r;
+    }
+    c->retire_all();
+    if (!c->opt.record_log && !c->opt.trace) {
+        // nothing can refer to retired nodes any more: drop them
+        c->base = c->next_id();
+        c->nodes.clear();
+        c->parent_arena.clear();
+        for (auto &a : c->arrays) {
+            a.writer = -1;
+            a.readers.clear();
+            a.host_copy = -1;
+        }
+        for (auto &s : c->streams) s.tail = -1;
+    }
+    return GDAG_OK;
+}
+
+int gdag_stream_wait_all(gdag_ctx *c, void *stream)
+{
+    if (!c) return GDAG_ERR_INVALID;
+    int r = c->guard();
+    if (r) return r;
+    for (size_t s = 0; s < c->streams.size(); ++s) {
+        gdag::Node *n = c->node(c->streams[s].tail);
+        if (!n || !n->active || n->event < 0) continue;
+        r = c->be->stream_wait(stream, c->events[(size_t)n->event]);
+        if (r) return c->be_fail(r, "stream wait");
+    }
+    return GDAG_OK;
+}
+
+int gdag_stream_fork(gdag_ctx *c, void *stream)
+{
+    if (!c) return GDAG_ERR_INVALID;
+    int r = c->guard();
+    if (r) return r;
+    if (c->streams.empty()) return GDAG_OK;
+    void *e;
+    r = c->be->event_create(&e, false);
+    if (r) return c->be_fail(r, "event create");
+    r = c->be->event_record(e, stream);
+    for (size_t s = 0; !r && s < c->streams.size(); ++s) r = c->be->stream_wait(c->streams[s].handle, e);
+    c->be->event_destroy(e);
+    if (r) return c->be_fail(r, "fork");
+    return GDAG_OK;
+}
+
+int gdag_dag_export(gdag_ctx *c, gdag_edge *buf, size_t cap, size_t *n) { return export_vec(c, c->edge_log, buf, cap, n); }
+int gdag_nodes_export(gdag_ctx *c, gdag_node_info *buf, size_t cap, size_t *n)
+{
+    return export_vec(c, c->node_log, buf, cap, n);
+}
+int gdag_ops_export(gdag_ctx *c, gdag_op *buf, size_t cap, size_t *n) { return export_vec(c, c->op_log, buf, cap, n); }
+
+int gdag_trace_export(gdag_ctx *c, gdag_trace_rec *buf, size_t cap, size_t *n)
+{
+    if (!c || !n) return GDAG_ERR_INVALID;
+    if (!c->opt.trace) return c->fail(GDAG_ERR_INVALID, "tracing needs options.trace = 1");
+    int r = c->guard();
+    if (r) return r;
+    for (size_t s = 0; s < c->streams.size(); ++s) {
+        r = c->poll_stream((int32_t)s);
+        if (r) return r;
+    }
+    size_t k = 0;
+    for (size_t i = 0; i < c->nodes.size(); ++i) {
+        const gdag::Node &nd = c->nodes[i];
+        if (nd.tev0 < 0 || nd.tev1 < 0) continue;
+        if (buf && k < cap) {
+            float a = 0.f, b = 0.f;
+            r = c->be->event_elapsed_ms(c->t0, c->tevents[(size_t)nd.tev0], &a);
+            if (!r) r = c->be->event_elapsed_ms(c->t0, c->tevents[(size_t)nd.tev1], &b);
+            if (r) return c->be_fail(r, "elapsed time");
+            buf[k] = gdag_trace_rec{c->base + (int64_t)i, nd.kind, nd.stream, (double)a, (double)b};
+        }
+        ++k;
+    }
+    *n = k;
+    return GDAG_OK;
+}
+
+int gdag_stats_get(gdag_ctx *c, gdag_stats *out)
+{
+    if (!c || !out) return GDAG_ERR_INVALID;
+    *out = c->st;
+    out->streams = (int32_t)c->streams.size();
+    out->active = (int32_t)c->active_count;
+    return GDAG_OK;
+}
+
+size_t gdag_scratch_bytes(const char *kernel, int64_t n) { return kernel ? gdag::scratch_bytes(kernel, n) : 0; }
+
+}  // extern "C"

@@ -1,0 +1,490 @@
+"""ctypes binding of libgdag (include/gdag.h): the same calls, argument
+marshalling only.  Every step of the hot path runs in the library's C++ runtime
+and CUDA kernels; nothing here computes.
+
+Module-level functions carry the C names and raise :class:`GdagError` on a
+negative status.  :class:`Context` is a thin convenience layer over them that
+accepts torch tensors (device memory) and Python scalars.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import struct
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libgdag.so")
+
+# ---------------------------------------------------------------- constants
+GDAG_OK = 0
+GDAG_ERR_INVALID = -1
+GDAG_ERR_CUDA = -2
+GDAG_ERR_TIMEOUT = -3
+GDAG_ERR_OOM = -4
+GDAG_ERR_POISONED = -5
+GDAG_ERR_BUSY = -6
+GDAG_ERR_NOT_FOUND = -7
+ERR_NAMES = {0: "OK", -1: "INVALID", -2: "CUDA", -3: "TIMEOUT", -4: "OOM", -5: "POISONED",
+             -6: "BUSY", -7: "NOT_FOUND"}
+
+GDAG_POLICY_SERIAL_SYNC = 0
+GDAG_POLICY_SERIAL_ASYNC = 1
+GDAG_POLICY_PARALLEL = 2
+GDAG_BACKEND_CUDA = 0
+GDAG_BACKEND_FAKE = 1
+
+GDAG_MODE_DEFAULT = 0
+GDAG_MODE_IN = 1
+GDAG_MODE_CONST = 2
+GDAG_MODE_OUT = 3
+GDAG_MODE_INOUT = 4
+GDAG_MODE_SIGNATURE = -1
+
+GDAG_EDGE_RAW, GDAG_EDGE_WAR, GDAG_EDGE_WAW = 0, 1, 2
+GDAG_NODE_KERNEL, GDAG_NODE_HOST_WRITE, GDAG_NODE_HOST_READ, GDAG_NODE_EXTERNAL = 0, 1, 2, 3
+GDAG_ARG_ARRAY, GDAG_ARG_SCALAR = 0, 1
+(GDAG_OP_LAUNCH, GDAG_OP_COPY_H2D, GDAG_OP_COPY_D2H, GDAG_OP_EXTERNAL, GDAG_OP_RECORD, GDAG_OP_WAIT,
+ GDAG_OP_HOST_WAIT, GDAG_OP_STREAM_SYNC, GDAG_OP_HOST_NODE, GDAG_OP_QUERY_DONE) = range(10)
+
+
+# ---------------------------------------------------------------- structs
+class gdag_dim3(ctypes.Structure):
+    _fields_ = [("x", ctypes.c_uint32), ("y", ctypes.c_uint32), ("z", ctypes.c_uint32)]
+
+
+class gdag_options(ctypes.Structure):
+    _fields_ = [("policy", ctypes.c_int32), ("backend", ctypes.c_int32), ("device", ctypes.c_int32),
+                ("max_streams", ctypes.c_int32), ("prefetch", ctypes.c_int32),
+                ("retire_by_query", ctypes.c_int32), ("record_log", ctypes.c_int32),
+                ("trace", ctypes.c_int32), ("timeout_ms", ctypes.c_int32),
+                ("fake_complete", ctypes.c_int32), ("fake_fail_sticky", ctypes.c_int32),
+                ("fake_fail_op", ctypes.c_int64)]
+
+
+class gdag_arg(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("mode", ctypes.c_int32), ("array", ctypes.c_int32),
+                ("size", ctypes.c_int32), ("value", ctypes.c_uint64)]
+
+
+class gdag_argspec(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("mode", ctypes.c_int32), ("size", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+class gdag_edge(ctypes.Structure):
+    _fields_ = [("src", ctypes.c_int64), ("dst", ctypes.c_int64), ("array", ctypes.c_int32),
+                ("kind", ctypes.c_int32)]
+
+
+class gdag_node_info(ctypes.Structure):
+    _fields_ = [("id", ctypes.c_int64), ("kind", ctypes.c_int32), ("stream", ctypes.c_int32)]
+
+
+class gdag_op(ctypes.Structure):
+    _fields_ = [("type", ctypes.c_int32), ("stream", ctypes.c_int32), ("event", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("node", ctypes.c_int64)]
+
+
+class gdag_trace_rec(ctypes.Structure):
+    _fields_ = [("node", ctypes.c_int64), ("kind", ctypes.c_int32), ("stream", ctypes.c_int32),
+                ("start_ms", ctypes.c_double), ("end_ms", ctypes.c_double)]
+
+
+class gdag_stats(ctypes.Structure):
+    _fields_ = [("nodes", ctypes.c_int64), ("edges", ctypes.c_int64), ("waits", ctypes.c_int64),
+                ("launches", ctypes.c_int64), ("copies", ctypes.c_int64), ("host_waits", ctypes.c_int64),
+                ("streams", ctypes.c_int32), ("active", ctypes.c_int32)]
+
+
+EXTERNAL_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
+
+_P = ctypes.POINTER
+_vp = ctypes.c_void_p
+_sz = ctypes.c_size_t
+_i32 = ctypes.c_int32
+_i64 = ctypes.c_int64
+_ctx = ctypes.c_void_p
+
+# name -> (restype, argtypes)
+SIGNATURES = {
+    "gdag_options_default": (None, [_P(gdag_options)]),
+    "gdag_create": (ctypes.c_int, [_P(_ctx), _P(gdag_options)]),
+    "gdag_destroy": (ctypes.c_int, [_ctx]),
+    "gdag_last_error": (ctypes.c_char_p, [_ctx]),
+    "gdag_add_stream": (ctypes.c_int, [_ctx, _vp]),
+    "gdag_array_register": (ctypes.c_int, [_ctx, _vp, _sz, _vp, _P(_i32)]),
+    "gdag_array_unregister": (ctypes.c_int, [_ctx, _i32]),
+    "gdag_array_host": (ctypes.c_int, [_ctx, _i32, _i32, _P(_vp)]),
+    "gdag_array_write": (ctypes.c_int, [_ctx, _i32, _vp, _sz, _sz]),
+    "gdag_array_read": (ctypes.c_int, [_ctx, _i32, _vp, _sz, _sz]),
+    "gdag_kernel_lookup": (ctypes.c_int, [_ctx, ctypes.c_char_p, _P(_i32)]),
+    "gdag_kernel_signature": (ctypes.c_int, [_ctx, _i32, _P(_i32), _P(gdag_argspec), _i32]),
+    "gdag_kernel_register": (ctypes.c_int, [_ctx, ctypes.c_char_p, _vp, _i32, _P(gdag_argspec), _P(_i32)]),
+    "gdag_launch": (ctypes.c_int, [_ctx, _i32, gdag_dim3, gdag_dim3, _sz, _P(gdag_arg), _i32, _P(_i64)]),
+    "gdag_launch_raw": (ctypes.c_int, [_ctx, _i32, gdag_dim3, gdag_dim3, _sz, _P(gdag_arg), _i32, _vp]),
+    "gdag_launch_external": (ctypes.c_int, [_ctx, EXTERNAL_FN, _vp, _P(_i32), _P(_i32), _i32, _P(_i64)]),
+    "gdag_sync": (ctypes.c_int, [_ctx]),
+    "gdag_stream_wait_all": (ctypes.c_int, [_ctx, _vp]),
+    "gdag_stream_fork": (ctypes.c_int, [_ctx, _vp]),
+    "gdag_dag_export": (ctypes.c_int, [_ctx, _P(gdag_edge), _sz, _P(_sz)]),
+    "gdag_nodes_export": (ctypes.c_int, [_ctx, _P(gdag_node_info), _sz, _P(_sz)]),
+    "gdag_ops_export": (ctypes.c_int, [_ctx, _P(gdag_op), _sz, _P(_sz)]),
+    "gdag_trace_export": (ctypes.c_int, [_ctx, _P(gdag_trace_rec), _sz, _P(_sz)]),
+    "gdag_stats_get": (ctypes.c_int, [_ctx, _P(gdag_stats)]),
+    "gdag_scratch_bytes": (_sz, [ctypes.c_char_p, _i64]),
+}
+
+_lib = None
+
+
+class GdagError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("gdag error %d (%s): %s" % (code, ERR_NAMES.get(code, "?"), msg))
+        self.code = code
+
+
+def lib():
+    """Load libgdag.so (built in-tree by __graft_entry__.build()).  There is
+    no fallback: a missing library is an error."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError("libgdag.so not built (%s); run __graft_entry__.build()" % LIB_PATH)
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(ctx, code):
+    if code < 0:
+        msg = lib().gdag_last_error(ctx) if ctx else b""
+        raise GdagError(code, (msg or b"").decode(errors="replace"))
+    return code
+
+
+# ---------------------------------------------------------- C-named calls
+def gdag_options_default():
+    o = gdag_options()
+    lib().gdag_options_default(ctypes.byref(o))
+    return o
+
+
+def gdag_create(opts=None):
+    h = _ctx()
+    code = lib().gdag_create(ctypes.byref(h), ctypes.byref(opts) if opts is not None else None)
+    if code < 0:
+        raise GdagError(code, "gdag_create failed")
+    return h
+
+
+def gdag_destroy(ctx):
+    return _check(None, lib().gdag_destroy(ctx))
+
+
+def gdag_add_stream(ctx, stream):
+    return _check(ctx, lib().gdag_add_stream(ctx, stream))
+
+
+def gdag_array_register(ctx, dev, nbytes, host=None):
+    a = _i32()
+    _check(ctx, lib().gdag_array_register(ctx, dev, nbytes, host, ctypes.byref(a)))
+    return a.value
+
+
+def gdag_array_unregister(ctx, a):
+    return _check(ctx, lib().gdag_array_unregister(ctx, a))
+
+
+def gdag_array_host(ctx, a, mode):
+    p = _vp()
+    _check(ctx, lib().gdag_array_host(ctx, a, mode, ctypes.byref(p)))
+    return p.value
+
+
+def gdag_array_write(ctx, a, src, off, nbytes):
+    return _check(ctx, lib().gdag_array_write(ctx, a, src, off, nbytes))
+
+
+def gdag_array_read(ctx, a, dst, off, nbytes):
+    return _check(ctx, lib().gdag_array_read(ctx, a, dst, off, nbytes))
+
+
+def gdag_kernel_lookup(ctx, name):
+    k = _i32()
+    _check(ctx, lib().gdag_kernel_lookup(ctx, name.encode(), ctypes.byref(k)))
+    return k.value
+
+
+def gdag_kernel_signature(ctx, k):
+    n = _i32()
+    spec = (gdag_argspec * 16)()
+    _check(ctx, lib().gdag_kernel_signature(ctx, k, ctypes.byref(n), spec, 16))
+    return [spec[i] for i in range(n.value)]
+
+
+def gdag_kernel_register(ctx, name, fn, specs):
+    k = _i32()
+    arr = (gdag_argspec * max(1, len(specs)))(*specs)
+    _check(ctx, lib().gdag_kernel_register(ctx, name.encode(), fn, len(specs), arr, ctypes.byref(k)))
+    return k.value
+
+
+def gdag_launch(ctx, k, grid, block, smem, args):
+    node = _i64()
+    arr = (gdag_arg * max(1, len(args)))(*args)
+    _check(ctx, lib().gdag_launch(ctx, k, grid, block, smem, arr, len(args), ctypes.byref(node)))
+    return node.value
+
+
+def gdag_launch_raw(ctx, k, grid, block, smem, args, stream):
+    arr = (gdag_arg * max(1, len(args)))(*args)
+    return _check(ctx, lib().gdag_launch_raw(ctx, k, grid, block, smem, arr, len(args), stream))
+
+
+def gdag_launch_external(ctx, fn, user, arrays, modes):
+    node = _i64()
+    n = len(arrays)
+    a = (_i32 * max(1, n))(*arrays)
+    m = (_i32 * max(1, n))(*modes)
+    _check(ctx, lib().gdag_launch_external(ctx, fn, user, a, m, n, ctypes.byref(node)))
+    return node.value
+
+
+def gdag_sync(ctx):
+    return _check(ctx, lib().gdag_sync(ctx))
+
+
+def gdag_stream_wait_all(ctx, stream):
+    return _check(ctx, lib().gdag_stream_wait_all(ctx, stream))
+
+
+def gdag_stream_fork(ctx, stream):
+    return _check(ctx, lib().gdag_stream_fork(ctx, stream))
+
+
+def _export(ctx, fn, T):
+    n = _sz()
+    _check(ctx, fn(ctx, None, 0, ctypes.byref(n)))
+    buf = (T * max(1, n.value))()
+    _check(ctx, fn(ctx, buf, n.value, ctypes.byref(n)))
+    return [buf[i] for i in range(n.value)]
+
+
+def gdag_dag_export(ctx):
+    return _export(ctx, lib().gdag_dag_export, gdag_edge)
+
+
+def gdag_nodes_export(ctx):
+    return _export(ctx, lib().gdag_nodes_export, gdag_node_info)
+
+
+def gdag_ops_export(ctx):
+    return _export(ctx, lib().gdag_ops_export, gdag_op)
+
+
+def gdag_trace_export(ctx):
+    return _export(ctx, lib().gdag_trace_export, gdag_trace_rec)
+
+
+def gdag_stats_get(ctx):
+    s = gdag_stats()
+    _check(ctx, lib().gdag_stats_get(ctx, ctypes.byref(s)))
+    return s
+
+
+def gdag_scratch_bytes(kernel, n):
+    return lib().gdag_scratch_bytes(kernel.encode(), n)
+
+
+# ------------------------------------------------------------ convenience
+def array_arg(a, mode=GDAG_MODE_SIGNATURE):
+    return gdag_arg(GDAG_ARG_ARRAY, mode, a, 0, 0)
+
+
+def scalar_arg(value, size):
+    if isinstance(value, float):
+        bits = struct.unpack("<I", struct.pack("<f", value))[0] if size == 4 else \
+            struct.unpack("<Q", struct.pack("<d", value))[0]
+    else:
+        bits = int(value) & ((1 << (8 * size)) - 1)
+    return gdag_arg(GDAG_ARG_SCALAR, 0, 0, size, bits)
+
+
+class Array:
+    """A registered array: a handle plus what it was registered with."""
+
+    __slots__ = ("handle", "nbytes", "tensor", "host", "name")
+
+    def __init__(self, handle, nbytes, tensor=None, host=None, name=None):
+        self.handle, self.nbytes, self.tensor, self.host, self.name = handle, nbytes, tensor, host, name
+
+    def __repr__(self):
+        return "Array(%d, %s, %d B)" % (self.handle, self.name, self.nbytes)
+
+
+class Mode:
+    """Per-call access-mode override: ``ctx.launch(k, Mode(a, GDAG_MODE_IN), ...)``."""
+
+    __slots__ = ("array", "mode")
+
+    def __init__(self, array, mode):
+        self.array, self.mode = array, mode
+
+
+class Context:
+    """One gdag context.  ``backend='fake'`` records operations only."""
+
+    def __init__(self, policy=GDAG_POLICY_PARALLEL, backend="cuda", device=0, max_streams=16, prefetch=True,
+                 retire_by_query=False, record_log=False, trace=False, timeout_ms=60000,
+                 fake_complete=False, fake_fail_op=-1, fake_fail_sticky=False):
+        o = gdag_options_default()
+        o.policy = policy
+        o.backend = GDAG_BACKEND_FAKE if backend == "fake" else GDAG_BACKEND_CUDA
+        o.device = device
+        o.max_streams = max_streams
+        o.prefetch = int(prefetch)
+        o.retire_by_query = int(retire_by_query)
+        o.record_log = int(record_log)
+        o.trace = int(trace)
+        o.timeout_ms = timeout_ms
+        o.fake_complete = int(fake_complete)
+        o.fake_fail_op = fake_fail_op
+        o.fake_fail_sticky = int(fake_fail_sticky)
+        self.options = o
+        self.h = gdag_create(o)
+        self._kernels = {}
+        self._keep = []
+
+    # lifetime
+    def close(self):
+        if self.h:
+            h, self.h = self.h, None
+            gdag_destroy(h)
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def last_error(self):
+        return (lib().gdag_last_error(self.h) or b"").decode()
+
+    # arrays
+    def array(self, tensor=None, *, dev=None, nbytes=None, host=None, name=None):
+        """Register a torch tensor (device memory) or a raw (dev, nbytes)."""
+        if tensor is not None:
+            dev = tensor.data_ptr()
+            nbytes = tensor.numel() * tensor.element_size()
+        hptr = host.data_ptr() if host is not None and hasattr(host, "data_ptr") else host
+        h = gdag_array_register(self.h, dev, nbytes, hptr)
+        return Array(h, nbytes, tensor, host, name)
+
+    def unregister(self, a):
+        gdag_array_unregister(self.h, a.handle)
+
+    def host_view(self, a, mode):
+        return gdag_array_host(self.h, a.handle, mode)
+
+    def write(self, a, src=None, off=0, nbytes=None):
+        """Host write; src is a host pointer (int), a numpy array or None."""
+        nbytes = a.nbytes - off if nbytes is None else nbytes
+        ptr = _host_ptr(src)
+        gdag_array_write(self.h, a.handle, ptr, off, nbytes)
+
+    def read(self, a, dst=None, off=0, nbytes=None):
+        nbytes = a.nbytes - off if nbytes is None else nbytes
+        gdag_array_read(self.h, a.handle, _host_ptr(dst), off, nbytes)
+
+    # kernels
+    def kernel(self, name):
+        k = self._kernels.get(name)
+        if k is None:
+            kid = gdag_kernel_lookup(self.h, name)
+            k = (kid, gdag_kernel_signature(self.h, kid))
+            self._kernels[name] = k
+        return k
+
+    def _args(self, name, args):
+        kid, spec = self.kernel(name)
+        if len(args) != len(spec):
+            raise GdagError(GDAG_ERR_INVALID, "%s takes %d arguments, got %d" % (name, len(spec), len(args)))
+        out = []
+        for s, v in zip(spec, args):
+            if s.kind == GDAG_ARG_ARRAY:
+                if isinstance(v, Mode):
+                    out.append(array_arg(v.array.handle, v.mode))
+                else:
+                    out.append(array_arg(v.handle))
+            else:
+                out.append(scalar_arg(v, s.size))
+        return kid, out
+
+    def launch(self, name, *args, grid=None, block=None, smem=0):
+        kid, a = self._args(name, args)
+        g = gdag_dim3(*grid) if grid else gdag_dim3(0, 0, 0)
+        b = gdag_dim3(*block) if block else gdag_dim3(0, 0, 0)
+        return gdag_launch(self.h, kid, g, b, smem, a)
+
+    def launch_raw(self, name, *args, stream, grid=None, block=None, smem=0):
+        kid, a = self._args(name, args)
+        g = gdag_dim3(*grid) if grid else gdag_dim3(0, 0, 0)
+        b = gdag_dim3(*block) if block else gdag_dim3(0, 0, 0)
+        gdag_launch_raw(self.h, kid, g, b, smem, a, stream)
+
+    def external(self, fn, arrays_modes, user=None):
+        cb = EXTERNAL_FN(fn)
+        self._keep.append(cb)
+        return gdag_launch_external(self.h, cb, user, [a.handle for a, _ in arrays_modes],
+                                    [m for _, m in arrays_modes])
+
+    # sync and inspection
+    def sync(self):
+        gdag_sync(self.h)
+
+    def wait_all(self, stream):
+        gdag_stream_wait_all(self.h, stream)
+
+    def fork(self, stream):
+        gdag_stream_fork(self.h, stream)
+
+    def edges(self):
+        return [(e.src, e.dst, e.array, e.kind) for e in gdag_dag_export(self.h)]
+
+    def nodes(self):
+        return [(n.id, n.kind, n.stream) for n in gdag_nodes_export(self.h)]
+
+    def ops(self):
+        return [(o.type, o.stream, o.event, o.node) for o in gdag_ops_export(self.h)]
+
+    def trace(self):
+        return [(t.node, t.kind, t.stream, t.start_ms, t.end_ms) for t in gdag_trace_export(self.h)]
+
+    def stats(self):
+        s = gdag_stats_get(self.h)
+        return {f: getattr(s, f) for f, _ in gdag_stats._fields_}
+
+
+def _host_ptr(x):
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "ctypes"):  # numpy
+        if not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("host buffer must be contiguous")
+        return x.ctypes.data
+    if hasattr(x, "data_ptr"):  # torch CPU tensor
+        return x.data_ptr()
+    raise TypeError("unsupported host buffer %r" % type(x))

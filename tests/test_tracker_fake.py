@@ -1,0 +1,259 @@
+"""The C++ dependency tracker and stream manager, driven through the C ABI with
+the recording fake backend (no GPU), against the brute-force oracle.  CPU
+only."""
+import random
+
+import pytest
+
+from oracle import dag as D
+from paper_2012_09646_gb300 import gdag as G
+from tests.test_oracle_dag import CASES, load_cases
+
+MODE_OF = {D.R: G.GDAG_MODE_IN, D.W: G.GDAG_MODE_OUT, D.RW: G.GDAG_MODE_INOUT}
+SPEC = G.gdag_argspec(G.GDAG_ARG_ARRAY, G.GDAG_MODE_DEFAULT, 0, 0)
+
+
+class Program:
+    """Feeds a list of oracle elements to a fake-backend context.
+
+    An element {array: mode} becomes a kernel launch over its arrays with
+    per-argument mode overrides; ``("write", a)`` and ``("read", a)`` become
+    host writes and reads."""
+
+    def __init__(self, n_arrays, **opts):
+        opts.setdefault("record_log", True)
+        self.ctx = G.Context(backend="fake", **opts)
+        self.arrays = [self.ctx.array(dev=0x10000 * (i + 1), nbytes=64, name="a%d" % i) for i in range(n_arrays)]
+        self.kern = {}
+        for n in range(1, 9):
+            self.kern[n] = G.gdag_kernel_register(self.ctx.h, "k%d" % n, None, [SPEC] * n)
+        self.elems = []
+
+    def kernel(self, acc):
+        items = list(acc.items())
+        args = [G.array_arg(self.arrays[a].handle, MODE_OF[m]) for a, m in items]
+        node = G.gdag_launch(self.ctx.h, self.kern[len(items)], G.gdag_dim3(1, 1, 1), G.gdag_dim3(32, 1, 1), 0, args)
+        assert node == len(self.elems)
+        self.elems.append(dict(acc))
+        return node
+
+    def write(self, a):
+        self.ctx.write(self.arrays[a], None)
+        self.elems.append({a: D.W})
+
+    def read(self, a):
+        self.ctx.read(self.arrays[a])
+        self.elems.append({a: D.R})
+
+
+def edges_of(ctx, names=None):
+    return {(s, d, a, k) for s, d, a, k in ctx.edges()}
+
+
+def run_random(rng, L, n_arrays, **opts):
+    p = Program(n_arrays, **opts)
+    for _ in range(L):
+        r = rng.random()
+        if r < 0.12:
+            p.write(rng.randrange(n_arrays))
+        elif r < 0.22:
+            p.read(rng.randrange(n_arrays))
+        else:
+            k = rng.randint(1, min(4, n_arrays))
+            arrs = rng.sample(range(n_arrays), k)
+            p.kernel({a: rng.choice([D.R, D.R, D.W, D.RW]) for a in arrs})
+    return p
+
+
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_paper_cases_through_tracker(name):
+    case = CASES[name]
+    names = sorted({a for e in case["elems"] for a in e})
+    idx = {a: i for i, a in enumerate(names)}
+    p = Program(len(names))
+    for e in case["elems"]:
+        p.kernel({idx[a]: m for a, m in e.items()})
+    want = {(i, j, idx[a], k) for i, j, a, k in case["edges"]}
+    assert edges_of(p.ctx) == want
+
+
+@pytest.mark.parametrize("seed", range(40))
+def test_random_programs_match_brute_force(seed):
+    rng = random.Random(seed)
+    opts = rng.choice([{}, {"max_streams": 2}, {"retire_by_query": True, "fake_complete": True},
+                       {"policy": G.GDAG_POLICY_SERIAL_ASYNC}, {"policy": G.GDAG_POLICY_SERIAL_SYNC},
+                       {"max_streams": 1}])
+    p = run_random(rng, rng.randint(1, 40), rng.randint(1, 6), **opts)
+    want = D.expected_edges(p.elems)
+    got = edges_of(p.ctx)
+    assert got == want
+    ops = p.ctx.ops()
+    # every edge is ordered by CUDA's stream/event rules plus host waits
+    assert D.check_hb(ops, want) == []
+    # waits only along true edges, never for a same-stream parent
+    assert D.waits_off_edges(ops, want) == []
+    # node ids are consecutive in program order
+    assert [n[0] for n in p.ctx.nodes()] == list(range(len(p.elems)))
+
+
+def test_vec_schedule_one_cross_stream_event():
+    """Section III-A, VEC example: K1 and K2 on two streams, the join K3 on
+    K1's stream with exactly one event wait (on K2); reading z retires all."""
+    p = Program(3)
+    x, y, z = 0, 1, 2
+    k1 = p.kernel({x: D.RW})
+    k2 = p.kernel({y: D.RW})
+    k3 = p.kernel({x: D.R, y: D.R, z: D.W})
+    nodes = {n: s for n, _k, s in p.ctx.nodes()}
+    assert nodes[k1] != nodes[k2]
+    assert nodes[k3] == nodes[k1]
+    waits = [o for o in p.ctx.ops() if o[0] == G.GDAG_OP_WAIT]
+    assert len(waits) == 1 and waits[0][3] == k2 and waits[0][1] == nodes[k3]
+    p.read(z)
+    st = p.ctx.stats()
+    assert st["active"] == 0 and st["streams"] == 2
+
+
+def test_fifo_reuse_and_no_new_stream_when_one_is_empty():
+    p = Program(8)
+    for a in range(4):
+        p.kernel({a: D.W})
+    assert p.ctx.stats()["streams"] == 4
+    p.ctx.sync()
+    before = p.ctx.stats()["streams"]
+    used = []
+    for a in range(4, 8):
+        p.kernel({a: D.W})
+        used.append(p.ctx.nodes()[-1][2])
+    assert p.ctx.stats()["streams"] == before
+    assert used == [0, 1, 2, 3]  # oldest empty first
+
+
+def test_first_child_on_parent_stream_later_children_elsewhere():
+    p = Program(4)
+    k0 = p.kernel({0: D.W})
+    c1 = p.kernel({0: D.R, 1: D.W})
+    c2 = p.kernel({0: D.R, 2: D.W})
+    c3 = p.kernel({0: D.R, 3: D.W})
+    s = {n: st for n, _k, st in p.ctx.nodes()}
+    assert s[c1] == s[k0]
+    assert len({s[c1], s[c2], s[c3]}) == 3
+
+
+def test_stream_cap_falls_back_to_lru():
+    p = Program(6, max_streams=3)
+    for a in range(6):
+        p.kernel({a: D.W})
+    assert p.ctx.stats()["streams"] == 3
+    s = [st for _n, _k, st in p.ctx.nodes()]
+    assert s == [0, 1, 2, 0, 1, 2]
+
+
+def test_host_write_war_waits_on_gpu_not_host():
+    p = Program(2)
+    p.kernel({0: D.R, 1: D.W})  # active reader of array 0
+    p.write(0)                  # WAR: the copy waits on the GPU
+    ops = p.ctx.ops()
+    assert not any(o[0] in (G.GDAG_OP_HOST_WAIT, G.GDAG_OP_STREAM_SYNC) for o in ops)
+    assert (0, 1, 0, D.WAR) in edges_of(p.ctx)
+
+
+def test_serial_sync_waits_after_every_op():
+    p = Program(3, policy=G.GDAG_POLICY_SERIAL_SYNC)
+    p.kernel({0: D.W})
+    p.kernel({1: D.W})
+    p.kernel({0: D.R, 1: D.R, 2: D.W})
+    ops = p.ctx.ops()
+    work = [o for o in ops if o[0] == G.GDAG_OP_LAUNCH]
+    hw = [o for o in ops if o[0] == G.GDAG_OP_HOST_WAIT]
+    assert len(work) == 3 and len(hw) == 3
+    assert {o[1] for o in work} == {0}
+    assert p.ctx.stats()["active"] == 0
+
+
+def test_serial_async_one_stream_no_waits():
+    p = Program(3, policy=G.GDAG_POLICY_SERIAL_ASYNC)
+    p.kernel({0: D.W})
+    p.kernel({1: D.W})
+    p.kernel({0: D.R, 1: D.R, 2: D.W})
+    ops = p.ctx.ops()
+    assert not any(o[0] in (G.GDAG_OP_WAIT, G.GDAG_OP_HOST_WAIT) for o in ops)
+    assert p.ctx.stats()["streams"] == 1
+
+
+def test_retire_by_query_drops_waits_on_finished_parents():
+    p = Program(3, retire_by_query=True, fake_complete=True)
+    p.kernel({0: D.W})
+    p.kernel({1: D.W})
+    p.kernel({0: D.R, 1: D.R, 2: D.W})
+    assert not any(o[0] == G.GDAG_OP_WAIT for o in p.ctx.ops())
+    assert len(edges_of(p.ctx)) == 2  # the logical edges stay
+
+
+def test_validation_errors_leave_no_trace():
+    ctx = G.Context(backend="fake", record_log=True)
+    a = ctx.array(dev=0x1000, nbytes=400)
+    c = ctx.array(dev=0x2000, nbytes=400)
+    with pytest.raises(G.GdagError) as e:
+        ctx.launch("bs_call", a, c, 101, 60.0, 0.1, 0.2, 1.0)  # n > 100 floats
+    assert e.value.code == G.GDAG_ERR_INVALID
+    with pytest.raises(G.GdagError):
+        ctx.launch("bs_call", a, c, 100)  # wrong argument count
+    with pytest.raises(G.GdagError):
+        G.gdag_launch(ctx.h, ctx.kernel("bs_call")[0], G.gdag_dim3(0, 0, 0), G.gdag_dim3(0, 0, 0), 0,
+                      [G.array_arg(99), G.array_arg(c.handle)] + [G.scalar_arg(1, 8)] + [G.scalar_arg(1.0, 4)] * 4)
+    with pytest.raises(G.GdagError):
+        G.gdag_launch(ctx.h, ctx.kernel("bs_call")[0], G.gdag_dim3(0, 0, 0), G.gdag_dim3(0, 0, 0), 0,
+                      [G.array_arg(a.handle), G.array_arg(c.handle)] + [G.scalar_arg(1, 4)] + [G.scalar_arg(1.0, 4)] * 4)
+    with pytest.raises(G.GdagError):
+        ctx.write(a, None, off=396, nbytes=8)
+    with pytest.raises(G.GdagError):
+        ctx.read(a, None, off=401, nbytes=0)
+    with pytest.raises(G.GdagError) as e:
+        ctx.kernel("no_such_kernel")
+    assert e.value.code == G.GDAG_ERR_NOT_FOUND
+    assert ctx.nodes() == [] and ctx.edges() == []
+    ctx.launch("bs_call", a, c, 100, 60.0, 0.1, 0.2, 1.0)
+    assert len(ctx.nodes()) == 1
+
+
+def test_injected_failure_and_poisoning():
+    ctx = G.Context(backend="fake", fake_fail_op=0)
+    a = ctx.array(dev=0x1000, nbytes=400)
+    with pytest.raises(G.GdagError) as e:
+        ctx.launch("vec_square", a, 100)
+    assert e.value.code == G.GDAG_ERR_CUDA
+    ctx.launch("vec_square", a, 100)  # not sticky: the context goes on
+    ctx.close()
+    ctx = G.Context(backend="fake", fake_fail_op=1, fake_fail_sticky=True)
+    a = ctx.array(dev=0x1000, nbytes=400)
+    with pytest.raises(G.GdagError) as e:
+        ctx.launch("vec_square", a, 100)  # op 0 launch, op 1 event record
+    assert e.value.code == G.GDAG_ERR_POISONED
+    with pytest.raises(G.GdagError) as e:
+        ctx.launch("vec_square", a, 100)
+    assert e.value.code == G.GDAG_ERR_POISONED
+    ctx.close()
+
+
+def test_host_wait_times_out_instead_of_hanging():
+    ctx = G.Context(backend="fake", fake_complete=2, timeout_ms=50)
+    a = ctx.array(dev=0x1000, nbytes=400)
+    ctx.launch("vec_square", a, 100)
+    with pytest.raises(G.GdagError) as e:
+        ctx.read(a)
+    assert e.value.code == G.GDAG_ERR_TIMEOUT
+    with pytest.raises(G.GdagError) as e:
+        ctx.sync()
+    assert e.value.code == G.GDAG_ERR_TIMEOUT
+
+
+def test_external_call_gets_chosen_stream():
+    seen = []
+    ctx = G.Context(backend="fake", record_log=True)
+    a = ctx.array(dev=0x1000, nbytes=400)
+    b = ctx.array(dev=0x2000, nbytes=400)
+    ctx.launch("vec_square", a, 100)
+    node = ctx.external(lambda s, u: seen.append(s), [(a, G.GDAG_MODE_IN), (b, G.GDAG_MODE_OUT)])
+    # fake backend does not call the function; the edge is still inferred
+    assert (0, node, a.handle, G.GDAG_EDGE_RAW) in ctx.edges()
