@@ -327,6 +327,38 @@ int gdag_stats_get(gdag_ctx *ctx, gdag_stats *out);
  * before its first use and is left zeroed-counter by every launch. */
 size_t gdag_scratch_bytes(const char *kernel, int64_t n);
 
+/* ------------------------------------------------- allocation-free entry
+ * The paper has no counterpart to this call; it exists for callers that
+ * cannot allocate device memory: plug-ins whose host application owns every
+ * device allocation, processes whose device memory is budgeted by an
+ * allocator they must not bypass, and latency-critical loops that cannot
+ * afford cudaMalloc/cudaFree (which may synchronize the device).
+ *
+ * gdag_vec_reduce_diff_noalloc computes *dev_z = sum_i (dev_x[i] - dev_y[i])
+ * over n floats (the VEC reduction, same kernel and same result as launching
+ * "vec_reduce_diff" through gdag_launch) on the caller's CUDA stream, without
+ * a context and without allocating: the caller passes the inputs and the
+ * one-float output, and the kernel's scratch (per-block partial sums and an
+ * arrival counter) is a fixed file-scope device array of
+ * GDAG_NOALLOC_SCRATCH_BYTES that every GPU loading the library holds until
+ * the process exits.  No cudaMalloc, cudaFree or allocating library routine
+ * is called.
+ *   - The first call on a device (with that device current) looks up the
+ *     array's device address and zeroes it; make that first call before any
+ *     stream capture on the device.
+ *   - Every call shares the one array per device and leaves the last call's
+ *     partial sums in it; each call clears the counter it needs on its own
+ *     stream first.  Calls whose kernels overlap on the GPU (different
+ *     streams, or different host threads, without ordering) race on the
+ *     array: order them on one stream or with events.
+ *   - The array holds 1024 partial sums; a request that would need more
+ *     (a device with more than 512 multiprocessors), a negative n, or a NULL
+ *     pointer is rejected with GDAG_ERR_INVALID before anything is enqueued.
+ *   - Returns GDAG_ERR_CUDA if the set-up or the launch fails. */
+#define GDAG_NOALLOC_SCRATCH_BYTES 16384
+int gdag_vec_reduce_diff_noalloc(const void *dev_x, const void *dev_y,
+                                 void *dev_z, int64_t n, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

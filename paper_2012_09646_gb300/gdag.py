@@ -132,6 +132,7 @@ SIGNATURES = {
     "gdag_trace_export": (ctypes.c_int, [_ctx, _P(gdag_trace_rec), _sz, _P(_sz)]),
     "gdag_stats_get": (ctypes.c_int, [_ctx, _P(gdag_stats)]),
     "gdag_scratch_bytes": (_sz, [ctypes.c_char_p, _i64]),
+    "gdag_vec_reduce_diff_noalloc": (ctypes.c_int, [_vp, _vp, _vp, _i64, _vp]),
 }
 
 _lib = None
@@ -298,6 +299,11 @@ def gdag_stats_get(ctx):
 
 def gdag_scratch_bytes(kernel, n):
     return lib().gdag_scratch_bytes(kernel.encode(), n)
+
+
+def gdag_vec_reduce_diff_noalloc(dev_x, dev_y, dev_z, n, stream):
+    """The allocation-free VEC reduction (no context; caller's stream)."""
+    return _check(None, lib().gdag_vec_reduce_diff_noalloc(dev_x, dev_y, dev_z, n, stream))
 
 
 # ------------------------------------------------------------ convenience
