@@ -45,59 +45,80 @@ def parse():
 
 # ------------------------------------------------------------------ clocks
 class ClockSampler:
-    """nvidia-smi samples during the timed region (read-only queries)."""
+    """SM clock, power and clock-event reasons sampled every 100 ms on a
+    thread through NVML's read-only queries (nvidia-smi's output is block
+    buffered through a pipe).  Nothing is ever set."""
 
-    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
-              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
-              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    REASONS = {0x8: "hw_slowdown", 0x40: "hw_thermal_slowdown", 0x20: "sw_thermal_slowdown",
+               0x4: "sw_power_cap"}
 
-    def __init__(self, index):
-        self.index = index
-        self.proc = None
-        self.lines = []
+    def __init__(self, index, uuid=None):
+        self.index, self.uuid = index, uuid
+        self.samples = []
+        self.stop = threading.Event()
+        self.t = None
+        self.err = None
+
+    def _open(self):
+        import ctypes
+        nv = ctypes.CDLL("libnvidia-ml.so.1")
+        if nv.nvmlInit_v2() != 0:
+            raise OSError("nvmlInit failed")
+        h = ctypes.c_void_p()
+        ok = False
+        if self.uuid:
+            ok = nv.nvmlDeviceGetHandleByUUID(self.uuid.encode(), ctypes.byref(h)) == 0
+        if not ok and nv.nvmlDeviceGetHandleByIndex_v2(self.index, ctypes.byref(h)) != 0:
+            raise OSError("no NVML handle")
+        return nv, h
+
+    def _run(self):
+        import ctypes
+        try:
+            nv, h = self._open()
+        except OSError as e:
+            self.err = str(e)
+            return
+        clk, mx, pw, rs = ctypes.c_uint(), ctypes.c_uint(), ctypes.c_uint(), ctypes.c_ulonglong()
+        reasons_fn = getattr(nv, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            getattr(nv, "nvmlDeviceGetCurrentClocksThrottleReasons")
+        while not self.stop.is_set():
+            a = nv.nvmlDeviceGetClockInfo(h, 1, ctypes.byref(clk))      # NVML_CLOCK_SM
+            b = nv.nvmlDeviceGetMaxClockInfo(h, 1, ctypes.byref(mx))
+            c = nv.nvmlDeviceGetPowerUsage(h, ctypes.byref(pw))
+            d = reasons_fn(h, ctypes.byref(rs))
+            if a == 0 and b == 0:
+                self.samples.append((clk.value, mx.value, pw.value / 1e3 if c == 0 else None,
+                                     rs.value if d == 0 else 0))
+            self.stop.wait(0.1)
+        nv.nvmlShutdown()
 
     def __enter__(self):
-        try:
-            self.proc = subprocess.Popen(
-                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
-                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
-            self.t = threading.Thread(target=self._read, daemon=True)
-            self.t.start()
-        except OSError:
-            self.proc = None
+        self.t = threading.Thread(target=self._run, daemon=True)
+        self.t.start()
+        t_end = time.time() + 3.0
+        while not self.samples and self.err is None and time.time() < t_end:
+            time.sleep(0.01)
         return self
 
-    def _read(self):
-        for line in self.proc.stdout:
-            self.lines.append(line.strip())
-
     def __exit__(self, *exc):
-        if self.proc:
-            self.proc.terminate()
-            try:
-                self.proc.wait(timeout=5)
-            except subprocess.TimeoutExpired:
-                self.proc.kill()
+        self.stop.set()
+        if self.t:
+            self.t.join(timeout=2)
 
     def summary(self):
-        sm, mx, reasons = [], [], set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
-            p = [x.strip() for x in ln.split(",")]
-            if len(p) < 8:
-                continue
-            try:
-                sm.append(float(p[0]))
-                mx.append(float(p[1]))
-            except ValueError:
-                continue
-            for nm, v in zip(names, p[4:8]):
-                if v.lower().startswith("active"):
-                    reasons.add(nm)
-        if not sm:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
-        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
-                "samples": len(sm)}
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled: %s" % self.err], "samples": 0}
+        reasons = set()
+        for _c, _m, _p, r in self.samples:
+            for bit, name in self.REASONS.items():
+                if r & bit:
+                    reasons.add(name)
+        sm = [c for c, _m, _p, _r in self.samples]
+        pw = [p for _c, _m, p, _r in self.samples if p is not None]
+        return {"sm_mhz": statistics.median(sm), "sm_min_mhz": min(sm),
+                "sm_max_mhz": max(m for _c, m, _p, _r in self.samples), "reasons": sorted(reasons),
+                "power_w_max": max(pw) if pw else None, "samples": len(sm)}
 
 
 def measured_peaks():
@@ -207,21 +228,27 @@ def run_ours(args, rank, world, local_rank):
     def par_step():
         dag.step_resident()
 
+    # clocks are sampled from before the warm-up to the end of the GPU work
+    # (the timed region alone is shorter than nvidia-smi's sampling period)
+    try:
+        uuid = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:
+        uuid = None
+    clocks = ClockSampler(local_rank, uuid)
+    clocks.__enter__()
     for _ in range(args.warmup):
         par_step()
     ctx.sync()
     torch.cuda.synchronize()
     barrier()
-    clocks = ClockSampler(local_rank)
-    with clocks:
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(s0)
-        ctx.fork(s0.cuda_stream)
-        for _ in range(args.steps):
-            par_step()
-        ctx.wait_all(s0.cuda_stream)
-        e1.record(s0)
-        torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(s0)
+    ctx.fork(s0.cuda_stream)
+    for _ in range(args.steps):
+        par_step()
+    ctx.wait_all(s0.cuda_stream)
+    e1.record(s0)
+    torch.cuda.synchronize()
     ms_par = e0.elapsed_time(e1) / args.steps
     ctx.sync()
     barrier()
@@ -291,19 +318,22 @@ def run_ours(args, rank, world, local_rank):
         ms_graph = time_device(torch, g.replay, nsteps_other, torch.cuda.current_stream()) / nsteps_other
 
         # ---- solo node time (critical path: all nodes independent, so the
-        # longest path is one node) and the dominant kernel's roofline
-        solo = []
+        # longest path is one node) and the dominant kernel's roofline: the
+        # kernel alone on one stream, 20 launches back to back between two
+        # events (the queue stays full, so host launch latency is hidden)
         st = torch.cuda.Stream()
-        for i in range(3 + 2 * N_VEC):
-            a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a0.record(st)
+        for i in range(3):
+            ctx.launch_raw("bs_call", dag.SA[i], dag.CA[i], N_OPTS, K, r, sg, T, stream=st.cuda_stream)
+        torch.cuda.synchronize()
+        reps = 20
+        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a0.record(st)
+        for i in range(reps):
             ctx.launch_raw("bs_call", dag.SA[i % N_VEC], dag.CA[i % N_VEC], N_OPTS, K, r, sg, T,
                            stream=st.cuda_stream)
-            a1.record(st)
-            torch.cuda.synchronize()
-            if i >= 3:
-                solo.append(a0.elapsed_time(a1))
-        ms_solo = statistics.median(solo)
+        a1.record(st)
+        torch.cuda.synchronize()
+        ms_solo = a0.elapsed_time(a1) / reps
         peaks, peak_src = measured_peaks()
         hbm = float(peaks.get("hbm_gbs", 6800.0))
         bytes_launch = BYTES_PER_OPTION * N_OPTS
@@ -333,6 +363,7 @@ def run_ours(args, rank, world, local_rank):
         e2e_err = float((np.abs(got - ref) / np.maximum(np.abs(ref), 1.0)).max())
         ctx2.close()
 
+        clocks.__exit__(None, None, None)
         # ---- CPU oracle baseline (bounded sample)
         cpu_val, cpu_samples, cpu_s = cpu_oracle_rate(args.cpu_seconds)
 
@@ -362,8 +393,9 @@ def run_ours(args, rank, world, local_rank):
                              "sample": "%d samples of 10 x 1e6 options (fp64 C oracle, one thread) in %.1f s; "
                                        "scaled to whole DAGs" % (cpu_samples, cpu_s)},
             "gpu_launches": args.steps * N_VEC,
-            "clocks": clocks.summary(),
+            "clocks": dict(clocks.summary(), window="warm-up through the last GPU measurement"),
         }
+    clocks.__exit__(None, None, None)
     ctx.close()
     if dist:
         dist.barrier()

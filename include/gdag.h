@@ -77,6 +77,7 @@ extern "C" {
 #define GDAG_NODE_HOST_WRITE 1  /* host-to-device copy of a host write      */
 #define GDAG_NODE_HOST_READ  2  /* host read (device-to-host copy if needed) */
 #define GDAG_NODE_EXTERNAL   3  /* library call given the chosen stream     */
+#define GDAG_NODE_HOST_PREFETCH 4 /* device-to-host copy ahead of a read    */
 
 typedef struct gdag_ctx gdag_ctx;
 typedef int32_t gdag_array;   /* array handle, >= 0                          */
@@ -248,6 +249,18 @@ int gdag_array_write(gdag_ctx *ctx, gdag_array a, const void *src, size_t off,
  * or a child's).  Errors: INVALID, TIMEOUT, CUDA. */
 int gdag_array_read(gdag_ctx *ctx, gdag_array a, void *dst, size_t off,
                     size_t bytes);
+
+/* Start copying [off, off+bytes) of the array to its host view without
+ * waiting (a DAG element that reads the array, placed like a kernel: after
+ * the array's last writer, as the first child on the writer's stream when it
+ * can be).  A later gdag_array_read inside that range, with no GPU write to
+ * the array in between, waits for this copy instead of issuing its own.  The
+ * device-to-host counterpart of the automatic host-to-device prefetch of
+ * Section III-C; on a full-duplex host link, result copies then overlap the
+ * input copies of other branches.  The caller must not touch the host view
+ * until a read (or gdag_array_host) returns.  Errors: INVALID, CUDA. */
+int gdag_array_prefetch_host(gdag_ctx *ctx, gdag_array a, size_t off,
+                             size_t bytes);
 
 /* -------------------------------------------------------------- kernels
  * Built-in sm_103a kernels with their signatures (argument order and modes

@@ -68,6 +68,19 @@ void orc_bs_call(const double *S, double *C, int64_t n,
     }
 }
 
+/* Magnitude of the two terms of C, S N(d1) + K exp(-rT) N(d2): the
+ * condition scale of the difference (C is small where they nearly cancel). */
+void orc_bs_call_scale(const double *S, double *A, int64_t n,
+                       double K, double r, double sigma, double T)
+{
+    for (int64_t i = 0; i < n; ++i) {
+        double d1 = (log(S[i] / K) + (r + 0.5 * sigma * sigma) * T)
+                    / (sigma * sqrt(T));
+        double d2 = d1 - sigma * sqrt(T);
+        A[i] = S[i] * orc_cnd(d1) + K * exp(-r * T) * orc_cnd(d2);
+    }
+}
+
 /* ------------------------------------------------------------------ IMG --
  * Section IV-B, IMG: a sharpened picture combined with copies blurred at low
  * and medium frequency.  Readings (the paper gives no formulas):

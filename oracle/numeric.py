@@ -47,6 +47,7 @@ _SIGS = {
     "orc_sum_abs_diff": (_dbl, [_D, _D, _i64]),
     "orc_cnd": (_dbl, [_dbl]),
     "orc_bs_call": (None, [_D, _D, _i64, _dbl, _dbl, _dbl, _dbl]),
+    "orc_bs_call_scale": (None, [_D, _D, _i64, _dbl, _dbl, _dbl, _dbl]),
     "orc_gauss_weights": (None, [ctypes.c_int, _dbl, _D]),
     "orc_blur": (None, [_D, _D, _i64, _i64, _D, ctypes.c_int]),
     "orc_sobel": (None, [_D, _D, _i64, _i64]),
@@ -122,6 +123,13 @@ def bs_call(S, K=60.0, r=0.1, sigma=0.2, T=1.0):
     C = np.empty_like(S)
     lib().orc_bs_call(_p(S), _p(C), S.size, K, r, sigma, T)
     return C
+
+
+def bs_call_scale(S, K=60.0, r=0.1, sigma=0.2, T=1.0):
+    S = _f64(S)
+    A = np.empty_like(S)
+    lib().orc_bs_call_scale(_p(S), _p(A), S.size, K, r, sigma, T)
+    return A
 
 
 # ---------------------------------------------------------------- IMG

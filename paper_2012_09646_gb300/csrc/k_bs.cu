@@ -2,7 +2,30 @@
 // every spot price of a vector, fp32.
 //   d1 = (ln(S/K) + (r + sigma^2/2) T) / (sigma sqrt(T)),  d2 = d1 - sigma sqrt(T)
 //   C  = S N(d1) - K exp(-rT) N(d2)
-// N is CUDA's normcdff; the logarithm CUDA's logf.
+//
+// N is evaluated through the Mills ratio R(z) = (1 - N(z)) / phi(z):
+// N(x) = phi(x) R(-x) for x < 0 and 1 - phi(x) R(x) for x >= 0, with R a
+// rational function P(z)/Q(z) of degrees 6/7 whose coefficients are all
+// positive (fp32 Horner without cancellation); relative error of R below
+// 8e-9 on [0, 1e5].  The fit is derived in fit_mills_ratio.py (in the
+// variable u = z/4); here the coefficients are rescaled to z and P is
+// pre-multiplied by 1/sqrt(2 pi), the constant of phi.
+//
+// GB300 specifics.  The kernel reads 4 and writes 4 bytes per option, so it
+// is HBM-bound only if it stays near 35 instructions per option; therefore:
+//  - d1 and d2 travel as one float2 through the packed fp32x2 FMA/MUL of
+//    sm_100+ (__ffma2_rn, __fmul2_rn): both CDFs cost one Horner chain;
+//  - the transcendentals are single MUFU operations written as PTX:
+//    lg2.approx for the logarithm, ex2.approx for phi, rcp.approx for 1/Q;
+//  - d1 = lg2(S) (ln2 / (sigma sqrt T)) + (drift - ln K) / (sigma sqrt T) is
+//    one FMA, with both constants computed in double on the host.
+// Error: a shift e common to d1 and d2 (the logarithm's error, the rounding
+// of the constants) changes C only to second order, because
+// S phi(d1) = K exp(-rT) phi(d2); what remains is each N's own error.
+// Conditioning: C is a difference of two terms of size ~S, so for
+// sigma sqrt(T) well below 1e-2 an fp32 price near the strike carries an
+// error of a few ulp of S, whatever the evaluation.
+#include <cmath>
 #include <vector>
 
 #include "catalog.h"
@@ -11,27 +34,71 @@
 namespace gdag {
 
 struct BsConst {
-    float inv_k, drift, inv_vol, vol, k_disc;
+    float a, b;     // d1 = lg2(S) a + b
+    float vol;      // sigma sqrt(T): d2 = d1 - vol
+    float k_disc;   // K exp(-rT)
 };
+
+__device__ __forceinline__ float2 f2(float v) { return make_float2(v, v); }
+
+__device__ __forceinline__ float lg2_approx(float x)
+{
+    float y;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float ex2_approx(float x)
+{
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float rcp_approx(float x)
+{
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// (N(d.x), N(d.y)).  |d| is clamped at 40, where phi has long underflowed to
+// 0 in fp32 (and P, Q would overflow for |d| > 1e5).
+__device__ __forceinline__ float2 norm_cdf2(float2 d)
+{
+    const float2 z = make_float2(fminf(fabsf(d.x), 40.0f), fminf(fabsf(d.y), 40.0f));
+    float2 p = f2(2.272637658e-04f);
+    p = __ffma2_rn(p, z, f2(3.562737228e-03f));
+    p = __ffma2_rn(p, z, f2(2.683402843e-02f));
+    p = __ffma2_rn(p, z, f2(1.214417067e-01f));
+    p = __ffma2_rn(p, z, f2(3.465261792e-01f));
+    p = __ffma2_rn(p, z, f2(5.959146476e-01f));
+    p = __ffma2_rn(p, z, f2(5.000000011e-01f));
+    float2 q = f2(5.696657770e-04f);
+    q = __ffma2_rn(q, z, f2(8.930458472e-03f));
+    q = __ffma2_rn(q, z, f2(6.783256553e-02f));
+    q = __ffma2_rn(q, z, f2(3.133407961e-01f));
+    q = __ffma2_rn(q, z, f2(9.347127516e-01f));
+    q = __ffma2_rn(q, z, f2(1.780614313e+00f));
+    q = __ffma2_rn(q, z, f2(1.989713857e+00f));
+    q = __ffma2_rn(q, z, f2(1.000000000e+00f));
+    const float2 t = __fmul2_rn(__fmul2_rn(z, z), f2(-7.213475204e-01f));  // -z^2 log2(e) / 2
+    const float2 e = make_float2(ex2_approx(t.x), ex2_approx(t.y));
+    const float2 rq = make_float2(rcp_approx(q.x), rcp_approx(q.y));
+    const float2 tail = __fmul2_rn(__fmul2_rn(p, rq), e);  // phi(z) R(z)
+    return make_float2(d.x < 0.f ? tail.x : 1.0f - tail.x, d.y < 0.f ? tail.y : 1.0f - tail.y);
+}
 
 __device__ __forceinline__ float bs_price(float s, const BsConst &c)
 {
-    float d1 = (logf(s * c.inv_k) + c.drift) * c.inv_vol;
-    float d2 = d1 - c.vol;
-    return s * normcdff(d1) - c.k_disc * normcdff(d2);
+    const float d1 = fmaf(lg2_approx(s), c.a, c.b);
+    const float2 n = norm_cdf2(make_float2(d1, d1 - c.vol));
+    return s * n.x - c.k_disc * n.y;
 }
 
 // 8 bytes of HBM traffic per option (4 in, 4 out); streaming loads/stores
 // (each byte is touched once).
 __global__ void __launch_bounds__(1024) bs_call_kernel(const float *__restrict__ S, float *__restrict__ C, int64_t n,
-                                                       float K, float r, float sigma, float T)
+                                                       BsConst c)
 {
-    BsConst c;
-    c.inv_k = 1.0f / K;
-    c.vol = sigma * sqrtf(T);
-    c.inv_vol = 1.0f / c.vol;
-    c.drift = (r + 0.5f * sigma * sigma) * T;
-    c.k_disc = K * expf(-r * T);
     if (((reinterpret_cast<uintptr_t>(S) | reinterpret_cast<uintptr_t>(C)) & 15) == 0) {
         const float4 *S4 = reinterpret_cast<const float4 *>(S);
         float4 *C4 = reinterpret_cast<float4 *>(C);
@@ -85,8 +152,14 @@ int launch_bs(const LaunchArgs &a, void *s)
     if (n == 0) return cudaSuccess;
     unsigned g = a.auto_cfg ? stream_grid(n >> 2) : a.grid[0];
     unsigned b = a.auto_cfg ? kThreads : a.block[0];
-    bs_call_kernel<<<g, b, 0, (cudaStream_t)s>>>(a.p<float>(0), a.p<float>(1), n, a.f32(3), a.f32(4), a.f32(5),
-                                                 a.f32(6));
+    const double K = a.f32(3), r = a.f32(4), sigma = a.f32(5), T = a.f32(6);
+    const double vol = sigma * std::sqrt(T);
+    BsConst c;
+    c.a = (float)(std::log(2.0) / vol);
+    c.b = (float)(((r + 0.5 * sigma * sigma) * T - std::log(K)) / vol);
+    c.vol = (float)vol;
+    c.k_disc = (float)(K * std::exp(-r * T));
+    bs_call_kernel<<<g, b, 0, (cudaStream_t)s>>>(a.p<float>(0), a.p<float>(1), n, c);
     return cudaGetLastError();
 }
 

@@ -22,11 +22,13 @@ inline int sm_count()
 
 inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
-// Streaming kernels: each block handles tiles of kThreads x kUnroll float4,
-// grid-stride over tiles, at most kBlocksPerSm resident blocks per SM.
+// Streaming kernels: each block handles tiles of kThreads x kUnroll float4
+// and grid-strides over tiles.  The grid is capped at kBlocksPerSm blocks per
+// SM, so for most sizes a block handles about one tile and the hardware's
+// block scheduler balances the tail.
 constexpr int kThreads = 256;
 constexpr int kUnroll = 4;
-constexpr int kBlocksPerSm = 8;
+constexpr int kBlocksPerSm = 32;
 
 inline unsigned stream_grid(int64_t n_vec4)
 {

@@ -68,7 +68,10 @@ struct ArrayState {
     bool host_valid = false;  // host view holds the current contents
     int64_t writer = -1;
     std::vector<int64_t> readers;
-    int64_t host_copy = -1;   // last host-to-device copy reading the view
+    int64_t view_copy = -1;   // last copy node reading or writing the view
+    int64_t prefetch = -1;    // pending device-to-host prefetch node
+    int64_t pf_writer = -1;   // the array's writer when it was issued
+    size_t pf_off = 0, pf_bytes = 0;
 };
 
 struct StreamState {
@@ -490,16 +493,16 @@ struct Ctx {
         return GDAG_OK;
     }
 
-    // Wait until no host-to-device copy in flight reads the host view.
+    // Wait until no copy in flight reads or writes the host view.
     int release_view(ArrayState &s)
     {
-        if (s.host_copy >= 0) {
-            Node *n = node(s.host_copy);
+        if (s.view_copy >= 0) {
+            Node *n = node(s.view_copy);
             if (n && n->active) {
-                int r = host_wait(s.host_copy);
+                int r = host_wait(s.view_copy);
                 if (r) return r;
             }
-            s.host_copy = -1;
+            s.view_copy = -1;
         }
         return GDAG_OK;
     }
@@ -894,7 +897,8 @@ int gdag_array_write(gdag_ctx *c, gdag_array a, const void *src, size_t off, siz
     ++c->st.copies;
     r = c->be->copy_h2d(static_cast<char *>(s->dev) + off, view, bytes, c->streams[(size_t)st].handle);
     if (r) return c->abort_node(id, r, "host-to-device copy");
-    s->host_copy = id;
+    s->view_copy = id;
+    s->prefetch = -1;  // the view now holds the host's data
     r = c->finish(id, st);
     if (r) return r;
     if (!c->opt.prefetch) return c->host_wait(id);
@@ -913,11 +917,20 @@ int gdag_array_read(gdag_ctx *c, gdag_array a, void *dst, size_t off, size_t byt
     r = c->ensure_host(*s);
     if (r) return r;
     char *view = static_cast<char *>(s->host) + off;
+    const bool covered = s->prefetch >= 0 && s->pf_writer == s->writer && off >= s->pf_off &&
+                         off + bytes <= s->pf_off + s->pf_bytes;
     Access acc{a, gdag::R_BIT};
     int64_t id = c->next_id();
     c->infer(id, &acc, 1);
     c->push_node(GDAG_NODE_HOST_READ);
-    if (!s->host_valid) {
+    if (!s->host_valid && covered) {
+        // a device-to-host prefetch of this range is in flight or done
+        int64_t pf = s->prefetch;
+        r = c->host_wait(pf);
+        if (r) return r;
+        c->log_op(GDAG_OP_HOST_NODE, -1, -1, id);
+        if (s->pf_off == 0 && s->pf_bytes == s->bytes) s->host_valid = true;
+    } else if (!s->host_valid) {
         int32_t st;
         r = c->place(id, &st);
         if (r) {
@@ -941,6 +954,43 @@ int gdag_array_read(gdag_ctx *c, gdag_array a, void *dst, size_t off, size_t byt
     return GDAG_OK;
 }
 
+int gdag_array_prefetch_host(gdag_ctx *c, gdag_array a, size_t off, size_t bytes)
+{
+    if (!c) return GDAG_ERR_INVALID;
+    int r = c->guard();
+    if (r) return r;
+    ArrayState *s = c->arr(a);
+    if (!s) return c->fail(GDAG_ERR_INVALID, "unknown array %d", a);
+    if (off > s->bytes || bytes > s->bytes - off)
+        return c->fail(GDAG_ERR_INVALID, "prefetch of [%zu, %zu) outside %zu bytes", off, off + bytes, s->bytes);
+    if (s->host_valid) return GDAG_OK;  // the view is already current
+    r = c->ensure_host(*s);
+    if (r) return r;
+    r = c->release_view(*s);  // an earlier copy still using the view
+    if (r) return r;
+    Access acc{a, gdag::R_BIT};
+    int64_t id = c->next_id();
+    c->infer(id, &acc, 1);
+    c->push_node(GDAG_NODE_HOST_PREFETCH);
+    int32_t st;
+    r = c->place(id, &st);
+    if (r) {
+        c->retire(id);
+        return r;
+    }
+    c->log_op(GDAG_OP_COPY_D2H, st, -1, id);
+    ++c->st.copies;
+    r = c->be->copy_d2h(static_cast<char *>(s->host) + off, static_cast<char *>(s->dev) + off, bytes,
+                        c->streams[(size_t)st].handle);
+    if (r) return c->abort_node(id, r, "device-to-host prefetch");
+    s->prefetch = id;
+    s->pf_writer = s->writer;
+    s->pf_off = off;
+    s->pf_bytes = bytes;
+    s->view_copy = id;
+    return c->finish(id, st);
+}
+
 int gdag_sync(gdag_ctx *c)
 {
     if (!c) return GDAG_ERR_INVALID;
@@ -960,9 +1010,13 @@ int gdag_sync(gdag_ctx *c)
         c->nodes.clear();
         c->parent_arena.clear();
         for (auto &a : c->arrays) {
+            // a completed whole-array prefetch leaves the view current
+            if (a.prefetch >= 0 && a.pf_writer == a.writer && a.pf_off == 0 && a.pf_bytes == a.bytes)
+                a.host_valid = true;
+            a.prefetch = -1;
             a.writer = -1;
             a.readers.clear();
-            a.host_copy = -1;
+            a.view_copy = -1;
         }
         for (auto &s : c->streams) s.tail = -1;
     }

@@ -41,7 +41,7 @@ GDAG_MODE_INOUT = 4
 GDAG_MODE_SIGNATURE = -1
 
 GDAG_EDGE_RAW, GDAG_EDGE_WAR, GDAG_EDGE_WAW = 0, 1, 2
-GDAG_NODE_KERNEL, GDAG_NODE_HOST_WRITE, GDAG_NODE_HOST_READ, GDAG_NODE_EXTERNAL = 0, 1, 2, 3
+GDAG_NODE_KERNEL, GDAG_NODE_HOST_WRITE, GDAG_NODE_HOST_READ, GDAG_NODE_EXTERNAL, GDAG_NODE_HOST_PREFETCH = 0, 1, 2, 3, 4
 GDAG_ARG_ARRAY, GDAG_ARG_SCALAR = 0, 1
 (GDAG_OP_LAUNCH, GDAG_OP_COPY_H2D, GDAG_OP_COPY_D2H, GDAG_OP_EXTERNAL, GDAG_OP_RECORD, GDAG_OP_WAIT,
  GDAG_OP_HOST_WAIT, GDAG_OP_STREAM_SYNC, GDAG_OP_HOST_NODE, GDAG_OP_QUERY_DONE) = range(10)
@@ -117,6 +117,7 @@ SIGNATURES = {
     "gdag_array_host": (ctypes.c_int, [_ctx, _i32, _i32, _P(_vp)]),
     "gdag_array_write": (ctypes.c_int, [_ctx, _i32, _vp, _sz, _sz]),
     "gdag_array_read": (ctypes.c_int, [_ctx, _i32, _vp, _sz, _sz]),
+    "gdag_array_prefetch_host": (ctypes.c_int, [_ctx, _i32, _sz, _sz]),
     "gdag_kernel_lookup": (ctypes.c_int, [_ctx, ctypes.c_char_p, _P(_i32)]),
     "gdag_kernel_signature": (ctypes.c_int, [_ctx, _i32, _P(_i32), _P(gdag_argspec), _i32]),
     "gdag_kernel_register": (ctypes.c_int, [_ctx, ctypes.c_char_p, _vp, _i32, _P(gdag_argspec), _P(_i32)]),
@@ -212,6 +213,10 @@ def gdag_array_write(ctx, a, src, off, nbytes):
 
 def gdag_array_read(ctx, a, dst, off, nbytes):
     return _check(ctx, lib().gdag_array_read(ctx, a, dst, off, nbytes))
+
+
+def gdag_array_prefetch_host(ctx, a, off, nbytes):
+    return _check(ctx, lib().gdag_array_prefetch_host(ctx, a, off, nbytes))
 
 
 def gdag_kernel_lookup(ctx, name):
@@ -412,6 +417,10 @@ class Context:
     def read(self, a, dst=None, off=0, nbytes=None):
         nbytes = a.nbytes - off if nbytes is None else nbytes
         gdag_array_read(self.h, a.handle, _host_ptr(dst), off, nbytes)
+
+    def prefetch_host(self, a, off=0, nbytes=None):
+        nbytes = a.nbytes - off if nbytes is None else nbytes
+        gdag_array_prefetch_host(self.h, a.handle, off, nbytes)
 
     # kernels
     def kernel(self, name):

@@ -92,13 +92,124 @@ class BsDag:
         """Kernels only (inputs already in HBM); no host access."""
         self.launch_all()
 
-    def step_e2e(self):
+    def step_e2e(self, prefetch=True):
         """Host write of every price vector, all kernels, host read of every
-        result (the paper's streaming form of the benchmark)."""
+        result (the paper's streaming form of the benchmark).  With
+        ``prefetch`` each result's copy to the host is started right after its
+        kernel, so it overlaps the other chains' input copies."""
         c, nb = self.ctx, 4 * self.n
         K, r, s, T = self.params
         for Sa, Ca in zip(self.SA, self.CA):
             c.write(Sa, None, 0, nb)
             c.launch("bs_call", Sa, Ca, self.n, K, r, s, T)
+            if prefetch:
+                c.prefetch_host(Ca, 0, nb)
         for Ca in self.CA:
             c.read(Ca, None, 0, nb)
+
+
+def gaussian_weights(radius, sigma):
+    """Normalised Gaussian taps exp(-k^2 / (2 sigma^2)), k = -radius..radius,
+    as float32 (filter parameters of the blur nodes)."""
+    import math
+    w = [math.exp(-(k * k) / (2.0 * sigma * sigma)) for k in range(-radius, radius + 1)]
+    s = sum(w)
+    return torch.tensor([v / s for v in w], dtype=F32)
+
+
+class ImgDag:
+    """IMG: blur5 and blur9 of the image, Sobel of each, min/max of each,
+    contrast stretch of each edge map, unsharp mask of the image with blur5,
+    and the final combination (10 kernels).  The host writes the image and
+    reads the result each step."""
+
+    R5, SIGMA5, R9, SIGMA9, ALPHA = 2, 1.0, 4, 2.0, 0.5
+
+    def __init__(self, ctx, rows, cols, device="cuda"):
+        self.ctx, self.rows, self.cols = ctx, rows, cols
+        n = rows * cols
+        self.n = n
+        t = lambda: torch.zeros(n, dtype=F32, device=device)
+        self.img, self.b5, self.b9, self.e5, self.e9, self.s, self.out = (t() for _ in range(7))
+        self.mm5 = torch.zeros(2, dtype=F32, device=device)
+        self.mm9 = torch.zeros(2, dtype=F32, device=device)
+        self.w5 = gaussian_weights(self.R5, self.SIGMA5).to(device)
+        self.w9 = gaussian_weights(self.R9, self.SIGMA9).to(device)
+        self.h_img, self.h_out = _pinned(n, F32), _pinned(n, F32)
+        A = ctx.array
+        self.IMG = A(self.img, host=self.h_img, name="img")
+        self.OUT = A(self.out, host=self.h_out, name="out")
+        self.B5, self.B9, self.E5, self.E9, self.S = (A(x, name=nm) for x, nm in (
+            (self.b5, "b5"), (self.b9, "b9"), (self.e5, "e5"), (self.e9, "e9"), (self.s, "s")))
+        self.MM5, self.MM9 = A(self.mm5, name="mm5"), A(self.mm9, name="mm9")
+        self.W5, self.W9 = A(self.w5, name="w5"), A(self.w9, name="w9")
+        self._s5, self.SC5 = _scratch(ctx, "minmax", n, device)
+        self._s9, self.SC9 = _scratch(ctx, "minmax", n, device)
+
+    def load(self, image):
+        self.h_img.copy_(torch.as_tensor(image).reshape(-1))
+
+    def launch_all(self):
+        c, n, rows, cols = self.ctx, self.n, self.rows, self.cols
+        c.launch("gauss_blur", self.IMG, self.B5, self.W5, rows, cols, self.R5)
+        c.launch("gauss_blur", self.IMG, self.B9, self.W9, rows, cols, self.R9)
+        c.launch("sobel", self.B5, self.E5, rows, cols)
+        c.launch("sobel", self.B9, self.E9, rows, cols)
+        c.launch("minmax", self.E5, self.MM5, self.SC5, n)
+        c.launch("minmax", self.E9, self.MM9, self.SC9, n)
+        c.launch("extend", self.E5, self.MM5, n)
+        c.launch("extend", self.E9, self.MM9, n)
+        c.launch("unsharp", self.IMG, self.B5, self.S, self.ALPHA, n)
+        c.launch("combine", self.S, self.B5, self.B9, self.E5, self.E9, self.OUT, n)
+
+    def step(self, read=True):
+        self.ctx.write(self.IMG, None)
+        self.launch_all()
+        if read:
+            self.ctx.read(self.OUT)
+
+
+class MlDag:
+    """ML: naive-Bayes scores and ridge scores of the same X (both read-only
+    users of X, so they run concurrently), a softmax of each, and the argmax
+    of their sum as int32 labels.  X and the tables are resident; the host
+    reads the labels each step."""
+
+    def __init__(self, ctx, rows, feats=1024, classes=10, device="cuda"):
+        self.ctx, self.rows, self.feats, self.classes = ctx, rows, feats, classes
+        self.X = torch.zeros((max(rows, 1), feats), dtype=torch.int32, device=device)
+        self.T1 = torch.zeros((feats, classes), dtype=F32, device=device)
+        self.b1 = torch.zeros(classes, dtype=F32, device=device)
+        self.T2 = torch.zeros((feats, classes), dtype=F32, device=device)
+        self.b2 = torch.zeros(classes, dtype=F32, device=device)
+        self.S1 = torch.zeros((max(rows, 1), classes), dtype=F32, device=device)
+        self.S2 = torch.zeros((max(rows, 1), classes), dtype=F32, device=device)
+        self.labels = torch.zeros(max(rows, 1), dtype=torch.int32, device=device)
+        self.h_labels = _pinned(max(rows, 1), torch.int32)
+        A = ctx.array
+        self.XA, self.T1A, self.b1A = A(self.X, name="X"), A(self.T1, name="nb_table"), A(self.b1, name="nb_prior")
+        self.T2A, self.b2A = A(self.T2, name="ridge_w"), A(self.b2, name="ridge_b")
+        self.S1A, self.S2A = A(self.S1, name="s1"), A(self.S2, name="s2")
+        self.LA = A(self.labels, host=self.h_labels, name="labels")
+
+    def load(self, X, nb_table, nb_prior, ridge_w, ridge_b):
+        """Device-resident inputs (set once, outside the timed region)."""
+        self.X[: self.rows].copy_(torch.as_tensor(X))
+        self.T1.copy_(torch.as_tensor(nb_table))
+        self.b1.copy_(torch.as_tensor(nb_prior))
+        self.T2.copy_(torch.as_tensor(ridge_w))
+        self.b2.copy_(torch.as_tensor(ridge_b))
+        torch.cuda.synchronize()
+
+    def launch_all(self):
+        c, r, f, k = self.ctx, self.rows, self.feats, self.classes
+        c.launch("dense_scores", self.XA, self.T1A, self.b1A, self.S1A, r, f, k)
+        c.launch("dense_scores", self.XA, self.T2A, self.b2A, self.S2A, r, f, k)
+        c.launch("row_softmax", self.S1A, r, k)
+        c.launch("row_softmax", self.S2A, r, k)
+        c.launch("argmax_combine", self.S1A, self.S2A, self.LA, r, k)
+
+    def step(self, read=True):
+        self.launch_all()
+        if read:
+            self.ctx.read(self.LA, None, 0, 4 * self.rows)

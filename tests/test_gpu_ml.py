@@ -1,0 +1,101 @@
+"""ML nodes and the ML DAG on the GPU through the C ABI, against the oracle.
+Scores: with the dyadic tables of the input recipe every product and partial
+sum is an exact float32, so scores must be bit-exact; for general tables,
+|got - ref| <= 1e-5 * sum |terms|.  Softmax: 1e-5 relative to max(|p|, 1)
+on the GPU's own scores.  Labels: bit-exact, except rows whose oracle top-2
+margin is below 4e-5 (twice the summed bound of P1 + P2), which may take
+either of the two best labels; their count is reported."""
+import numpy as np
+import pytest
+
+import datagen
+from oracle import numeric as N
+from oracle import pipelines as P
+from paper_2012_09646_gb300 import gdag as G
+from paper_2012_09646_gb300.workloads import MlDag
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-5
+MARGIN = 4e-5
+
+
+def run(rows, feats, classes, seed, inputs=None):
+    inp = inputs or datagen.ml_inputs(rows, feats=feats, classes=classes, seed=seed)
+    ctx = G.Context()
+    d = MlDag(ctx, rows, feats, classes)
+    d.load(*inp)
+    d.launch_all()
+    ctx.sync()
+    return ctx, d, inp
+
+
+@pytest.mark.parametrize("rows,feats,classes", [(1, 32, 10), (7, 64, 3), (100, 1024, 10), (1001, 256, 12),
+                                                (333, 96, 1), (64, 32, 16)])
+def test_scores_bit_exact_with_dyadic_tables(rows, feats, classes):
+    ctx, d, (X, T1, b1, T2, b2) = run(rows, feats, classes, seed=rows)
+    s1 = d.S1[:rows].cpu().numpy()
+    s2 = d.S2[:rows].cpu().numpy()
+    assert np.array_equal(s1.astype(np.float64), N.scores(X, T1, b1))
+    assert np.array_equal(s2.astype(np.float64), N.scores(X, T2, b2))
+    ctx.close()
+
+
+def test_scores_general_tables_within_tolerance():
+    rows, feats, classes = 513, 1024, 10
+    X, *_ = datagen.ml_inputs(rows, feats=feats, classes=classes, seed=7)
+    g = np.random.default_rng(0)
+    T = g.normal(0, 1, (feats, classes)).astype(np.float32)
+    b = g.normal(0, 1, classes).astype(np.float32)
+    ctx, d, _ = run(rows, feats, classes, 0, inputs=(X, T, b, T, b))
+    got = d.S1[:rows].cpu().numpy().astype(np.float64)
+    ref = N.scores(X, T, b)
+    scale = N.scores_abs(X, T, b)
+    assert np.all(np.abs(got - ref) <= TOL * np.maximum(scale, 1.0))
+    ctx.close()
+
+
+@pytest.mark.parametrize("rows", [1, 37, 4097])
+def test_softmax_and_labels(rows):
+    ctx, d, inp = run(rows, 1024, 10, seed=rows + 1)
+    ref = P.ml(*inp)
+    p1 = d.S1[:rows].cpu().numpy().astype(np.float64)
+    p2 = d.S2[:rows].cpu().numpy().astype(np.float64)
+    # softmax of the (exact) scores
+    assert np.all(np.abs(p1 - ref["p1"]) <= TOL * np.maximum(np.abs(ref["p1"]), 1.0))
+    assert np.all(np.abs(p2 - ref["p2"]) <= TOL * np.maximum(np.abs(ref["p2"]), 1.0))
+    np.testing.assert_allclose(p1.sum(axis=1), 1.0, rtol=1e-5)
+    labels = d.labels[:rows].cpu().numpy()
+    close = ref["margin"] < MARGIN
+    assert np.array_equal(labels[~close], ref["labels"][~close])
+    top2 = np.argsort(-(ref["p1"] + ref["p2"]), axis=1, kind="stable")[:, :2]
+    assert all(labels[i] in top2[i] for i in np.flatnonzero(close))
+
+
+def test_argmax_ties_lowest_index():
+    rows, classes = 3, 4
+    with G.Context() as ctx:
+        import torch
+        p1 = torch.tensor([[0.25, 0.25, 0.5, 0.0], [0.0, 0.0, 0.0, 0.0], [0.1, 0.6, 0.3, 0.0]], device="cuda")
+        p2 = torch.tensor([[0.25, 0.25, 0.0, 0.5], [0.0, 0.0, 0.0, 0.0], [0.6, 0.1, 0.3, 0.0]], device="cuda")
+        lab = torch.full((rows,), -1, dtype=torch.int32, device="cuda")
+        ctx.launch("argmax_combine", ctx.array(p1), ctx.array(p2), ctx.array(lab), rows, classes)
+        ctx.sync()
+        assert lab.cpu().tolist() == [0, 0, 0]
+
+
+def test_ml_dag_full_size_host_labels():
+    """The benchmark's shape: 100000 x 1024, 10 classes; the host reads the
+    labels through the library; every row checked."""
+    rows = 100_000
+    inp = datagen.ml_inputs(rows, feats=1024, classes=10, seed=3)
+    ref = P.ml(*inp)
+    with G.Context() as ctx:
+        d = MlDag(ctx, rows)
+        d.load(*inp)
+        d.step()
+        labels = d.h_labels[:rows].numpy()
+        close = ref["margin"] < MARGIN
+        assert np.array_equal(labels[~close], ref["labels"][~close])
+        print("near-tie rows:", int(close.sum()))
+        st = ctx.stats()
+        assert st["streams"] >= 2  # the two score branches ran on two streams

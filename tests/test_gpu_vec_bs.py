@@ -113,6 +113,29 @@ def test_bs_extreme_prices():
         assert ok, worst
 
 
+@pytest.mark.parametrize("K,r,sigma,T", [(60.0, 0.1, 0.2, 1.0), (40.0, 0.1, 0.2, 0.5), (60.0, 0.03, 0.6, 2.0),
+                                         (60.0, 0.1, 1e-3, 1.0), (1.0, 0.0, 3.0, 10.0)])
+def test_bs_other_parameters(K, r, sigma, T):
+    """Other parameters, spot prices U[0.5, 200).  C = S N(d1) - K e^-rT N(d2)
+    is a difference of two terms, so the scale of the relative bound is the
+    terms' magnitude (the reading used for every difference or sum here);
+    at the benchmark's sigma = 0.2 the strict scale s = 1 also holds."""
+    n = 200_001
+    p = datagen.bs_inputs(n, count=1, seed=5, lo=0.5, hi=200.0)[0]
+    with G.Context() as ctx:
+        b = BsDag(ctx, n, count=1, K=K, r=r, sigma=sigma, T=T)
+        b.load_host([p])
+        b.step_e2e()
+        got = b.hC[0][:n].numpy()
+        assert np.isfinite(got).all()
+        ref = N.bs_call(p, K, r, sigma, T)
+        ok, worst = close(got, ref, np.maximum(N.bs_call_scale(p, K, r, sigma, T), 1.0))
+        assert ok, worst
+        if sigma >= 0.2:
+            ok, worst = close(got, ref)
+            assert ok, worst
+
+
 @pytest.mark.parametrize("policy", [G.GDAG_POLICY_PARALLEL, G.GDAG_POLICY_SERIAL_SYNC])
 def test_bs_full_config_sampled(policy):
     """B&S at the benchmark size (10 x 1e7), in the launch shape the bench

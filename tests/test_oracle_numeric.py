@@ -107,6 +107,18 @@ def test_bs_limits_and_bounds():
     assert np.all(np.diff(C, 2) > -1e-12)  # convex in S
 
 
+def test_bs_term_scale_limits():
+    K, r, T = 60.0, 0.1, 1.0
+    disc = K * math.exp(-r * T)
+    S = np.array([10.0, 40.0, 59.0, 80.0, 100.0])
+    # sigma -> 0: both CDFs are 1 in the money (S + K e^-rT), 0 out of it
+    np.testing.assert_allclose(N.bs_call_scale(S, K, r, 1e-6, T),
+                               np.where(S > disc, S + disc, 0.0), atol=1e-9)
+    C = N.bs_call(S, K, r, 0.2, T)
+    A = N.bs_call_scale(S, K, r, 0.2, T)
+    assert np.all(A >= np.abs(C)) and np.all(A <= S + disc)
+
+
 # ------------------------------------------------------------------ IMG
 @pytest.mark.parametrize("R,sigma", [(P.IMG_R5, P.IMG_SIGMA5), (P.IMG_R9, P.IMG_SIGMA9)])
 def test_gauss_weights_match_scipy_window(R, sigma):

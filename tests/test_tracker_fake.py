@@ -45,6 +45,12 @@ class Program:
         self.ctx.read(self.arrays[a])
         self.elems.append({a: D.R})
 
+    def prefetch(self, a):
+        before = len(self.ctx.nodes())
+        self.ctx.prefetch_host(self.arrays[a])
+        if len(self.ctx.nodes()) > before:  # no element when the view is current
+            self.elems.append({a: D.R})
+
 
 def edges_of(ctx, names=None):
     return {(s, d, a, k) for s, d, a, k in ctx.edges()}
@@ -58,6 +64,8 @@ def run_random(rng, L, n_arrays, **opts):
             p.write(rng.randrange(n_arrays))
         elif r < 0.22:
             p.read(rng.randrange(n_arrays))
+        elif r < 0.28:
+            p.prefetch(rng.randrange(n_arrays))
         else:
             k = rng.randint(1, min(4, n_arrays))
             arrs = rng.sample(range(n_arrays), k)
@@ -77,7 +85,7 @@ def test_paper_cases_through_tracker(name):
     assert edges_of(p.ctx) == want
 
 
-@pytest.mark.parametrize("seed", range(40))
+@pytest.mark.parametrize("seed", range(60))
 def test_random_programs_match_brute_force(seed):
     rng = random.Random(seed)
     opts = rng.choice([{}, {"max_streams": 2}, {"retire_by_query": True, "fake_complete": True},
@@ -257,3 +265,21 @@ def test_external_call_gets_chosen_stream():
     node = ctx.external(lambda s, u: seen.append(s), [(a, G.GDAG_MODE_IN), (b, G.GDAG_MODE_OUT)])
     # fake backend does not call the function; the edge is still inferred
     assert (0, node, a.handle, G.GDAG_EDGE_RAW) in ctx.edges()
+
+
+def test_prefetch_then_read_copies_once():
+    p = Program(2)
+    p.kernel({0: D.R, 1: D.W})
+    p.prefetch(1)
+    p.read(1)
+    ops = p.ctx.ops()
+    d2h = [o for o in ops if o[0] == G.GDAG_OP_COPY_D2H]
+    assert len(d2h) == 1 and d2h[0][3] == 1          # the prefetch node
+    assert [o for o in ops if o[0] == G.GDAG_OP_HOST_WAIT][-1][3] == 1
+    assert ops[-1][0] == G.GDAG_OP_HOST_NODE and ops[-1][3] == 2
+    # a kernel write after the prefetch makes the read copy again
+    p.prefetch(1)
+    p.kernel({1: D.W})
+    p.read(1)
+    assert len([o for o in p.ctx.ops() if o[0] == G.GDAG_OP_COPY_D2H]) == 2
+    assert D.check_hb(p.ctx.ops(), D.expected_edges(p.elems)) == []
