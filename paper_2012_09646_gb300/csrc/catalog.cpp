@@ -11,6 +11,9 @@ void append_vec_kernels(std::vector<KernelEntry> &v);
 void append_bs_kernels(std::vector<KernelEntry> &v);
 void append_img_kernels(std::vector<KernelEntry> &v);
 void append_ml_kernels(std::vector<KernelEntry> &v);
+void append_hits_kernels(std::vector<KernelEntry> &v);
+size_t spmv_part_bytes(int64_t rows_plus_nnz);
+size_t spmv_carry_bytes(int64_t rows_plus_nnz);
 
 namespace {
 const std::vector<KernelEntry> &table()
@@ -21,6 +24,7 @@ const std::vector<KernelEntry> &table()
         append_bs_kernels(v);
         append_img_kernels(v);
         append_ml_kernels(v);
+        append_hits_kernels(v);
         return v;
     }();
     return t;
@@ -32,9 +36,12 @@ const KernelEntry &builtin(int i) { return table()[(size_t)i]; }
 
 size_t scratch_bytes(const char *kernel, int64_t n)
 {
-    (void)n;
     if (!std::strcmp(kernel, "vec_reduce_diff")) return reduce_scratch_bytes<1>();
     if (!std::strcmp(kernel, "minmax")) return reduce_scratch_bytes<2>();
+    if (!std::strcmp(kernel, "l2norm")) return reduce_scratch_bytes<1>();
+    // for the two SpMV buffers n is nrows + nnz
+    if (!std::strcmp(kernel, "spmv_partition")) return spmv_part_bytes(n);
+    if (!std::strcmp(kernel, "spmv_csr")) return spmv_carry_bytes(n);
     return 0;
 }
 

@@ -95,42 +95,40 @@ __device__ __forceinline__ float bs_price(float s, const BsConst &c)
 }
 
 // 8 bytes of HBM traffic per option (4 in, 4 out); streaming loads/stores
-// (each byte is touched once).
+// (each byte is touched once).  The grid is sized to the resident block
+// count (one wave) and each thread walks float4s with a stride of the whole
+// grid, loading the next float4 before pricing the current one: every block
+// gets the same work to within one float4 per thread, so no tail wave.
 __global__ void __launch_bounds__(1024) bs_call_kernel(const float *__restrict__ S, float *__restrict__ C, int64_t n,
                                                        BsConst c)
 {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     if (((reinterpret_cast<uintptr_t>(S) | reinterpret_cast<uintptr_t>(C)) & 15) == 0) {
         const float4 *S4 = reinterpret_cast<const float4 *>(S);
         float4 *C4 = reinterpret_cast<float4 *>(C);
         const int64_t n4 = n >> 2;
-        const int64_t bd = blockDim.x;
-        const int64_t tile = bd * kUnroll;
-        for (int64_t base = (int64_t)blockIdx.x * tile; base < n4; base += (int64_t)gridDim.x * tile) {
-            float4 v[kUnroll];
-#pragma unroll
-            for (int k = 0; k < kUnroll; ++k) {
-                int64_t i = base + threadIdx.x + k * bd;
-                if (i < n4) v[k] = __ldcs(S4 + i);
-            }
-#pragma unroll
-            for (int k = 0; k < kUnroll; ++k) {
-                int64_t i = base + threadIdx.x + k * bd;
-                if (i < n4) {
-                    float4 o;
-                    o.x = bs_price(v[k].x, c);
-                    o.y = bs_price(v[k].y, c);
-                    o.z = bs_price(v[k].z, c);
-                    o.w = bs_price(v[k].w, c);
-                    __stcs(C4 + i, o);
-                }
-            }
+        int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (i < n4) v = __ldcs(S4 + i);
+        while (i < n4) {
+            const int64_t nx = i + stride;
+            float4 w = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (nx < n4) w = __ldcs(S4 + nx);
+            float4 o;
+            o.x = bs_price(v.x, c);
+            o.y = bs_price(v.y, c);
+            o.z = bs_price(v.z, c);
+            o.w = bs_price(v.w, c);
+            __stcs(C4 + i, o);
+            v = w;
+            i = nx;
         }
         if (blockIdx.x == 0 && threadIdx.x < (n & 3)) {
-            int64_t i = (n4 << 2) + threadIdx.x;
-            C[i] = bs_price(S[i], c);
+            int64_t t = (n4 << 2) + threadIdx.x;
+            C[t] = bs_price(S[t], c);
         }
     } else {
-        for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
             C[i] = bs_price(S[i], c);
     }
 }
@@ -150,8 +148,17 @@ int launch_bs(const LaunchArgs &a, void *s)
 {
     int64_t n = a.i64(2);
     if (n == 0) return cudaSuccess;
-    unsigned g = a.auto_cfg ? stream_grid(n >> 2) : a.grid[0];
     unsigned b = a.auto_cfg ? kThreads : a.block[0];
+    unsigned g = a.grid[0];
+    if (a.auto_cfg) {
+        static int per_sm = 0;  // resident blocks of kThreads per SM
+        if (!per_sm && cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, bs_call_kernel, kThreads, 0) != cudaSuccess)
+            per_sm = 4;
+        if (per_sm < 1) per_sm = 1;
+        const int64_t need = ceil_div((n >> 2) > 0 ? (n >> 2) : 1, kThreads);
+        const int64_t wave = (int64_t)sm_count() * per_sm;
+        g = (unsigned)(need < wave ? need : wave);
+    }
     const double K = a.f32(3), r = a.f32(4), sigma = a.f32(5), T = a.f32(6);
     const double vol = sigma * std::sqrt(T);
     BsConst c;

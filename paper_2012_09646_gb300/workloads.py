@@ -213,3 +213,71 @@ class MlDag:
         self.launch_all()
         if read:
             self.ctx.read(self.LA, None, 0, 4 * self.rows)
+
+
+class HitsDag:
+    """HITS: per iteration a' = A^T h and h' = A a (two SpMVs that read the
+    previous iterate, so they run concurrently), the L2 norm of each and the
+    scaling by it; ping-pong buffers.  The graph (CSR of A and of A^T, int32
+    indices, float32 weights) is resident; the merge-path partition of each
+    matrix is computed once by a spmv_partition node.  The host writes
+    a = h = 1 and reads both final vectors."""
+
+    def __init__(self, ctx, csr, csc, device="cuda"):
+        self.ctx = ctx
+        rp, col, val = csr
+        trp, tcol, tval = csc
+        self.n = n = len(rp) - 1
+        self.nnz = nnz = int(rp[-1])
+        i32 = torch.int32
+        dev = lambda a, dt: torch.as_tensor(a).to(dtype=dt).to(device)
+        self.A = (dev(rp, i32), dev(col, i32), dev(val, F32))
+        self.AT = (dev(trp, i32), dev(tcol, i32), dev(tval, F32))
+        A = ctx.array
+        self.AA = [A(t, name=nm) for t, nm in zip(self.A, ("rowptr", "col", "val"))]
+        self.ATA = [A(t, name=nm) for t, nm in zip(self.AT, ("t_rowptr", "t_col", "t_val"))]
+        pb = G.gdag_scratch_bytes("spmv_partition", n + nnz)
+        cb = G.gdag_scratch_bytes("spmv_csr", n + nnz)
+        self._pA = torch.zeros(pb, dtype=torch.uint8, device=device)
+        self._pAT = torch.zeros(pb, dtype=torch.uint8, device=device)
+        self._cA = torch.zeros(cb, dtype=torch.uint8, device=device)
+        self._cAT = torch.zeros(cb, dtype=torch.uint8, device=device)
+        self.PA, self.PAT = A(self._pA, name="part_A"), A(self._pAT, name="part_AT")
+        self.CA, self.CAT = A(self._cA, name="carry_A"), A(self._cAT, name="carry_AT")
+        v = lambda: torch.zeros(max(n, 1), dtype=F32, device=device)
+        self.vec = {"a": v(), "h": v(), "a2": v(), "h2": v()}
+        self.h_a, self.h_h = _pinned(max(n, 1), F32), _pinned(max(n, 1), F32)
+        self.V = {k: A(t, host=self.h_a if k == "a" else (self.h_h if k == "h" else None), name=k)
+                  for k, t in self.vec.items()}
+        self.norms = torch.zeros(2, dtype=F32, device=device)
+        self.NA = A(self.norms[0:1], name="norm_a")
+        self.NH = A(self.norms[1:2], name="norm_h")
+        self._sa, self.SA = _scratch(ctx, "l2norm", n, device)
+        self._sh, self.SH = _scratch(ctx, "l2norm", n, device)
+        ctx.launch("spmv_partition", self.AA[0], self.PA, n, nnz)
+        ctx.launch("spmv_partition", self.ATA[0], self.PAT, n, nnz)
+
+    def iterate(self, a, h, a_next, h_next):
+        c, n, nnz = self.ctx, self.n, self.nnz
+        c.launch("spmv_csr", *self.ATA, self.V[h], self.PAT, self.V[a_next], self.CAT, n, nnz)
+        c.launch("spmv_csr", *self.AA, self.V[a], self.PA, self.V[h_next], self.CA, n, nnz)
+        c.launch("l2norm", self.V[a_next], self.NA, self.SA, n)
+        c.launch("l2norm", self.V[h_next], self.NH, self.SH, n)
+        c.launch("scale", self.V[a_next], self.NA, n)
+        c.launch("scale", self.V[h_next], self.NH, n)
+
+    def run(self, iters=5, read=True):
+        """Host writes a = h = 1, then `iters` iterations; returns the names
+        of the buffers holding the final (a, h)."""
+        self.h_a.fill_(1.0)
+        self.h_h.fill_(1.0)
+        self.ctx.write(self.V["a"], None, 0, 4 * self.n)
+        self.ctx.write(self.V["h"], None, 0, 4 * self.n)
+        cur, nxt = ("a", "h"), ("a2", "h2")
+        for _ in range(iters):
+            self.iterate(cur[0], cur[1], nxt[0], nxt[1])
+            cur, nxt = nxt, cur
+        if read:
+            for k in cur:
+                self.ctx.read(self.V[k], None, 0, 4 * self.n)
+        return cur
