@@ -1,12 +1,15 @@
 """Benchmark: DAG makespan of the B&S program (10 independent Black-Scholes
 nodes over 10 x 1e7 float32 prices) under the run-time DAG scheduler, beside
 serial single-stream execution, a hand-built CUDA Graph of the same DAG, the
-critical-path bound from the solo node time, and the CPU oracle.
+critical-path bound from the solo node times, and the CPU oracle; then the
+same comparison for every other DAG of the suite (VEC, IMG, ML, HITS at their
+configured sizes) under ``dags``.
 
 One JSON line on rank 0.  ``value`` = DAGs per second with the inputs already
 resident in HBM; ``e2e`` = the same metric through the public API with the
 host writing every input and reading every result each step (pinned host
-buffers, copies inside the timed region).
+buffers, copies inside the timed region), with the copy/compute overlaps of
+one traced step.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 """
@@ -40,6 +43,12 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--dags", default="all", choices=["all", "bs"],
+                    help="also measure the VEC, IMG, ML and HITS DAGs (rank 0)")
+    ap.add_argument("--profile", default=None, choices=["bs", "vec", "img", "ml", "hits"],
+                    help="run only --steps steps of one DAG through the library (a small, "
+                         "single-context command for ncu captures); prints nothing")
+    ap.add_argument("--img-size", type=int, default=4096)
     return ap.parse_args()
 
 
@@ -183,16 +192,372 @@ def run_reference(args, rank):
 
 
 # ----------------------------------------------------------------- our arm
-def time_device(torch, fn, steps, stream):
-    """CUDA-event time of `steps` calls of fn(), bracketed on `stream`."""
+class Recorder:
+    """Forwards every call to a Context and records the program's elements in
+    issue order (kernel launches with their arguments, host writes, reads and
+    prefetches), so that each node can be re-run alone for its solo time."""
+
+    def __init__(self, ctx):
+        self.ctx = ctx
+        self.log = []
+
+    def launch(self, name, *args, **kw):
+        self.log.append(("k", name, args))
+        return self.ctx.launch(name, *args, **kw)
+
+    def write(self, a, src=None, off=0, nbytes=None):
+        self.log.append(("h2d", a, a.nbytes - off if nbytes is None else nbytes))
+        return self.ctx.write(a, src, off, nbytes)
+
+    def read(self, a, dst=None, off=0, nbytes=None):
+        self.log.append(("d2h", a, a.nbytes - off if nbytes is None else nbytes))
+        return self.ctx.read(a, dst, off, nbytes)
+
+    def prefetch_host(self, a, off=0, nbytes=None):
+        self.log.append(("d2h", a, a.nbytes - off if nbytes is None else nbytes))
+        return self.ctx.prefetch_host(a, off, nbytes)
+
+    def __getattr__(self, k):
+        return getattr(self.ctx, k)
+
+
+def alg_bytes(name, a):
+    """Algorithmic HBM bytes of one node: every input read once, every output
+    written once (the per-unit figures of the design's roofline table)."""
+    if name in ("vec_square", "bs_call"):
+        n = a[1] if name == "vec_square" else a[2]
+        return 8 * n
+    if name == "vec_reduce_diff":
+        return 8 * a[4]
+    if name in ("gauss_blur", "sobel"):
+        r, c = (a[3], a[4]) if name == "gauss_blur" else (a[2], a[3])
+        return 8 * r * c
+    if name == "minmax":
+        return 4 * a[3]
+    if name in ("extend", "scale"):
+        return 8 * a[2]
+    if name == "unsharp":
+        return 12 * a[4]
+    if name == "combine":
+        return 24 * a[6]
+    if name == "dense_scores":
+        rows, feats, classes = a[4], a[5], a[6]
+        return 4 * rows * feats + 4 * rows * classes + 4 * feats * classes
+    if name == "row_softmax":
+        return 8 * a[1] * a[2]
+    if name == "argmax_combine":
+        return 8 * a[3] * a[4] + 4 * a[3]
+    if name == "spmv_csr":
+        n, nnz = a[7], a[8]
+        return 4 * (n + 1) + 8 * nnz + 4 * n + 4 * n
+    if name == "l2norm":
+        return 4 * a[3]
+    return 0
+
+
+class Spec:
+    """One benchmark DAG: build(ctx) -> program object; step(obj) issues one
+    DAG through the library; hand(obj, ctx, H) issues the same DAG by hand on
+    explicit streams (the CUDA Graph baseline); host_sync: whether each step
+    ends with the host reading a result."""
+    name = ""
+    host_sync = False
+
+    def __init__(self, G, W, data):
+        self.G, self.W, self.data = G, W, data
+
+
+class BsSpec(Spec):
+    name = "B&S"
+
+    def build(self, ctx):
+        d = self.W.BsDag(ctx, N_OPTS, count=N_VEC, host=False)
+        d.load_device(self.data["bs"])
+        return d
+
+    def step(self, d):
+        d.step_resident()
+
+    def hand(self, d, ctx, H):
+        K, r, s, T = BS_PARAMS
+        for i in range(N_VEC):
+            H.k(i, "bs_call", d.SA[i], d.CA[i], N_OPTS, K, r, s, T)
+
+
+class VecSpec(Spec):
+    name = "VEC"
+    host_sync = True
+
+    def build(self, ctx):
+        d = self.W.VecDag(ctx, 1_000_000)
+        d.load(*self.data["vec"])
+        return d
+
+    def step(self, d):
+        d.step(read=True)
+
+    def hand(self, d, ctx, H):
+        n = d.n
+        H.copy(0, d.x, d.hx)
+        H.k(0, "vec_square", d.X, n)
+        H.copy(1, d.y, d.hy)
+        H.k(1, "vec_square", d.Y, n)
+        H.dep(0, 1)
+        H.k(0, "vec_reduce_diff", d.X, d.Y, d.Z, d.S, n)
+        H.copy(0, d.hz, d.z)
+
+
+class ImgSpec(Spec):
+    name = "IMG"
+
+    def build(self, ctx):
+        d = self.W.ImgDag(ctx, 4096, 4096)
+        d.img.copy_(self.data["img"])
+        return d
+
+    def step(self, d):
+        d.launch_all()
+
+    def hand(self, d, ctx, H):
+        n, R, C = d.n, d.rows, d.cols
+        H.k(0, "gauss_blur", d.IMG, d.B5, d.W5, R, C, d.R5)
+        H.k(1, "gauss_blur", d.IMG, d.B9, d.W9, R, C, d.R9)
+        H.dep(2, 0)
+        H.k(2, "unsharp", d.IMG, d.B5, d.S, d.ALPHA, n)
+        H.k(0, "sobel", d.B5, d.E5, R, C)
+        H.k(1, "sobel", d.B9, d.E9, R, C)
+        H.k(0, "minmax", d.E5, d.MM5, d.SC5, n)
+        H.k(1, "minmax", d.E9, d.MM9, d.SC9, n)
+        H.k(0, "extend", d.E5, d.MM5, n)
+        H.k(1, "extend", d.E9, d.MM9, n)
+        H.dep(0, 1)
+        H.dep(0, 2)
+        H.k(0, "combine", d.S, d.B5, d.B9, d.E5, d.E9, d.OUT, n)
+
+
+class MlSpec(Spec):
+    name = "ML"
+
+    def build(self, ctx):
+        d = self.W.MlDag(ctx, 100_000)
+        d.load(*self.data["ml"])
+        return d
+
+    def step(self, d):
+        d.launch_all()
+
+    def hand(self, d, ctx, H):
+        r, f, k = d.rows, d.feats, d.classes
+        H.k(0, "dense_scores", d.XA, d.T1A, d.b1A, d.S1A, r, f, k)
+        H.k(1, "dense_scores", d.XA, d.T2A, d.b2A, d.S2A, r, f, k)
+        H.k(0, "row_softmax", d.S1A, r, k)
+        H.k(1, "row_softmax", d.S2A, r, k)
+        H.dep(0, 1)
+        H.k(0, "argmax_combine", d.S1A, d.S2A, d.LA, r, k)
+
+
+class HitsSpec(Spec):
+    name = "HITS"
+    ITERS = 5
+
+    def build(self, ctx):
+        csr, csc = self.data["hits"]
+        d = self.W.HitsDag(ctx, csr, csc)
+        d.run(iters=0, read=False)  # a = h = 1
+        return d
+
+    def step(self, d):
+        cur, nxt = ("a", "h"), ("a2", "h2")
+        for _ in range(self.ITERS):
+            d.iterate(cur[0], cur[1], nxt[0], nxt[1])
+            cur, nxt = nxt, cur
+
+    def hand(self, d, ctx, H):
+        n, nnz = d.n, d.nnz
+        cur, nxt = ("a", "h"), ("a2", "h2")
+        for it in range(self.ITERS):
+            if it:
+                H.dep(0, 1)  # s0 reads the hub vector s1 finished, and overwrites s1's input
+                H.dep(1, 0)
+            H.k(0, "spmv_csr", *d.ATA, d.V[cur[1]], d.PAT, d.V[nxt[0]], d.CAT, n, nnz)
+            H.k(1, "spmv_csr", *d.AA, d.V[cur[0]], d.PA, d.V[nxt[1]], d.CA, n, nnz)
+            H.k(0, "l2norm", d.V[nxt[0]], d.NA, d.SA, n)
+            H.k(1, "l2norm", d.V[nxt[1]], d.NH, d.SH, n)
+            H.k(0, "scale", d.V[nxt[0]], d.NA, n)
+            H.k(1, "scale", d.V[nxt[1]], d.NH, n)
+            cur, nxt = nxt, cur
+        H.dep(0, 1)
+
+
+class Hand:
+    """Explicit multi-stream schedule for stream capture: every stream forks
+    from the capture stream and joins back into it."""
+
+    def __init__(self, torch, ctx, nstreams, cap):
+        self.torch, self.ctx, self.cap = torch, ctx, cap
+        self.s = [torch.cuda.Stream() for _ in range(nstreams)]
+        fork = torch.cuda.Event()
+        fork.record(cap)
+        for st in self.s:
+            st.wait_event(fork)
+
+    def k(self, i, name, *args):
+        self.ctx.launch_raw(name, *args, stream=self.s[i].cuda_stream)
+
+    def copy(self, i, dst, src):
+        with self.torch.cuda.stream(self.s[i]):
+            dst.copy_(src, non_blocking=True)
+
+    def dep(self, to, frm):
+        ev = self.torch.cuda.Event()
+        ev.record(self.s[frm])
+        self.s[to].wait_event(ev)
+
+    def join(self):
+        for st in self.s:
+            ev = self.torch.cuda.Event()
+            ev.record(st)
+            self.cap.wait_event(ev)
+
+
+def make_data(datagen, which):
+    import numpy as np
+    import torch
+    data = {}
+    if "bs" in which:
+        data["bs"] = datagen.bs_inputs(N_OPTS, count=N_VEC, seed=1)
+    if "vec" in which:
+        data["vec"] = datagen.vec_inputs(1_000_000, seed=0)
+    if "img" in which:
+        data["img"] = torch.from_numpy(datagen.image(4096, 4096, seed=2).reshape(-1)).cuda()
+    if "ml" in which:
+        data["ml"] = datagen.ml_inputs(100_000, feats=1024, classes=10, seed=3)
+    if "hits" in which:
+        data["hits"] = datagen.hits_graph(10_000_000, 50_000_000, seed=4)
+    return data
+
+
+def measure_dag(torch, G, spec, steps, peak_gbs, link):
+    """Makespan per DAG under each policy and as a hand-built CUDA Graph,
+    the critical-path and resource bounds."""
+    s0 = torch.cuda.Stream()
+    out = {}
+
+    def timed_ctx(policy):
+        ctx = G.Context(policy=policy)
+        obj = spec.build(ctx)
+        for _ in range(3):
+            spec.step(obj)
+        ctx.sync()
+        torch.cuda.synchronize()
+        if policy == G.GDAG_POLICY_SERIAL_SYNC:
+            t0 = time.perf_counter()
+            for _ in range(steps):
+                spec.step(obj)
+            ctx.sync()
+            ms = (time.perf_counter() - t0) * 1e3 / steps
+        else:
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(s0)
+            ctx.fork(s0.cuda_stream)
+            for _ in range(steps):
+                spec.step(obj)
+            ctx.wait_all(s0.cuda_stream)
+            e1.record(s0)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / steps
+        ctx.sync()
+        return ctx, obj, ms
+
+    ctx, obj, out["parallel"] = timed_ctx(G.GDAG_POLICY_PARALLEL)
+    streams_used = ctx.stats()["streams"]
+    c2, o2, out["serial_async_one_stream"] = timed_ctx(G.GDAG_POLICY_SERIAL_ASYNC)
+    c2.close()
+    del o2
+    c3, o3, out["serial_sync"] = timed_ctx(G.GDAG_POLICY_SERIAL_SYNC)
+    c3.close()
+    del o3
+
+    # hand-built CUDA Graph of the same DAG
+    g = torch.cuda.CUDAGraph()
+    cap = torch.cuda.Stream()
+    torch.cuda.synchronize()
+    with torch.cuda.graph(g, stream=cap):
+        H = Hand(torch, ctx, 10 if spec.name == "B&S" else 3, cap)
+        spec.hand(obj, ctx, H)
+        H.join()
+    for _ in range(3):
+        g.replay()
+    torch.cuda.synchronize()
+    cur = torch.cuda.current_stream()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    torch.cuda.synchronize()
-    e0.record(stream)
-    for _ in range(steps):
-        fn()
-    e1.record(stream)
-    torch.cuda.synchronize()
-    return e0.elapsed_time(e1)
+    if spec.host_sync:
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            g.replay()
+            torch.cuda.synchronize()  # the host reads the result each step
+        out["hand_cuda_graph"] = (time.perf_counter() - t0) * 1e3 / steps
+    else:
+        e0.record(cur)
+        for _ in range(steps):
+            g.replay()
+        e1.record(cur)
+        torch.cuda.synchronize()
+        out["hand_cuda_graph"] = e0.elapsed_time(e1) / steps
+    del g
+
+    # critical path from solo node times along the library's own edges
+    lctx = G.Context(record_log=True)
+    rec = Recorder(lctx)
+    lobj = spec.build(rec)
+    lctx.sync()
+    first = len(rec.log)
+    spec.step(lobj)
+    lctx.sync()
+    elems = rec.log
+    st = torch.cuda.Stream()
+    solo_cache = {}
+
+    def solo(e):
+        kind = e[0]
+        if kind == "k":
+            key = (e[1],) + tuple(getattr(x, "handle", x) for x in e[2])
+            if key not in solo_cache:
+                for _ in range(2):
+                    lctx.launch_raw(e[1], *e[2], stream=st.cuda_stream)
+                a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a0.record(st)
+                for _ in range(5):
+                    lctx.launch_raw(e[1], *e[2], stream=st.cuda_stream)
+                a1.record(st)
+                torch.cuda.synchronize()
+                solo_cache[key] = a0.elapsed_time(a1) / 5
+            return solo_cache[key]
+        nb = e[2]
+        return nb / (link[kind] * 1e9) * 1e3
+    weights = [solo(e) if i >= first else 0.0 for i, e in enumerate(elems)]
+    edges = [(s, d) for s, d, _a, _k in lctx.edges()]
+    from paper_2012_09646_gb300.analysis import critical_path
+    cp = critical_path(weights, edges)
+    hbm = sum(alg_bytes(e[1], [getattr(x, "handle", x) for x in e[2]]) for e in elems[first:] if e[0] == "k")
+    h2d = sum(e[2] for e in elems[first:] if e[0] == "h2d")
+    d2h = sum(e[2] for e in elems[first:] if e[0] == "d2h")
+    res = max(cp, hbm / (peak_gbs * 1e9) * 1e3, h2d / (link["h2d"] * 1e9) * 1e3, d2h / (link["d2h"] * 1e9) * 1e3)
+    out["critical_path_bound"] = cp
+    out["resource_bound"] = res
+    out["sum_solo"] = sum(weights)
+    lctx.close()
+    ctx.close()
+    kern = sum(1 for e in elems[first:] if e[0] == "k")
+    return {
+        "makespan_ms": out, "nodes": len(elems) - first, "kernels": kern, "streams": streams_used,
+        "algorithmic_hbm_bytes": hbm, "h2d_bytes": h2d, "d2h_bytes": d2h,
+        "speedup_vs_serial_async": out["serial_async_one_stream"] / out["parallel"],
+        "speedup_vs_serial_sync": out["serial_sync"] / out["parallel"],
+        "vs_hand_cuda_graph": out["hand_cuda_graph"] / out["parallel"],
+        "frac_of_cp_bound": cp / out["parallel"], "frac_of_resource_bound": res / out["parallel"],
+        "launches_per_step": kern,
+    }
 
 
 def run_ours(args, rank, world, local_rank):
@@ -202,8 +567,9 @@ def run_ours(args, rank, world, local_rank):
     import __graft_entry__
     __graft_entry__.build()
     import datagen
+    from paper_2012_09646_gb300 import analysis
     from paper_2012_09646_gb300 import gdag as G
-    from paper_2012_09646_gb300.workloads import BsDag
+    from paper_2012_09646_gb300 import workloads as W
 
     dev = torch.device("cuda", local_rank)
     torch.cuda.set_device(dev)
@@ -216,20 +582,18 @@ def run_ours(args, rank, world, local_rank):
         if dist:
             dist.barrier()
 
-    prices = datagen.bs_inputs(N_OPTS, count=N_VEC, seed=1 + rank)
+    which = ["bs"] + (["vec", "img", "ml", "hits"] if args.dags == "all" and rank == 0 else [])
+    data = make_data(datagen, which)
+    prices = data["bs"]
     s0 = torch.cuda.Stream()
     K, r, sg, T = BS_PARAMS
+    peaks, peak_src = measured_peaks()
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
 
-    # ---- headline: PARALLEL policy, inputs resident in HBM
+    # ---- headline: B&S under the PARALLEL policy, inputs resident in HBM
     ctx = G.Context(device=local_rank, policy=G.GDAG_POLICY_PARALLEL)
-    dag = BsDag(ctx, N_OPTS, count=N_VEC, host=False)
+    dag = W.BsDag(ctx, N_OPTS, count=N_VEC, host=False)
     dag.load_device(prices)
-
-    def par_step():
-        dag.step_resident()
-
-    # clocks are sampled from before the warm-up to the end of the GPU work
-    # (the timed region alone is shorter than nvidia-smi's sampling period)
     try:
         uuid = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
     except Exception:
@@ -237,7 +601,7 @@ def run_ours(args, rank, world, local_rank):
     clocks = ClockSampler(local_rank, uuid)
     clocks.__enter__()
     for _ in range(args.warmup):
-        par_step()
+        dag.step_resident()
     ctx.sync()
     torch.cuda.synchronize()
     barrier()
@@ -245,7 +609,7 @@ def run_ours(args, rank, world, local_rank):
     e0.record(s0)
     ctx.fork(s0.cuda_stream)
     for _ in range(args.steps):
-        par_step()
+        dag.step_resident()
     ctx.wait_all(s0.cuda_stream)
     e1.record(s0)
     torch.cuda.synchronize()
@@ -261,66 +625,7 @@ def run_ours(args, rank, world, local_rank):
     out = None
     if rank == 0:
         nsteps_other = max(5, args.steps // 2)
-
-        # ---- serial single stream (asynchronous) and serial synchronous
-        def serial_ms(policy):
-            c = G.Context(device=local_rank, policy=policy)
-            d = BsDag(c, N_OPTS, count=N_VEC, host=False)
-            d.S = dag.S  # same resident inputs
-            d.SA = [c.array(t) for t in dag.S]
-            for _ in range(3):
-                d.step_resident()
-            c.sync()
-            torch.cuda.synchronize()
-            if policy == G.GDAG_POLICY_SERIAL_SYNC:
-                t0 = time.perf_counter()
-                for _ in range(nsteps_other):
-                    d.step_resident()
-                c.sync()
-                ms = (time.perf_counter() - t0) * 1e3 / nsteps_other
-            else:
-                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                e0.record(s0)
-                c.fork(s0.cuda_stream)
-                for _ in range(nsteps_other):
-                    d.step_resident()
-                c.wait_all(s0.cuda_stream)
-                e1.record(s0)
-                torch.cuda.synchronize()
-                ms = e0.elapsed_time(e1) / nsteps_other
-            c.sync()
-            c.close()
-            return ms
-
-        ms_serial_async = serial_ms(G.GDAG_POLICY_SERIAL_ASYNC)
-        ms_serial_sync = serial_ms(G.GDAG_POLICY_SERIAL_SYNC)
-
-        # ---- hand-built CUDA Graph: ten streams forked from one, joined back
-        side = [torch.cuda.Stream() for _ in range(N_VEC)]
-        g = torch.cuda.CUDAGraph()
-        cap = torch.cuda.Stream()
-        torch.cuda.synchronize()
-        with torch.cuda.graph(g, stream=cap):
-            fork = torch.cuda.Event()
-            fork.record(cap)
-            joins = []
-            for i in range(N_VEC):
-                side[i].wait_event(fork)
-                ctx.launch_raw("bs_call", dag.SA[i], dag.CA[i], N_OPTS, K, r, sg, T, stream=side[i].cuda_stream)
-                ev = torch.cuda.Event()
-                ev.record(side[i])
-                joins.append(ev)
-            for ev in joins:
-                cap.wait_event(ev)
-        for _ in range(3):
-            g.replay()
-        torch.cuda.synchronize()
-        ms_graph = time_device(torch, g.replay, nsteps_other, torch.cuda.current_stream()) / nsteps_other
-
-        # ---- solo node time (critical path: all nodes independent, so the
-        # longest path is one node) and the dominant kernel's roofline: the
-        # kernel alone on one stream, 20 launches back to back between two
-        # events (the queue stays full, so host launch latency is hidden)
+        # ---- the dominant kernel alone: bs_call, 20 launches back to back
         st = torch.cuda.Stream()
         for i in range(3):
             ctx.launch_raw("bs_call", dag.SA[i], dag.CA[i], N_OPTS, K, r, sg, T, stream=st.cuda_stream)
@@ -334,16 +639,35 @@ def run_ours(args, rank, world, local_rank):
         a1.record(st)
         torch.cuda.synchronize()
         ms_solo = a0.elapsed_time(a1) / reps
-        peaks, peak_src = measured_peaks()
-        hbm = float(peaks.get("hbm_gbs", 6800.0))
         bytes_launch = BYTES_PER_OPTION * N_OPTS
         achieved = bytes_launch / (ms_solo * 1e-3) / 1e9
-        ms_cp = ms_solo
-        ms_res = max(ms_cp, N_VEC * bytes_launch / (hbm * 1e9) * 1e3)
+
+        # ---- host link bandwidths (copy engines), for the transfer bounds
+        link = {}
+        hb = torch.empty(N_OPTS, dtype=torch.float32, pin_memory=True)
+        db = torch.empty(N_OPTS, dtype=torch.float32, device=dev)
+        for kind, (dst, src) in (("h2d", (db, hb)), ("d2h", (hb, db))):
+            dst.copy_(src, non_blocking=True)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for _ in range(3):
+                dst.copy_(src, non_blocking=True)
+            torch.cuda.synchronize()
+            link[kind] = 3 * 4 * N_OPTS / (time.perf_counter() - t0) / 1e9
+        del hb, db
+
+        # ---- every DAG of the suite: policies, hand-built CUDA Graph, bounds
+        specs = [BsSpec(G, W, data)]
+        if args.dags == "all":
+            specs += [VecSpec(G, W, data), ImgSpec(G, W, data), MlSpec(G, W, data), HitsSpec(G, W, data)]
+        dags = {}
+        for sp in specs:
+            dags[sp.name] = measure_dag(torch, G, sp, nsteps_other, hbm, link)
+        bsm = dags["B&S"]["makespan_ms"]
 
         # ---- e2e through the public API with host buffers
         ctx2 = G.Context(device=local_rank, policy=G.GDAG_POLICY_PARALLEL)
-        d2 = BsDag(ctx2, N_OPTS, count=N_VEC, host=True)
+        d2 = W.BsDag(ctx2, N_OPTS, count=N_VEC, host=True)
         d2.load_host(prices)
         for _ in range(2):
             d2.step_e2e()
@@ -355,19 +679,30 @@ def run_ours(args, rank, world, local_rank):
             d2.step_e2e()
         ms_e2e = (time.perf_counter() - t0) * 1e3 / n_e2e
         ctx2.sync()
-        # results are the oracle's on a sample (a cheap guard, not the parity test)
         from oracle import numeric as N
         idx = np.arange(0, N_OPTS, 997)
         ref = N.bs_call(prices[3][idx], K, r, sg, T)
         got = d2.hC[3].numpy()[idx].astype(np.float64)
         e2e_err = float((np.abs(got - ref) / np.maximum(np.abs(ref), 1.0)).max())
         ctx2.close()
-
+        # one traced e2e step: copy/compute overlap (Section IV-F)
+        ctx3 = G.Context(device=local_rank, trace=True)
+        d3 = W.BsDag(ctx3, N_OPTS, count=N_VEC, host=True)
+        d3.load_host(prices)
+        d3.step_e2e()
+        ctx3.sync()
+        tr = ctx3.trace()
+        comp = [(t[3], t[4]) for t in tr if t[1] == G.GDAG_NODE_KERNEL]
+        tran = [(t[3], t[4]) for t in tr if t[1] != G.GDAG_NODE_KERNEL]
+        overlap = analysis.overlap_metrics(comp, tran)
+        ctx3.close()
         clocks.__exit__(None, None, None)
+
         # ---- CPU oracle baseline (bounded sample)
         cpu_val, cpu_samples, cpu_s = cpu_oracle_rate(args.cpu_seconds)
 
         value = world * 1e3 / ms_all
+        gpu_launches = args.steps * N_VEC
         out = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_all, "higher_is_better": True, "scaling": "weak",
@@ -375,24 +710,25 @@ def run_ours(args, rank, world, local_rank):
             "config": {"workload": WORKLOAD, "policy": "PARALLEL (run-time DAG, multi-stream)",
                        "l2": "inputs larger than L2 (800 MB touched per step)",
                        "parallelism": "replicas" if world > 1 else "single GPU"},
-            "makespan_ms": {"parallel": ms_par, "serial_async_one_stream": ms_serial_async,
-                            "serial_sync": ms_serial_sync, "hand_cuda_graph": ms_graph,
-                            "critical_path_bound": ms_cp, "resource_bound": ms_res},
-            "speedup_vs_serial_async": ms_serial_async / ms_par,
-            "speedup_vs_serial_sync": ms_serial_sync / ms_par,
-            "vs_hand_cuda_graph": ms_graph / ms_par,
-            "frac_of_cp_bound": ms_cp / ms_par, "frac_of_resource_bound": ms_res / ms_par,
+            "makespan_ms": dict(bsm, parallel_headline=ms_par),
+            "speedup_vs_serial_async": bsm["serial_async_one_stream"] / ms_par,
+            "speedup_vs_serial_sync": bsm["serial_sync"] / ms_par,
+            "vs_hand_cuda_graph": bsm["hand_cuda_graph"] / ms_par,
+            "frac_of_cp_bound": bsm["critical_path_bound"] / ms_par,
+            "frac_of_resource_bound": bsm["resource_bound"] / ms_par,
             "roofline": {"kernel": "bs_call", "bound": "hbm", "achieved": achieved, "peak": hbm,
                          "peak_source": peak_src + " hbm_gbs (burst; kernel timed alone)", "unit": "GB/s",
                          "frac": achieved / hbm, "traffic": None,
                          "algorithmic_bytes_per_launch": bytes_launch, "launch_ms": ms_solo},
             "e2e": {"value": 1e3 / ms_e2e, "unit": UNIT, "ms_per_step": ms_e2e,
                     "h2d_bytes_per_step": N_VEC * 4 * N_OPTS, "d2h_bytes_per_step": N_VEC * 4 * N_OPTS,
-                    "max_rel_err_sampled": e2e_err},
+                    "max_rel_err_sampled": e2e_err, "overlap": overlap,
+                    "link_gbs": link, "link_bound_ms": N_VEC * 4 * N_OPTS / (min(link.values()) * 1e9) * 1e3},
+            "dags": dags,
             "cpu_baseline": {"value": cpu_val, "unit": UNIT, "cores": 1, "kind": "oracle",
                              "sample": "%d samples of 10 x 1e6 options (fp64 C oracle, one thread) in %.1f s; "
                                        "scaled to whole DAGs" % (cpu_samples, cpu_s)},
-            "gpu_launches": args.steps * N_VEC,
+            "gpu_launches": gpu_launches,
             "clocks": dict(clocks.summary(), window="warm-up through the last GPU measurement"),
         }
     clocks.__exit__(None, None, None)
@@ -404,8 +740,52 @@ def run_ours(args, rank, world, local_rank):
         print(json.dumps(out), flush=True)
 
 
+def run_profile(args):
+    """One DAG, one PARALLEL context, warm-up plus --steps steps, nothing
+    else on the device (a few GB at most)."""
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    import datagen
+    from paper_2012_09646_gb300 import gdag as G
+    from paper_2012_09646_gb300 import workloads as W
+    torch.cuda.set_device(0)
+    ctx = G.Context()
+    if args.profile == "bs":
+        d = W.BsDag(ctx, N_OPTS, count=N_VEC, host=False)
+        d.load_device(datagen.bs_inputs(N_OPTS, count=N_VEC, seed=1))
+        step = d.step_resident
+    elif args.profile == "vec":
+        d = W.VecDag(ctx, 1_000_000)
+        d.load(*datagen.vec_inputs(1_000_000, seed=0))
+        step = d.step
+    elif args.profile == "img":
+        n = args.img_size
+        d = W.ImgDag(ctx, n, n)
+        d.img.copy_(torch.from_numpy(datagen.image(n, n, seed=2).reshape(-1)).cuda())
+        step = d.launch_all
+    elif args.profile == "ml":
+        d = W.MlDag(ctx, 100_000)
+        d.load(*datagen.ml_inputs(100_000, feats=1024, classes=10, seed=3))
+        step = d.launch_all
+    else:
+        d = W.HitsDag(ctx, *datagen.hits_graph(10_000_000, 50_000_000, seed=4))
+        d.run(iters=0, read=False)
+        spec = HitsSpec(G, W, {})
+        step = lambda: spec.step(d)
+    for _ in range(args.warmup + args.steps):
+        step()
+    ctx.sync()
+    torch.cuda.synchronize()
+    ctx.close()
+
+
 def main():
     args = parse()
+    if args.profile:
+        run_profile(args)
+        return
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))

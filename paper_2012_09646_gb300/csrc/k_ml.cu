@@ -171,17 +171,26 @@ template <int NC4> int scores_launch(const LaunchArgs &a, cudaStream_t s)
     const int rows = a.i32(4), feats = a.i32(5), classes = a.i32(6);
     if (rows == 0) return cudaSuccess;
     const size_t smem = dense_smem(feats, classes);
-    static bool configured = false;  // per process; the attribute is per function
+    // per process: raise the dynamic shared-memory limit once and remember
+    // the occupancy of the last table size (no device queries on later
+    // launches, so the launch can be stream-captured)
+    static bool configured = false;
+    static size_t occ_smem = 0;
+    static int occ_blocks = 0;
     if (!configured) {
         cudaError_t e = cudaFuncSetAttribute(dense_scores_kernel<NC4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              200 * 1024);
         if (e != cudaSuccess) return e;
         configured = true;
     }
-    int per_sm = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, dense_scores_kernel<NC4>, kMlThreads, smem);
-    if (e != cudaSuccess) return e;
-    if (per_sm < 1) per_sm = 1;
+    if (occ_smem != smem) {
+        int per_sm = 0;
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, dense_scores_kernel<NC4>, kMlThreads, smem);
+        if (e != cudaSuccess) return e;
+        occ_blocks = per_sm < 1 ? 1 : per_sm;
+        occ_smem = smem;
+    }
+    const int per_sm = occ_blocks;
     const int64_t groups = ceil_div(rows, 8 * (kMlThreads / 32));
     int64_t grid = (int64_t)sm_count() * per_sm;
     if (grid > groups) grid = groups;
