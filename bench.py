@@ -49,6 +49,8 @@ def parse():
                     help="run only --steps steps of one DAG through the library (a small, "
                          "single-context command for ncu captures); prints nothing")
     ap.add_argument("--img-size", type=int, default=4096)
+    ap.add_argument("--serve", type=int, default=1, help="run the serving benchmark (with --dags all)")
+    ap.add_argument("--serve-seconds", type=float, default=1.0, help="seconds of Poisson arrivals per rate")
     return ap.parse_args()
 
 
@@ -259,12 +261,20 @@ class Spec:
     """One benchmark DAG: build(ctx) -> program object; step(obj) issues one
     DAG through the library; hand(obj, ctx, H) issues the same DAG by hand on
     explicit streams (the CUDA Graph baseline); host_sync: whether each step
-    ends with the host reading a result."""
+    ends with the host reading a result.  capture_step / after_replay: the
+    part of a step that can be recorded as a graph, and what follows each
+    replay (the host read)."""
     name = ""
     host_sync = False
 
     def __init__(self, G, W, data):
         self.G, self.W, self.data = G, W, data
+
+    def capture_step(self, obj):
+        self.step(obj)
+
+    def after_replay(self, ctx, obj):
+        pass
 
 
 class BsSpec(Spec):
@@ -295,6 +305,12 @@ class VecSpec(Spec):
 
     def step(self, d):
         d.step(read=True)
+
+    def capture_step(self, d):
+        d.step(read=False)
+
+    def after_replay(self, ctx, d):
+        ctx.read(d.Z)
 
     def hand(self, d, ctx, H):
         n = d.n
@@ -471,6 +487,24 @@ def measure_dag(torch, G, spec, steps, peak_gbs, link):
 
     ctx, obj, out["parallel"] = timed_ctx(G.GDAG_POLICY_PARALLEL)
     streams_used = ctx.stats()["streams"]
+    # the same DAG captured once by the library and replayed as one element
+    gid = ctx.capture(lambda: spec.capture_step(obj))
+    for _ in range(3):
+        ctx.replay(gid)
+        spec.after_replay(ctx, obj)
+    ctx.sync()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(s0)
+    ctx.fork(s0.cuda_stream)
+    for _ in range(steps):
+        ctx.replay(gid)
+        spec.after_replay(ctx, obj)
+    ctx.wait_all(s0.cuda_stream)
+    e1.record(s0)
+    torch.cuda.synchronize()
+    out["library_graph"] = e0.elapsed_time(e1) / steps
+    ctx.drop_graph(gid)
     c2, o2, out["serial_async_one_stream"] = timed_ctx(G.GDAG_POLICY_SERIAL_ASYNC)
     c2.close()
     del o2
@@ -555,6 +589,7 @@ def measure_dag(torch, G, spec, steps, peak_gbs, link):
         "speedup_vs_serial_async": out["serial_async_one_stream"] / out["parallel"],
         "speedup_vs_serial_sync": out["serial_sync"] / out["parallel"],
         "vs_hand_cuda_graph": out["hand_cuda_graph"] / out["parallel"],
+        "library_graph_vs_hand_cuda_graph": out["hand_cuda_graph"] / out["library_graph"],
         "frac_of_cp_bound": cp / out["parallel"], "frac_of_resource_bound": res / out["parallel"],
         "launches_per_step": kern,
     }
@@ -665,6 +700,23 @@ def run_ours(args, rank, world, local_rank):
             dags[sp.name] = measure_dag(torch, G, sp, nsteps_other, hbm, link)
         bsm = dags["B&S"]["makespan_ms"]
 
+        # ---- serving: Poisson streams of DAG requests on one context
+        serve_out = None
+        if args.dags == "all" and args.serve:
+            from paper_2012_09646_gb300 import serve as SV
+            scales = [0.125, 0.25, 0.5, 1.0]
+            inputs = SV.Inputs(datagen, scales, full=data)
+            serve_out = {"kinds": list(SV.KINDS), "scale_buckets": scales,
+                         "budget_gb": 40, "response_bytes_max": SV.RESPONSE_BYTES, "runs": []}
+            for rate in (2000.0, 1000.0):
+                srv = SV.Server(inputs)
+                srv.warm()
+                reqs = SV.poisson_requests(rate, int(rate * args.serve_seconds), scales, seed=7)
+                srv.run(reqs)
+                srv.close()
+                serve_out["runs"].append(dict(SV.latency_summary(reqs), offered_req_s=rate))
+            del inputs
+
         # ---- e2e through the public API with host buffers
         ctx2 = G.Context(device=local_rank, policy=G.GDAG_POLICY_PARALLEL)
         d2 = W.BsDag(ctx2, N_OPTS, count=N_VEC, host=True)
@@ -725,6 +777,7 @@ def run_ours(args, rank, world, local_rank):
                     "max_rel_err_sampled": e2e_err, "overlap": overlap,
                     "link_gbs": link, "link_bound_ms": N_VEC * 4 * N_OPTS / (min(link.values()) * 1e9) * 1e3},
             "dags": dags,
+            "serve": serve_out,
             "cpu_baseline": {"value": cpu_val, "unit": UNIT, "cores": 1, "kind": "oracle",
                              "sample": "%d samples of 10 x 1e6 options (fp64 C oracle, one thread) in %.1f s; "
                                        "scaled to whole DAGs" % (cpu_samples, cpu_s)},

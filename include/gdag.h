@@ -78,10 +78,12 @@ extern "C" {
 #define GDAG_NODE_HOST_READ  2  /* host read (device-to-host copy if needed) */
 #define GDAG_NODE_EXTERNAL   3  /* library call given the chosen stream     */
 #define GDAG_NODE_HOST_PREFETCH 4 /* device-to-host copy ahead of a read    */
+#define GDAG_NODE_GRAPH      5  /* replay of a captured CUDA graph          */
 
 typedef struct gdag_ctx gdag_ctx;
 typedef int32_t gdag_array;   /* array handle, >= 0                          */
 typedef int32_t gdag_kernel;  /* kernel handle, >= 0                         */
+typedef int32_t gdag_graph;   /* captured graph handle, >= 0                 */
 
 typedef struct {
     uint32_t x, y, z;
@@ -192,8 +194,11 @@ typedef struct {
 void gdag_options_default(gdag_options *o);
 
 /* Create a context.  opts may be NULL (defaults).  With the CUDA backend the
- * device is made current; streams are created lazily (non-blocking streams,
- * owned by the library).  Errors: INVALID, CUDA, OOM. */
+ * device is made current; streams are created lazily and owned by the
+ * library.  They are ordinary (blocking) streams, so device work the caller
+ * issued on the legacy default stream before an element (for example a fill
+ * of a freshly allocated scratch array) is ordered before it.  Errors:
+ * INVALID, CUDA, OOM. */
 int gdag_create(gdag_ctx **out, const gdag_options *opts);
 
 /* Wait for all work (bounded by timeout_ms), then free every library-owned
@@ -312,6 +317,13 @@ int gdag_launch_external(gdag_ctx *ctx, void (*fn)(void *stream, void *user),
 /* Wait for every stream (bounded) and retire every node. */
 int gdag_sync(gdag_ctx *ctx);
 
+/* Non-blocking: *done = 1 if node's work has completed (it and its
+ * ancestors are then retired, as after a host wait), 0 if it is still
+ * running.  Lets a dispatcher poll many in-flight DAGs without blocking on
+ * any (Section III-B: results become available when the host asks).
+ * Errors: INVALID (unknown node, or while capturing), CUDA. */
+int gdag_node_query(gdag_ctx *ctx, int64_t node, int32_t *done);
+
 /* Make the caller's CUDA stream wait for all work issued so far, without
  * blocking the host (a join for timing events or stream capture). */
 int gdag_stream_wait_all(gdag_ctx *ctx, void *stream);
@@ -319,6 +331,34 @@ int gdag_stream_wait_all(gdag_ctx *ctx, void *stream);
 /* Make every pool stream wait for the caller's stream's work issued so far
  * (a fork: later nodes run after it). */
 int gdag_stream_fork(gdag_ctx *ctx, void *stream);
+
+/* ------------------------------------------------ captured DAG shapes
+ * A program that repeats the same sequence of elements can record it once
+ * as a CUDA graph and replay it; the replay is one DAG element, so it mixes
+ * with dynamically scheduled elements.  (Section II names the up-front,
+ * static DAG of CUDA Graphs as the alternative the paper's scheduler avoids;
+ * this keeps the dynamic inference and adds replay of a shape that is known
+ * to repeat.)
+ *
+ * gdag_capture_begin waits for all work (as gdag_sync), then records instead
+ * of executing: every element issued until gdag_capture_end is inferred and
+ * placed on streams as usual, and its launches, copies, event records and
+ * waits become the nodes and edges of one graph.  While capturing, host
+ * reads, prefetches, waits, syncs and unregistering return GDAG_ERR_INVALID,
+ * and host writes must copy from the array's host view (src NULL): a replay
+ * copies whatever the view holds at replay time.  Needs an asynchronous
+ * policy.  gdag_capture_end instantiates the graph; nothing captured has
+ * run.  Errors: INVALID, CUDA. */
+int gdag_capture_begin(gdag_ctx *ctx);
+int gdag_capture_end(gdag_ctx *ctx, gdag_graph *out);
+
+/* Replay graph g as one DAG element whose accesses are the union of the
+ * captured elements' accesses (edges, stream choice and waits as for a
+ * kernel).  The arrays must still be registered. */
+int gdag_graph_launch(gdag_ctx *ctx, gdag_graph g, int64_t *node_out);
+
+/* Wait for all work, then free graph g. */
+int gdag_graph_destroy(gdag_ctx *ctx, gdag_graph g);
 
 /* ---------------------------------------------------------- inspection */
 
@@ -364,9 +404,10 @@ size_t gdag_scratch_bytes(const char *kernel, int64_t n);
  *     stream first.  Calls whose kernels overlap on the GPU (different
  *     streams, or different host threads, without ordering) race on the
  *     array: order them on one stream or with events.
- *   - The array holds 1024 partial sums; a request that would need more
- *     (a device with more than 512 multiprocessors), a negative n, or a NULL
- *     pointer is rejected with GDAG_ERR_INVALID before anything is enqueued.
+ *   - The array holds 1024 partial sums, the most any launch of this
+ *     reduction uses (its grid is capped at 1024 blocks); a request that
+ *     would need more, a negative n, or a NULL pointer is rejected with
+ *     GDAG_ERR_INVALID before anything is enqueued.
  *   - Returns GDAG_ERR_CUDA if the set-up or the launch fails. */
 #define GDAG_NOALLOC_SCRATCH_BYTES 16384
 int gdag_vec_reduce_diff_noalloc(const void *dev_x, const void *dev_y,

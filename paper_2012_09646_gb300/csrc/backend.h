@@ -40,6 +40,11 @@ class Backend {
     virtual int copy_h2d(void *dst, const void *src, size_t bytes, void *s) = 0;
     virtual int copy_d2h(void *dst, const void *src, size_t bytes, void *s) = 0;
     virtual int external(void (*fn)(void *, void *), void *user, void *s) = 0;
+    // Stream capture into a CUDA graph and its replay.
+    virtual int capture_begin(void *s) = 0;
+    virtual int capture_end(void *s, void **exec) = 0;  // instantiated graph
+    virtual int graph_launch(void *exec, void *s) = 0;
+    virtual int graph_destroy(void *exec) = 0;
     virtual int host_alloc(void **p, size_t bytes) = 0;
     virtual int host_free(void *p) = 0;
     virtual bool is_fake() const = 0;

@@ -55,8 +55,11 @@ class CudaBackend final : public Backend {
     }
     int stream_create(void **s) override
     {
+        // blocking streams: device work the caller put on the legacy default
+        // stream (allocation fills, copies by the framework that owns the
+        // memory) is ordered before anything issued here afterwards
         cudaStream_t st;
-        int r = chk(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking), "cudaStreamCreate");
+        int r = chk(cudaStreamCreateWithFlags(&st, cudaStreamDefault), "cudaStreamCreate");
         if (!r) *s = st;
         return r;
     }
@@ -124,6 +127,26 @@ class CudaBackend final : public Backend {
         fn(s, user);
         return chk(cudaGetLastError(), "external call");
     }
+    int capture_begin(void *s) override
+    {
+        return chk(cudaStreamBeginCapture((cudaStream_t)s, cudaStreamCaptureModeThreadLocal), "cudaStreamBeginCapture");
+    }
+    int capture_end(void *s, void **exec) override
+    {
+        cudaGraph_t g = nullptr;
+        int r = chk(cudaStreamEndCapture((cudaStream_t)s, &g), "cudaStreamEndCapture");
+        if (r) return r;
+        cudaGraphExec_t ge = nullptr;
+        r = chk(cudaGraphInstantiate(&ge, g, 0), "cudaGraphInstantiate");
+        cudaGraphDestroy(g);
+        if (!r) *exec = ge;
+        return r;
+    }
+    int graph_launch(void *exec, void *s) override
+    {
+        return chk(cudaGraphLaunch((cudaGraphExec_t)exec, (cudaStream_t)s), "cudaGraphLaunch");
+    }
+    int graph_destroy(void *exec) override { return chk(cudaGraphExecDestroy((cudaGraphExec_t)exec), "cudaGraphExecDestroy"); }
     int host_alloc(void **p, size_t bytes) override
     {
         return chk(cudaHostAlloc(p, bytes ? bytes : 1, cudaHostAllocPortable), "cudaHostAlloc");
@@ -177,6 +200,14 @@ class FakeBackend final : public Backend {
     int copy_h2d(void *, const void *, size_t, void *) override { return op(); }
     int copy_d2h(void *, const void *, size_t, void *) override { return op(); }
     int external(void (*)(void *, void *), void *, void *) override { return op(); }
+    int capture_begin(void *) override { return BE_OK; }
+    int capture_end(void *, void **exec) override
+    {
+        *exec = (void *)(uintptr_t)(0x200000 + next_++);
+        return BE_OK;
+    }
+    int graph_launch(void *, void *) override { return op(); }
+    int graph_destroy(void *) override { return BE_OK; }
     int host_alloc(void **p, size_t bytes) override
     {
         *p = std::malloc(bytes ? bytes : 1);

@@ -18,75 +18,171 @@
 namespace gdag {
 
 constexpr int kTileW = 64, kTileH = 32;   // output tile of one 256-thread block
-constexpr int kTx = 64, kTy = 4;          // block shape
+constexpr int kImgThreads = 256;
 constexpr int kMaxRadius = 8;
 
 __device__ __forceinline__ int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
 
-// Separable Gaussian blur with radius R: horizontal pass from the staged
-// input into shared memory, vertical pass from there to the output.  Per
-// output: 2(2R+1) FMAs; DRAM: one read and one write of the image.
-template <int R>
-__global__ void __launch_bounds__(kTx *kTy) gauss_blur_kernel(const float *__restrict__ in, float *__restrict__ out,
-                                                              const float *__restrict__ w, int rows, int cols)
+// Stage rows y0-R .. y0+kTileH+R-1 and columns x0-HALO .. x0+kTileW+HALO-1 of
+// the image into s (row stride IW = kTileW + 2 HALO, HALO a multiple of 4),
+// clamping coordinates to the image.  Interior blocks of an image whose
+// rows are 16-byte aligned use 128-bit loads; border blocks clamp per pixel.
+template <int R, int HALO, int IW>
+__device__ __forceinline__ void stage_tile(const float *__restrict__ in, float *s, int rows, int cols, int x0, int y0)
 {
-    constexpr int IW = kTileW + 2 * R, IH = kTileH + 2 * R;
-    __shared__ float s_in[IH][IW];
-    __shared__ float s_h[IH][kTileW];
-    __shared__ float s_w[2 * R + 1];
-    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * kTx + tx;
+    constexpr int IH = kTileH + 2 * R;
+    const bool fast = (cols & 3) == 0 && (reinterpret_cast<uintptr_t>(in) & 15) == 0 && x0 >= HALO &&
+                      x0 + kTileW + HALO <= cols;
+    if (fast) {
+        constexpr int V = IW / 4;  // float4 per staged row
+        constexpr int PER = (IH * V + kImgThreads - 1) / kImgThreads;
+        float4 v[PER];  // every load of the thread in flight before any store
+#pragma unroll
+        for (int k = 0; k < PER; ++k) {
+            const int i = threadIdx.x + k * kImgThreads;
+            if (i < IH * V) {
+                const int r = i / V, c4 = i - r * V;
+                const int y = clampi(y0 + r - R, 0, rows - 1);
+                v[k] = *reinterpret_cast<const float4 *>(in + (size_t)y * cols + (x0 - HALO) + 4 * c4);
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < PER; ++k) {
+            const int i = threadIdx.x + k * kImgThreads;
+            if (i < IH * V) {
+                const int r = i / V, c4 = i - r * V;
+                *reinterpret_cast<float4 *>(s + r * IW + 4 * c4) = v[k];
+            }
+        }
+    } else {
+        for (int i = threadIdx.x; i < IH * IW; i += kImgThreads) {
+            const int r = i / IW, c = i - r * IW;
+            const int y = clampi(y0 + r - R, 0, rows - 1);
+            s[r * IW + c] = in[(size_t)y * cols + clampi(x0 + c - HALO, 0, cols - 1)];
+        }
+    }
+}
+
+// Store two rows of four outputs (x .. x+3, rows y, y+1) with bounds checks.
+__device__ __forceinline__ void store_2x4(float *__restrict__ out, int rows, int cols, int x, int y, float4 a, float4 b)
+{
+    const bool vec = (cols & 3) == 0 && (reinterpret_cast<uintptr_t>(out) & 15) == 0 && x + 3 < cols;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int yy = y + h;
+        if (yy >= rows) break;
+        const float4 v = h ? b : a;
+        float *o = out + (size_t)yy * cols + x;
+        if (vec) {
+            *reinterpret_cast<float4 *>(o) = v;
+        } else {
+            if (x < cols) o[0] = v.x;
+            if (x + 1 < cols) o[1] = v.y;
+            if (x + 2 < cols) o[2] = v.z;
+            if (x + 3 < cols) o[3] = v.w;
+        }
+    }
+}
+
+// Separable Gaussian blur with radius R.  Horizontal pass: each thread makes
+// four adjacent outputs of one staged row from 4 + 2R inputs (packed fp32x2
+// FMAs); vertical pass: each thread makes a 4-column x 2-row block from
+// 2 + 2R rows of the horizontal result.  Per output 2(2R+1) FMAs and about
+// one 32-bit shared-memory access; DRAM: one read and one write of the image.
+template <int R>
+__global__ void __launch_bounds__(kImgThreads) gauss_blur_kernel(const float *__restrict__ in, float *__restrict__ out,
+                                                                 const float *__restrict__ w, int rows, int cols)
+{
+    constexpr int HALO = (R + 3) / 4 * 4;
+    constexpr int IW = kTileW + 2 * HALO, IH = kTileH + 2 * R;
+    __shared__ __align__(16) float s_in[IH * IW];
+    __shared__ __align__(16) float s_h[IH * kTileW];
+    float wr[2 * R + 1];
+#pragma unroll
+    for (int k = 0; k <= 2 * R; ++k) wr[k] = w[k];
     const int x0 = blockIdx.x * kTileW, y0 = blockIdx.y * kTileH;
-    if (tid < 2 * R + 1) s_w[tid] = w[tid];
-    for (int r = ty; r < IH; r += kTy) {
-        const size_t row = (size_t)clampi(y0 + r - R, 0, rows - 1) * cols;
-        for (int c = tx; c < IW; c += kTx) s_in[r][c] = in[row + clampi(x0 + c - R, 0, cols - 1)];
+    stage_tile<R, HALO, IW>(in, s_in, rows, cols, x0, y0);
+    __syncthreads();
+    // horizontal: IH rows x 16 groups of four columns
+    for (int t = threadIdx.x; t < IH * (kTileW / 4); t += kImgThreads) {
+        const int r = t >> 4, g = t & 15;
+        const float *row = s_in + r * IW + 4 * g;  // inputs 4g .. 4g + 4 + 2 HALO
+        float v[4 + 2 * HALO];
+#pragma unroll
+        for (int k = 0; k < (4 + 2 * HALO) / 4; ++k) {
+            const float4 q = reinterpret_cast<const float4 *>(row)[k];
+            v[4 * k] = q.x;
+            v[4 * k + 1] = q.y;
+            v[4 * k + 2] = q.z;
+            v[4 * k + 3] = q.w;
+        }
+        float2 lo = make_float2(0.f, 0.f), hi = lo;  // outputs (0,1) and (2,3)
+#pragma unroll
+        for (int k = 0; k <= 2 * R; ++k) {
+            const float2 wk = make_float2(wr[k], wr[k]);
+            const int o = HALO - R + k;
+            lo = __ffma2_rn(wk, make_float2(v[o], v[o + 1]), lo);
+            hi = __ffma2_rn(wk, make_float2(v[o + 2], v[o + 3]), hi);
+        }
+        reinterpret_cast<float4 *>(s_h + r * kTileW)[g] = make_float4(lo.x, lo.y, hi.x, hi.y);
     }
     __syncthreads();
-    for (int r = ty; r < IH; r += kTy) {
-        float acc = 0.f;
+    // vertical: 16 column groups x 16 row pairs, one block per thread
+    const int g = threadIdx.x & 15, rp = threadIdx.x >> 4;
+    float4 col[2 + 2 * R];
 #pragma unroll
-        for (int k = 0; k <= 2 * R; ++k) acc = fmaf(s_w[k], s_in[r][tx + k], acc);
-        s_h[r][tx] = acc;
-    }
-    __syncthreads();
-    const int x = x0 + tx;
-    if (x >= cols) return;
-    for (int r = ty; r < kTileH; r += kTy) {
-        const int y = y0 + r;
-        if (y >= rows) break;
-        float acc = 0.f;
+    for (int k = 0; k < 2 + 2 * R; ++k) col[k] = reinterpret_cast<const float4 *>(s_h + (2 * rp + k) * kTileW)[g];
+    float2 a01 = make_float2(0.f, 0.f), a23 = a01, b01 = a01, b23 = a01;
 #pragma unroll
-        for (int k = 0; k <= 2 * R; ++k) acc = fmaf(s_w[k], s_h[r + k][tx], acc);
-        out[(size_t)y * cols + x] = acc;
+    for (int k = 0; k <= 2 * R; ++k) {
+        const float2 wk = make_float2(wr[k], wr[k]);
+        a01 = __ffma2_rn(wk, make_float2(col[k].x, col[k].y), a01);
+        a23 = __ffma2_rn(wk, make_float2(col[k].z, col[k].w), a23);
+        b01 = __ffma2_rn(wk, make_float2(col[k + 1].x, col[k + 1].y), b01);
+        b23 = __ffma2_rn(wk, make_float2(col[k + 1].z, col[k + 1].w), b23);
     }
+    store_2x4(out, rows, cols, x0 + 4 * g, y0 + 2 * rp, make_float4(a01.x, a01.y, a23.x, a23.y),
+              make_float4(b01.x, b01.y, b23.x, b23.y));
 }
 
 // Sobel magnitude: gx = right column - left column with weights (1, 2, 1),
 // gy = bottom row - top row with weights (1, 2, 1); out = sqrt(gx^2 + gy^2).
-__global__ void __launch_bounds__(kTx *kTy) sobel_kernel(const float *__restrict__ in, float *__restrict__ out,
-                                                         int rows, int cols)
+// Each thread makes a 4-column x 2-row block from a 6 x 4 window.
+__global__ void __launch_bounds__(kImgThreads) sobel_kernel(const float *__restrict__ in, float *__restrict__ out,
+                                                            int rows, int cols)
 {
-    constexpr int IW = kTileW + 2, IH = kTileH + 2;
-    __shared__ float s[IH][IW];
-    const int tx = threadIdx.x, ty = threadIdx.y;
+    constexpr int HALO = 4, IW = kTileW + 2 * HALO, IH = kTileH + 2;
+    __shared__ __align__(16) float s[IH * IW];
     const int x0 = blockIdx.x * kTileW, y0 = blockIdx.y * kTileH;
-    for (int r = ty; r < IH; r += kTy) {
-        const size_t row = (size_t)clampi(y0 + r - 1, 0, rows - 1) * cols;
-        for (int c = tx; c < IW; c += kTx) s[r][c] = in[row + clampi(x0 + c - 1, 0, cols - 1)];
-    }
+    stage_tile<1, HALO, IW>(in, s, rows, cols, x0, y0);
     __syncthreads();
-    const int x = x0 + tx;
-    if (x >= cols) return;
-    for (int r = ty; r < kTileH; r += kTy) {
-        const int y = y0 + r;
-        if (y >= rows) break;
-        const float a = s[r][tx], b = s[r][tx + 1], c = s[r][tx + 2];
-        const float d = s[r + 1][tx], f = s[r + 1][tx + 2];
-        const float g = s[r + 2][tx], h = s[r + 2][tx + 1], i = s[r + 2][tx + 2];
-        const float gx = (c + 2.f * f + i) - (a + 2.f * d + g);
-        const float gy = (g + 2.f * h + i) - (a + 2.f * b + c);
-        out[(size_t)y * cols + x] = sqrtf(gx * gx + gy * gy);
-    }
+    const int g = threadIdx.x & 15, rp = threadIdx.x >> 4;
+    float m[4][12];  // staged rows 2rp .. 2rp+3, columns 4g .. 4g+11 (pixel 4g+c-HALO)
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const float4 q = reinterpret_cast<const float4 *>(s + (2 * rp + r) * IW + 4 * g)[k];
+            m[r][4 * k] = q.x;
+            m[r][4 * k + 1] = q.y;
+            m[r][4 * k + 2] = q.z;
+            m[r][4 * k + 3] = q.w;
+        }
+    float o[2][4];
+#pragma unroll
+    for (int h = 0; h < 2; ++h)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int c = HALO + j;  // the output pixel's column in m
+            const float a = m[h][c - 1], b = m[h][c], cc = m[h][c + 1];
+            const float d = m[h + 1][c - 1], f = m[h + 1][c + 1];
+            const float gg = m[h + 2][c - 1], hh = m[h + 2][c], i = m[h + 2][c + 1];
+            const float gx = (cc + 2.f * f + i) - (a + 2.f * d + gg);
+            const float gy = (gg + 2.f * hh + i) - (a + 2.f * b + cc);
+            o[h][j] = sqrtf(gx * gx + gy * gy);
+        }
+    store_2x4(out, rows, cols, x0 + 4 * g, y0 + 2 * rp, make_float4(o[0][0], o[0][1], o[0][2], o[0][3]),
+              make_float4(o[1][0], o[1][1], o[1][2], o[1][3]));
 }
 
 // (min, max) of n floats -> mm[0], mm[1].  Exact (min and max round
@@ -314,7 +410,7 @@ template <int R> void blur_launch(const LaunchArgs &a, cudaStream_t s)
 {
     int rows = a.i32(3), cols = a.i32(4);
     dim3 g((unsigned)ceil_div(cols, kTileW), (unsigned)ceil_div(rows, kTileH));
-    gauss_blur_kernel<R><<<g, dim3(kTx, kTy), 0, s>>>(a.p<float>(0), a.p<float>(1), a.p<float>(2), rows, cols);
+    gauss_blur_kernel<R><<<g, kImgThreads, 0, s>>>(a.p<float>(0), a.p<float>(1), a.p<float>(2), rows, cols);
 }
 
 int launch_blur(const LaunchArgs &a, void *sv)
@@ -345,7 +441,7 @@ int launch_sobel(const LaunchArgs &a, void *s)
 {
     int rows = a.i32(2), cols = a.i32(3);
     dim3 g((unsigned)ceil_div(cols, kTileW), (unsigned)ceil_div(rows, kTileH));
-    sobel_kernel<<<g, dim3(kTx, kTy), 0, (cudaStream_t)s>>>(a.p<float>(0), a.p<float>(1), rows, cols);
+    sobel_kernel<<<g, kImgThreads, 0, (cudaStream_t)s>>>(a.p<float>(0), a.p<float>(1), rows, cols);
     return cudaGetLastError();
 }
 

@@ -49,51 +49,82 @@ __global__ void __launch_bounds__(kMlThreads) dense_scores_kernel(const int *__r
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int q = lane & 3;            // quarter of the features
-    const int rsub = lane >> 2;        // row within the warp's group of 8
+    const int rsub = lane >> 2;        // rows rsub and rsub + 8 of the warp's 16
     const int warps_total = gridDim.x * (kMlThreads / 32);
     const float4 *tq = reinterpret_cast<const float4 *>(st + q * qs);
-    for (int row0 = (blockIdx.x * (kMlThreads / 32) + warp) * 8; row0 < rows; row0 += warps_total * 8) {
-        const int row = row0 + rsub;
-        const bool live = row < rows;
-        float2 acc[NC4 * 2];
+    for (int row0 = (blockIdx.x * (kMlThreads / 32) + warp) * 16; row0 < rows; row0 += warps_total * 16) {
+        const int ra = row0 + rsub, rb = ra + 8;
+        const bool la = ra < rows, lb = rb < rows;
+        float2 acc_a[NC4 * 2], acc_b[NC4 * 2];
 #pragma unroll
-        for (int k = 0; k < NC4 * 2; ++k) acc[k] = make_float2(0.f, 0.f);
-        const int4 *xr = reinterpret_cast<const int4 *>(X + (size_t)(live ? row : 0) * feats + q * fq);
+        for (int k = 0; k < NC4 * 2; ++k) acc_a[k] = acc_b[k] = make_float2(0.f, 0.f);
+        const int4 *xa = reinterpret_cast<const int4 *>(X + (size_t)(la ? ra : 0) * feats + q * fq);
+        const int4 *xb = reinterpret_cast<const int4 *>(X + (size_t)(lb ? rb : 0) * feats + q * fq);
+        const int4 zero = make_int4(0, 0, 0, 0);
+        // software pipeline: the next 8 features of both rows are in flight
+        // while the current 8 are multiplied
+        int4 a0 = la ? xa[0] : zero, a1 = la ? xa[1] : zero;
+        int4 b0 = lb ? xb[0] : zero, b1 = lb ? xb[1] : zero;
         for (int f0 = 0; f0 < fq; f0 += kMlFeatStep) {
-            int4 a = make_int4(0, 0, 0, 0), b = a;
-            if (live) {
-                a = xr[f0 / 4];
-                b = xr[f0 / 4 + 1];
+            const int nf = f0 + kMlFeatStep;
+            int4 na0 = zero, na1 = zero, nb0 = zero, nb1 = zero;
+            if (nf < fq) {
+                if (la) {
+                    na0 = xa[nf / 4];
+                    na1 = xa[nf / 4 + 1];
+                }
+                if (lb) {
+                    nb0 = xb[nf / 4];
+                    nb1 = xb[nf / 4 + 1];
+                }
             }
-            const int xv[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+            const int va[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+            const int vb[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
 #pragma unroll
             for (int j = 0; j < 8; ++j) {
-                const float x = __int2float_rn(xv[j]);
-                const float2 xx = make_float2(x, x);
+                const float fa = __int2float_rn(va[j]), fb = __int2float_rn(vb[j]);
+                const float2 xxa = make_float2(fa, fa), xxb = make_float2(fb, fb);
                 const float4 *trow = tq + (f0 + j) * NC4;
 #pragma unroll
                 for (int k = 0; k < NC4; ++k) {
                     const float4 t = trow[k];
-                    acc[2 * k] = __ffma2_rn(xx, make_float2(t.x, t.y), acc[2 * k]);
-                    acc[2 * k + 1] = __ffma2_rn(xx, make_float2(t.z, t.w), acc[2 * k + 1]);
+                    const float2 t01 = make_float2(t.x, t.y), t23 = make_float2(t.z, t.w);
+                    acc_a[2 * k] = __ffma2_rn(xxa, t01, acc_a[2 * k]);
+                    acc_a[2 * k + 1] = __ffma2_rn(xxa, t23, acc_a[2 * k + 1]);
+                    acc_b[2 * k] = __ffma2_rn(xxb, t01, acc_b[2 * k]);
+                    acc_b[2 * k + 1] = __ffma2_rn(xxb, t23, acc_b[2 * k + 1]);
                 }
             }
+            a0 = na0;
+            a1 = na1;
+            b0 = nb0;
+            b1 = nb1;
         }
         // combine the four quarters: (q0 + q1) + (q2 + q3), same order on
         // every run
 #pragma unroll
         for (int k = 0; k < NC4 * 2; ++k) {
-            acc[k].x += __shfl_xor_sync(0xffffffffu, acc[k].x, 1);
-            acc[k].y += __shfl_xor_sync(0xffffffffu, acc[k].y, 1);
-            acc[k].x += __shfl_xor_sync(0xffffffffu, acc[k].x, 2);
-            acc[k].y += __shfl_xor_sync(0xffffffffu, acc[k].y, 2);
+            acc_a[k].x += __shfl_xor_sync(0xffffffffu, acc_a[k].x, 1);
+            acc_a[k].y += __shfl_xor_sync(0xffffffffu, acc_a[k].y, 1);
+            acc_a[k].x += __shfl_xor_sync(0xffffffffu, acc_a[k].x, 2);
+            acc_a[k].y += __shfl_xor_sync(0xffffffffu, acc_a[k].y, 2);
+            acc_b[k].x += __shfl_xor_sync(0xffffffffu, acc_b[k].x, 1);
+            acc_b[k].y += __shfl_xor_sync(0xffffffffu, acc_b[k].y, 1);
+            acc_b[k].x += __shfl_xor_sync(0xffffffffu, acc_b[k].x, 2);
+            acc_b[k].y += __shfl_xor_sync(0xffffffffu, acc_b[k].y, 2);
         }
-        if (live && q == 0) {
-            float *out = S + (size_t)row * classes;
+        if (q == 0) {
 #pragma unroll
-            for (int k = 0; k < NC4 * 2; ++k) {
-                if (2 * k < classes) out[2 * k] = bias[2 * k] + acc[k].x;
-                if (2 * k + 1 < classes) out[2 * k + 1] = bias[2 * k + 1] + acc[k].y;
+            for (int h = 0; h < 2; ++h) {
+                const int row = h ? rb : ra;
+                if (!(h ? lb : la)) continue;
+                const float2 *acc = h ? acc_b : acc_a;
+                float *out = S + (size_t)row * classes;
+#pragma unroll
+                for (int k = 0; k < NC4 * 2; ++k) {
+                    if (2 * k < classes) out[2 * k] = bias[2 * k] + acc[k].x;
+                    if (2 * k + 1 < classes) out[2 * k + 1] = bias[2 * k + 1] + acc[k].y;
+                }
             }
         }
     }
@@ -191,7 +222,7 @@ template <int NC4> int scores_launch(const LaunchArgs &a, cudaStream_t s)
         occ_smem = smem;
     }
     const int per_sm = occ_blocks;
-    const int64_t groups = ceil_div(rows, 8 * (kMlThreads / 32));
+    const int64_t groups = ceil_div(rows, 16 * (kMlThreads / 32));
     int64_t grid = (int64_t)sm_count() * per_sm;
     if (grid > groups) grid = groups;
     dense_scores_kernel<NC4><<<(unsigned)grid, kMlThreads, smem, s>>>(a.p<int>(0), a.p<float>(1), a.p<float>(2),

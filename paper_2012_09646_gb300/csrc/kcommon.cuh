@@ -44,7 +44,7 @@ constexpr int kReduceMaxBlocks = 1024;
 inline unsigned reduce_grid(int64_t n_vec4)
 {
     int64_t tiles = ceil_div(n_vec4 > 0 ? n_vec4 : 1, (int64_t)kThreads * kUnroll);
-    int64_t cap = (int64_t)sm_count() * 2;
+    int64_t cap = (int64_t)sm_count() * 6;  // enough bytes in flight per SM
     if (cap > kReduceMaxBlocks) cap = kReduceMaxBlocks;
     return (unsigned)(tiles < cap ? tiles : cap);
 }

@@ -124,6 +124,28 @@ struct Ctx {
     // scratch for one element
     std::vector<int64_t> par;
 
+    // stream capture (CUDA graphs of a repeated DAG shape)
+    bool capturing = false;
+    void *cap_stream = nullptr;
+    std::vector<Access> cap_access;  // union of the captured elements' accesses
+    struct Graph {
+        void *exec = nullptr;
+        std::vector<Access> access;
+        bool live = false;
+    };
+    std::vector<Graph> graphs;
+
+    void capture_note(const Access *acc, int n)
+    {
+        if (!capturing) return;
+        for (int i = 0; i < n; ++i) {
+            size_t j = 0;
+            while (j < cap_access.size() && cap_access[j].array != acc[i].array) ++j;
+            if (j == cap_access.size()) cap_access.push_back(acc[i]);
+            else cap_access[j].bits |= acc[i].bits;
+        }
+    }
+
     // ------------------------------------------------------------- errors
     int fail(int code, const char *fmt, ...)
     {
@@ -143,7 +165,7 @@ struct Ctx {
 
     void log_op(int type, int stream, int event, int64_t node)
     {
-        if (opt.record_log) op_log.push_back(gdag_op{type, stream, event, 0, node});
+        if (opt.record_log && !capturing) op_log.push_back(gdag_op{type, stream, event, 0, node});
     }
 
     // ------------------------------------------------------------- nodes
@@ -207,6 +229,7 @@ struct Ctx {
     {
         Node *n = node(id);
         if (!n || !n->active) return GDAG_OK;
+        if (capturing) return fail(GDAG_ERR_INVALID, "a host wait is not possible while capturing");
         if (n->event < 0) {
             retire(id);
             return GDAG_OK;
@@ -261,6 +284,10 @@ struct Ctx {
         s.handle = h;
         streams.push_back(s);
         *out = (int32_t)streams.size() - 1;
+        if (capturing) {  // a stream created during capture joins it
+            int rr = fork_from(cap_stream, h);
+            if (rr) return rr;
+        }
         if (opt.trace && !t0) {
             int rr = be->event_create(&t0, true);
             if (rr) return be_fail(rr, "event create");
@@ -355,10 +382,23 @@ struct Ctx {
         if (opt.record_log) node_log.push_back(gdag_node_info{next_id() - 1, kind, -1});
     }
 
+    // Make stream `to` wait for the work issued so far on `from`.
+    int fork_from(void *from, void *to)
+    {
+        void *e;
+        int r = be->event_create(&e, false);
+        if (r) return be_fail(r, "event create");
+        r = be->event_record(e, from);
+        if (!r) r = be->stream_wait(to, e);
+        be->event_destroy(e);
+        if (r) return be_fail(r, "fork");
+        return GDAG_OK;
+    }
+
     // Optionally retire completed parents without a host wait.
     int retire_done_parents()
     {
-        if (!opt.retire_by_query) return GDAG_OK;
+        if (!opt.retire_by_query || capturing) return GDAG_OK;
         for (int64_t p : par) {
             Node *n = node(p);
             if (!n || !n->active || n->event < 0) continue;
@@ -592,6 +632,13 @@ int gdag_destroy(gdag_ctx *c)
             if (r && !rc) rc = r;
         }
     }
+    if (c->capturing) {
+        void *exec = nullptr;
+        if (!c->be->capture_end(c->cap_stream, &exec) && exec) c->be->graph_destroy(exec);
+    }
+    for (auto &g : c->graphs)
+        if (g.live) c->be->graph_destroy(g.exec);
+    if (c->cap_stream) c->be->stream_destroy(c->cap_stream);
     for (auto &a : c->arrays)
         if (a.live && a.host_owned) c->be->host_free(a.host);
     for (void *e : c->events) c->be->event_destroy(e);
@@ -645,6 +692,7 @@ int gdag_array_unregister(gdag_ctx *c, gdag_array a)
     if (!c) return GDAG_ERR_INVALID;
     ArrayState *s = c->arr(a);
     if (!s) return c->fail(GDAG_ERR_INVALID, "unknown array %d", a);
+    if (c->capturing) return c->fail(GDAG_ERR_INVALID, "not allowed while capturing");
     if (!c->poisoned) {
         std::vector<int64_t> users = s->readers;
         if (s->writer >= 0) users.push_back(s->writer);
@@ -770,6 +818,7 @@ int gdag_launch(gdag_ctx *c, gdag_kernel k, gdag_dim3 grid, gdag_dim3 block, siz
     int nacc;
     r = resolve(c, k, grid, block, smem, args, nargs, la, acc, &nacc);
     if (r) return r;
+    c->capture_note(acc, nacc);
     int64_t id = c->next_id();
     c->infer(id, acc, nacc);
     for (int i = 0; i < nacc; ++i)
@@ -824,6 +873,7 @@ int gdag_launch_external(gdag_ctx *c, void (*fn)(void *, void *), void *user, co
         if (j == nacc) acc[nacc++] = Access{arrays[i], bits};
         else acc[j].bits |= bits;
     }
+    c->capture_note(acc, nacc);
     int64_t id = c->next_id();
     c->infer(id, acc, nacc);
     for (int i = 0; i < nacc; ++i)
@@ -847,6 +897,7 @@ int gdag_array_host(gdag_ctx *c, gdag_array a, int32_t mode, void **out)
     if (!c || !out) return GDAG_ERR_INVALID;
     int r = c->guard();
     if (r) return r;
+    if (c->capturing) return c->fail(GDAG_ERR_INVALID, "not allowed while capturing");
     ArrayState *s = c->arr(a);
     if (!s) return c->fail(GDAG_ERR_INVALID, "unknown array %d", a);
     r = c->ensure_host(*s);
@@ -877,11 +928,14 @@ int gdag_array_write(gdag_ctx *c, gdag_array a, const void *src, size_t off, siz
     if (r) return r;
     char *view = static_cast<char *>(s->host) + off;
     if (src && src != view) {
+        if (c->capturing)
+            return c->fail(GDAG_ERR_INVALID, "while capturing, a host write copies from the host view (src NULL)");
         r = c->release_view(*s);
         if (r) return r;
         std::memcpy(view, src, bytes);
     }
     Access acc{a, gdag::W_BIT};
+    c->capture_note(&acc, 1);
     int64_t id = c->next_id();
     c->infer(id, &acc, 1);
     bool full = off == 0 && bytes == s->bytes;
@@ -910,6 +964,7 @@ int gdag_array_read(gdag_ctx *c, gdag_array a, void *dst, size_t off, size_t byt
     if (!c) return GDAG_ERR_INVALID;
     int r = c->guard();
     if (r) return r;
+    if (c->capturing) return c->fail(GDAG_ERR_INVALID, "not allowed while capturing");
     ArrayState *s = c->arr(a);
     if (!s) return c->fail(GDAG_ERR_INVALID, "unknown array %d", a);
     if (off > s->bytes || bytes > s->bytes - off)
@@ -959,6 +1014,7 @@ int gdag_array_prefetch_host(gdag_ctx *c, gdag_array a, size_t off, size_t bytes
     if (!c) return GDAG_ERR_INVALID;
     int r = c->guard();
     if (r) return r;
+    if (c->capturing) return c->fail(GDAG_ERR_INVALID, "not allowed while capturing");
     ArrayState *s = c->arr(a);
     if (!s) return c->fail(GDAG_ERR_INVALID, "unknown array %d", a);
     if (off > s->bytes || bytes > s->bytes - off)
@@ -996,6 +1052,7 @@ int gdag_sync(gdag_ctx *c)
     if (!c) return GDAG_ERR_INVALID;
     int r = c->guard();
     if (r) return r;
+    if (c->capturing) return c->fail(GDAG_ERR_INVALID, "not allowed while capturing");
     for (size_t s = 0; s < c->streams.size(); ++s) {
         if (c->streams[s].active == 0) continue;
         c->log_op(GDAG_OP_STREAM_SYNC, (int)s, -1, -1);
@@ -1028,6 +1085,7 @@ int gdag_stream_wait_all(gdag_ctx *c, void *stream)
     if (!c) return GDAG_ERR_INVALID;
     int r = c->guard();
     if (r) return r;
+    if (c->capturing) return c->fail(GDAG_ERR_INVALID, "not allowed while capturing");
     for (size_t s = 0; s < c->streams.size(); ++s) {
         gdag::Node *n = c->node(c->streams[s].tail);
         if (!n || !n->active || n->event < 0) continue;
@@ -1042,6 +1100,7 @@ int gdag_stream_fork(gdag_ctx *c, void *stream)
     if (!c) return GDAG_ERR_INVALID;
     int r = c->guard();
     if (r) return r;
+    if (c->capturing) return c->fail(GDAG_ERR_INVALID, "not allowed while capturing");
     if (c->streams.empty()) return GDAG_OK;
     void *e;
     r = c->be->event_create(&e, false);
@@ -1084,6 +1143,142 @@ int gdag_trace_export(gdag_ctx *c, gdag_trace_rec *buf, size_t cap, size_t *n)
         ++k;
     }
     *n = k;
+    return GDAG_OK;
+}
+
+
+
+int gdag_node_query(gdag_ctx *c, int64_t node, int32_t *done)
+{
+    if (!c || !done) return GDAG_ERR_INVALID;
+    int r = c->guard();
+    if (r) return r;
+    if (c->capturing) return c->fail(GDAG_ERR_INVALID, "not allowed while capturing");
+    if (node < 0 || node >= c->next_id()) return c->fail(GDAG_ERR_INVALID, "unknown node %lld", (long long)node);
+    gdag::Node *n = c->node(node);
+    if (!n || !n->active) {  // retired, or dropped after a sync
+        *done = 1;
+        return GDAG_OK;
+    }
+    if (n->event < 0) {
+        *done = 0;
+        return GDAG_OK;
+    }
+    const int q = c->be->event_query(c->events[(size_t)n->event]);
+    if (q == gdag::BE_NOT_READY) {
+        *done = 0;
+        return GDAG_OK;
+    }
+    if (q != gdag::BE_OK) return c->be_fail(q, "event query");
+    c->log_op(GDAG_OP_QUERY_DONE, n->stream, n->event, node);
+    c->retire(node);
+    *done = 1;
+    return GDAG_OK;
+}
+
+int gdag_capture_begin(gdag_ctx *c)
+{
+    if (!c) return GDAG_ERR_INVALID;
+    int r = c->guard();
+    if (r) return r;
+    if (c->capturing) return c->fail(GDAG_ERR_INVALID, "a capture is already open");
+    if (c->opt.policy == GDAG_POLICY_SERIAL_SYNC)
+        return c->fail(GDAG_ERR_INVALID, "capture needs an asynchronous policy");
+    r = gdag_sync(c);  // no parent from before the capture can remain active
+    if (r) return r;
+    if (!c->cap_stream) {
+        r = c->be->stream_create(&c->cap_stream);
+        if (r) return c->be_fail(r, "stream create");
+    }
+    r = c->be->capture_begin(c->cap_stream);
+    if (r) return c->be_fail(r, "capture begin");
+    c->capturing = true;
+    c->cap_access.clear();
+    for (auto &st : c->streams) {
+        r = c->fork_from(c->cap_stream, st.handle);
+        if (r) return r;
+    }
+    return GDAG_OK;
+}
+
+int gdag_capture_end(gdag_ctx *c, gdag_graph *out)
+{
+    if (!c || !out) return GDAG_ERR_INVALID;
+    if (!c->capturing) return c->fail(GDAG_ERR_INVALID, "no capture is open");
+    int r = GDAG_OK;
+    for (auto &st : c->streams) {  // every stream joins back into the origin
+        r = c->fork_from(st.handle, c->cap_stream);
+        if (r) break;
+    }
+    void *exec = nullptr;
+    int rr = c->be->capture_end(c->cap_stream, &exec);
+    c->capturing = false;
+    // nothing captured has run: the captured nodes leave the frontier
+    c->retire_all();
+    if (!c->opt.record_log && !c->opt.trace) {
+        c->base = c->next_id();
+        c->nodes.clear();
+        c->parent_arena.clear();
+        for (auto &a : c->arrays) {
+            a.writer = -1;
+            a.readers.clear();
+            a.view_copy = -1;
+            a.prefetch = -1;
+        }
+        for (auto &st : c->streams) st.tail = -1;
+    }
+    if (r) return r;
+    if (rr) return c->be_fail(rr, "capture end");
+    Ctx::Graph g;
+    g.exec = exec;
+    g.access = c->cap_access;
+    g.live = true;
+    c->graphs.push_back(g);
+    *out = (gdag_graph)c->graphs.size() - 1;
+    return GDAG_OK;
+}
+
+int gdag_graph_launch(gdag_ctx *c, gdag_graph g, int64_t *node_out)
+{
+    if (!c) return GDAG_ERR_INVALID;
+    int r = c->guard();
+    if (r) return r;
+    if (c->capturing) return c->fail(GDAG_ERR_INVALID, "not allowed while capturing");
+    if (g < 0 || (size_t)g >= c->graphs.size() || !c->graphs[(size_t)g].live)
+        return c->fail(GDAG_ERR_INVALID, "unknown graph %d", g);
+    const Ctx::Graph &gr = c->graphs[(size_t)g];
+    for (const auto &a : gr.access)
+        if (!c->arr(a.array)) return c->fail(GDAG_ERR_INVALID, "graph uses unregistered array %d", a.array);
+    int64_t id = c->next_id();
+    c->infer(id, gr.access.data(), (int)gr.access.size());
+    for (const auto &a : gr.access)
+        if (a.bits & gdag::W_BIT) c->arrays[(size_t)a.array].host_valid = false;
+    c->push_node(GDAG_NODE_GRAPH);
+    if (node_out) *node_out = id;
+    int32_t s;
+    r = c->place(id, &s);
+    if (r) {
+        c->retire(id);
+        return r;
+    }
+    c->log_op(GDAG_OP_LAUNCH, s, -1, id);
+    r = c->be->graph_launch(gr.exec, c->streams[(size_t)s].handle);
+    if (r) return c->abort_node(id, r, "graph launch");
+    return c->finish(id, s);
+}
+
+int gdag_graph_destroy(gdag_ctx *c, gdag_graph g)
+{
+    if (!c) return GDAG_ERR_INVALID;
+    if (g < 0 || (size_t)g >= c->graphs.size() || !c->graphs[(size_t)g].live)
+        return c->fail(GDAG_ERR_INVALID, "unknown graph %d", g);
+    // a launched replay may still run: wait for every stream first
+    if (!c->poisoned) {
+        int r = gdag_sync(c);
+        if (r) return r;
+    }
+    c->be->graph_destroy(c->graphs[(size_t)g].exec);
+    c->graphs[(size_t)g] = Ctx::Graph();
     return GDAG_OK;
 }
 

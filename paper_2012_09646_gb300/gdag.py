@@ -42,6 +42,7 @@ GDAG_MODE_SIGNATURE = -1
 
 GDAG_EDGE_RAW, GDAG_EDGE_WAR, GDAG_EDGE_WAW = 0, 1, 2
 GDAG_NODE_KERNEL, GDAG_NODE_HOST_WRITE, GDAG_NODE_HOST_READ, GDAG_NODE_EXTERNAL, GDAG_NODE_HOST_PREFETCH = 0, 1, 2, 3, 4
+GDAG_NODE_GRAPH = 5
 GDAG_ARG_ARRAY, GDAG_ARG_SCALAR = 0, 1
 (GDAG_OP_LAUNCH, GDAG_OP_COPY_H2D, GDAG_OP_COPY_D2H, GDAG_OP_EXTERNAL, GDAG_OP_RECORD, GDAG_OP_WAIT,
  GDAG_OP_HOST_WAIT, GDAG_OP_STREAM_SYNC, GDAG_OP_HOST_NODE, GDAG_OP_QUERY_DONE) = range(10)
@@ -132,6 +133,11 @@ SIGNATURES = {
     "gdag_ops_export": (ctypes.c_int, [_ctx, _P(gdag_op), _sz, _P(_sz)]),
     "gdag_trace_export": (ctypes.c_int, [_ctx, _P(gdag_trace_rec), _sz, _P(_sz)]),
     "gdag_stats_get": (ctypes.c_int, [_ctx, _P(gdag_stats)]),
+    "gdag_node_query": (ctypes.c_int, [_ctx, _i64, _P(_i32)]),
+    "gdag_capture_begin": (ctypes.c_int, [_ctx]),
+    "gdag_capture_end": (ctypes.c_int, [_ctx, _P(_i32)]),
+    "gdag_graph_launch": (ctypes.c_int, [_ctx, _i32, _P(_i64)]),
+    "gdag_graph_destroy": (ctypes.c_int, [_ctx, _i32]),
     "gdag_scratch_bytes": (_sz, [ctypes.c_char_p, _i64]),
     "gdag_vec_reduce_diff_noalloc": (ctypes.c_int, [_vp, _vp, _vp, _i64, _vp]),
 }
@@ -302,6 +308,32 @@ def gdag_stats_get(ctx):
     return s
 
 
+def gdag_node_query(ctx, node):
+    d = _i32()
+    _check(ctx, lib().gdag_node_query(ctx, node, ctypes.byref(d)))
+    return bool(d.value)
+
+
+def gdag_capture_begin(ctx):
+    return _check(ctx, lib().gdag_capture_begin(ctx))
+
+
+def gdag_capture_end(ctx):
+    g = _i32()
+    _check(ctx, lib().gdag_capture_end(ctx, ctypes.byref(g)))
+    return g.value
+
+
+def gdag_graph_launch(ctx, g):
+    node = _i64()
+    _check(ctx, lib().gdag_graph_launch(ctx, g, ctypes.byref(node)))
+    return node.value
+
+
+def gdag_graph_destroy(ctx, g):
+    return _check(ctx, lib().gdag_graph_destroy(ctx, g))
+
+
 def gdag_scratch_bytes(kernel, n):
     return lib().gdag_scratch_bytes(kernel.encode(), n)
 
@@ -463,6 +495,28 @@ class Context:
         self._keep.append(cb)
         return gdag_launch_external(self.h, cb, user, [a.handle for a, _ in arrays_modes],
                                     [m for _, m in arrays_modes])
+
+    # captured DAG shapes
+    def capture(self, fn):
+        """Record fn() (which issues elements on this context) as a graph;
+        returns its handle."""
+        gdag_capture_begin(self.h)
+        try:
+            fn()
+        except BaseException:
+            gdag_capture_end(self.h)
+            raise
+        return gdag_capture_end(self.h)
+
+    def done(self, node):
+        """Non-blocking: has this node completed?"""
+        return gdag_node_query(self.h, node)
+
+    def replay(self, g):
+        return gdag_graph_launch(self.h, g)
+
+    def drop_graph(self, g):
+        gdag_graph_destroy(self.h, g)
 
     # sync and inspection
     def sync(self):

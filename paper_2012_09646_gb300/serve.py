@@ -1,0 +1,413 @@
+"""Serving loop over the run-time DAG scheduler.
+
+Requests are DAG programs (VEC, B&S, IMG+ML, HITS) scaled by a factor s, and
+they arrive as a Poisson stream.  One dispatcher thread does four things:
+
+* admits queued requests in arrival order while their working set fits the
+  HBM budget (continuous batching: a request admitted while others run simply
+  adds nodes to the same context; independent requests share no arrays, so
+  the scheduler puts them on separate streams and they overlap on the GPU);
+* issues each admitted request's elements without blocking, ending with a
+  device-to-host prefetch of the response;
+* polls in-flight requests with a non-blocking node query, reads the response
+  of each one that finished (served from the prefetched host view), and
+  releases its memory;
+* records each request's latency, from its arrival time to the moment its
+  response is on the host.
+
+Inputs that a request only reads (price books, images, feature matrices,
+graphs) are resident per scale bucket and shared by every request of that
+bucket.  A response is the head of the request's result (at most
+``RESPONSE_BYTES``); the rest of the result stays on the device.
+"""
+from __future__ import annotations
+
+import collections
+import math
+import time
+
+import numpy as np
+import torch
+
+from . import gdag as G
+from . import workloads as W
+
+KINDS = ("VEC", "B&S", "IMG+ML", "HITS")
+RESPONSE_BYTES = 64 * 1024
+F32 = torch.float32
+
+
+def bucket_scales(levels=7):
+    """Scale buckets 1/64, 1/32, ..., 1: a drawn s is rounded up to one."""
+    return [2.0 ** -k for k in range(levels - 1, -1, -1)]
+
+
+class Inputs:
+    """Read-only inputs per (kind, bucket), generated once and resident."""
+
+    def __init__(self, datagen, scales, kinds=KINDS, device="cuda", hits_full=(10_000_000, 50_000_000),
+                 full=None):
+        """``full``: already generated full-scale inputs to reuse for s = 1
+        (keys "bs", "img", "ml", "hits" as the benchmark builds them)."""
+        self.scales = scales
+        self.data = {}
+        full = full or {}
+        for s in scales:
+            if s == 1.0 and full:
+                self._from_full(full, kinds, device)
+                continue
+            if "VEC" in kinds:
+                n = max(1, int(1_000_000 * s))
+                x, y = datagen.vec_inputs(n, seed=10)
+                hx = torch.from_numpy(x).pin_memory()
+                hy = torch.from_numpy(y).pin_memory()
+                self.data[("VEC", s)] = {"n": n, "hx": hx, "hy": hy}
+            if "B&S" in kinds:
+                n = max(4, int(10_000_000 * s))
+                S = [torch.from_numpy(p).to(device) for p in datagen.bs_inputs(n, count=10, seed=11)]
+                self.data[("B&S", s)] = {"n": n, "S": S}
+            if "IMG+ML" in kinds:
+                side = max(8, int(4096 * math.sqrt(s)) // 8 * 8)
+                img = torch.from_numpy(datagen.image(side, side, seed=12).reshape(-1)).to(device)
+                rows = max(1, int(100_000 * s))
+                X, T1, b1, T2, b2 = datagen.ml_inputs(rows, feats=1024, classes=10, seed=13)
+                t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(device)
+                self.data[("IMG+ML", s)] = {"side": side, "img": img, "rows": rows, "X": t(X), "T1": t(T1),
+                                            "b1": t(b1), "T2": t(T2), "b2": t(b2)}
+            if "HITS" in kinds:
+                n = max(64, int(hits_full[0] * s))
+                nnz = max(64, int(hits_full[1] * s))
+                csr, csc = datagen.hits_graph(n, nnz, seed=14)
+                i32 = torch.int32
+                d = lambda a, dt: torch.from_numpy(np.ascontiguousarray(a)).to(dt).to(device)
+                self.data[("HITS", s)] = {"n": n, "nnz": nnz,
+                                          "A": (d(csr[0], i32), d(csr[1], i32), d(csr[2], F32)),
+                                          "AT": (d(csc[0], i32), d(csc[1], i32), d(csc[2], F32))}
+
+    def _from_full(self, full, kinds, device):
+        import datagen
+        t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(device)
+        if "VEC" in kinds:
+            x, y = datagen.vec_inputs(1_000_000, seed=10)
+            self.data[("VEC", 1.0)] = {"n": 1_000_000, "hx": torch.from_numpy(x).pin_memory(),
+                                       "hy": torch.from_numpy(y).pin_memory()}
+        if "B&S" in kinds:
+            self.data[("B&S", 1.0)] = {"n": full["bs"][0].size, "S": [t(p) for p in full["bs"]]}
+        if "IMG+ML" in kinds:
+            X, T1, b1, T2, b2 = full["ml"]
+            self.data[("IMG+ML", 1.0)] = {"side": 4096, "img": full["img"].to(device), "rows": X.shape[0],
+                                          "X": t(X), "T1": t(T1), "b1": t(b1), "T2": t(T2), "b2": t(b2)}
+        if "HITS" in kinds:
+            csr, csc = full["hits"]
+            i32 = torch.int32
+            d = lambda a, dt: torch.from_numpy(np.ascontiguousarray(a)).to(dt).to(device)
+            self.data[("HITS", 1.0)] = {"n": len(csr[0]) - 1, "nnz": int(csr[0][-1]),
+                                        "A": (d(csr[0], i32), d(csr[1], i32), d(csr[2], F32)),
+                                        "AT": (d(csc[0], i32), d(csc[1], i32), d(csc[2], F32))}
+
+    def bucket(self, s):
+        for b in self.scales:
+            if s <= b * (1 + 1e-12):
+                return b
+        return self.scales[-1]
+
+
+class Request:
+    __slots__ = ("rid", "kind", "scale", "arrival", "admitted", "done_at", "bytes", "final", "tensors", "arrays",
+                 "resp", "resp_view", "slot", "scratch", "need")
+
+    def __init__(self, rid, kind, scale, arrival):
+        self.rid, self.kind, self.scale, self.arrival = rid, kind, scale, arrival
+        self.admitted = self.done_at = None
+        self.bytes = 0
+        self.final = -1
+        self.tensors, self.arrays = [], []
+        self.resp = None
+        self.resp_view = None
+        self.slot = None
+        self.scratch = []
+        self.need = 0
+
+
+class Server:
+    """One gdag context shared by every request."""
+
+    def __init__(self, inputs, budget_bytes=40 << 30, max_streams=32, device="cuda"):
+        self.inp = inputs
+        self.budget = budget_bytes
+        self.used = 0
+        self.device = device
+        self.ctx = G.Context(max_streams=max_streams, retire_by_query=True)
+        self.shared = {}
+        self._slots = []  # pinned response buffers, reused
+        self._scratch_pool = {}
+        self.partitions = {}
+
+    # ---------------------------------------------------------- helpers
+    def _arr(self, r, t, host=None, name=None):
+        r.tensors.append(t)
+        a = self.ctx.array(t, host=host, name=name)
+        r.arrays.append(a)
+        r.bytes += t.numel() * t.element_size()
+        return a
+
+    def _shared(self, key, t):
+        """Register a resident read-only input once."""
+        k = (key, t.data_ptr())
+        if k not in self.shared:
+            self.shared[k] = self.ctx.array(t)
+        return self.shared[k]
+
+    def _zeroed(self, r, nbytes):
+        """Reduction scratch from a pool: zeroed once when created (the
+        kernels leave their arrival counters at zero), so serving issues no
+        fill kernels that would order behind in-flight requests."""
+        pool = self._scratch_pool.setdefault(nbytes, [])
+        if pool:
+            t, a = pool.pop()
+        else:
+            t = torch.zeros(nbytes, dtype=torch.uint8, device=self.device)
+            a = self.ctx.array(t)
+        r.scratch.append((nbytes, t, a))
+        r.bytes += nbytes
+        return a
+
+    def _slot(self):
+        return self._slots.pop() if self._slots else torch.empty(RESPONSE_BYTES // 4, dtype=F32, pin_memory=True)
+
+    def working_bytes(self, r):
+        """Bytes of the private arrays a request will allocate."""
+        d = self.inp.data[(r.kind, self.inp.bucket(r.scale))]
+        if r.kind == "VEC":
+            return 8 * d["n"] + 4 + 16400
+        if r.kind == "B&S":
+            return 40 * d["n"]
+        if r.kind == "IMG+ML":
+            n = d["side"] ** 2
+            return 6 * 4 * n + 2 * 16400 + 80 * d["rows"] + 4 * d["rows"]
+        n, nnz = d["n"], d["nnz"]
+        return 16 * n + 8 + 2 * 8200 + 16 * (n + nnz) // 1792 + 64
+
+    # ----------------------------------------------------------- issue
+    def issue(self, r):
+        """Issue every element of request r (never blocks)."""
+        c = self.ctx
+        b = self.inp.bucket(r.scale)
+        d = self.inp.data[(r.kind, b)]
+        dev = self.device
+        r.slot = self._slot()
+        if r.kind == "VEC":
+            n = d["n"]
+            X = self._arr(r, torch.empty(n, dtype=F32, device=dev), host=d["hx"])
+            Y = self._arr(r, torch.empty(n, dtype=F32, device=dev), host=d["hy"])
+            Z = self._arr(r, torch.empty(1, dtype=F32, device=dev), host=r.slot)
+            S = self._zeroed(r, G.gdag_scratch_bytes("vec_reduce_diff", n))
+            c.write(X, None, 0, 4 * n)
+            c.write(Y, None, 0, 4 * n)
+            c.launch("vec_square", X, n)
+            c.launch("vec_square", Y, n)
+            c.launch("vec_reduce_diff", X, Y, Z, S, n)
+            r.resp = (Z, 4)
+        elif r.kind == "B&S":
+            n = d["n"]
+            outs = []
+            for i, St in enumerate(d["S"]):
+                Sa = self._shared(("bs", b, i), St)
+                Ca = self._arr(r, torch.empty(n, dtype=F32, device=dev), host=r.slot if i == 0 else None)
+                c.launch("bs_call", Sa, Ca, n, 60.0, 0.1, 0.2, 1.0)
+                outs.append(Ca)
+            r.resp = (outs[0], min(4 * n, RESPONSE_BYTES))
+        elif r.kind == "IMG+ML":
+            side, rows = d["side"], d["rows"]
+            n = side * side
+            IMG = self._shared(("img", b), d["img"])
+            t = lambda: torch.empty(n, dtype=F32, device=dev)
+            B5, B9, E5, E9, Sh = (self._arr(r, t()) for _ in range(5))
+            OUT = self._arr(r, t(), host=r.slot)
+            MM5 = self._arr(r, torch.empty(2, dtype=F32, device=dev))
+            MM9 = self._arr(r, torch.empty(2, dtype=F32, device=dev))
+            SC5 = self._zeroed(r, G.gdag_scratch_bytes("minmax", n))
+            SC9 = self._zeroed(r, G.gdag_scratch_bytes("minmax", n))
+            w5, w9 = self._weights()
+            c.launch("gauss_blur", IMG, B5, w5, side, side, 2)
+            c.launch("gauss_blur", IMG, B9, w9, side, side, 4)
+            c.launch("sobel", B5, E5, side, side)
+            c.launch("sobel", B9, E9, side, side)
+            c.launch("minmax", E5, MM5, SC5, n)
+            c.launch("minmax", E9, MM9, SC9, n)
+            c.launch("extend", E5, MM5, n)
+            c.launch("extend", E9, MM9, n)
+            c.launch("unsharp", IMG, B5, Sh, 0.5, n)
+            c.launch("combine", Sh, B5, B9, E5, E9, OUT, n)
+            XA = self._shared(("X", b), d["X"])
+            T1, B1 = self._shared(("T1", b), d["T1"]), self._shared(("b1", b), d["b1"])
+            T2, B2 = self._shared(("T2", b), d["T2"]), self._shared(("b2", b), d["b2"])
+            S1 = self._arr(r, torch.empty(rows * 10, dtype=F32, device=dev))
+            S2 = self._arr(r, torch.empty(rows * 10, dtype=F32, device=dev))
+            LAB = self._arr(r, torch.empty(rows, dtype=torch.int32, device=dev))
+            c.launch("dense_scores", XA, T1, B1, S1, rows, 1024, 10)
+            c.launch("dense_scores", XA, T2, B2, S2, rows, 1024, 10)
+            c.launch("row_softmax", S1, rows, 10)
+            c.launch("row_softmax", S2, rows, 10)
+            c.launch("argmax_combine", S1, S2, LAB, rows, 10)
+            # the response: the head of the combined image (the labels stay
+            # on the device)
+            r.resp = (OUT, min(4 * n, RESPONSE_BYTES))
+        else:
+            n, nnz = d["n"], d["nnz"]
+            A = [self._shared(("A", b, i), t) for i, t in enumerate(d["A"])]
+            AT = [self._shared(("AT", b, i), t) for i, t in enumerate(d["AT"])]
+            PA, PAT = self._partitions(b, A, AT, n, nnz)
+            v = {k: self._arr(r, torch.empty(n, dtype=F32, device=dev), host=r.slot if k == "a2" else None)
+                 for k in ("a", "h", "a2", "h2")}
+            NA = self._arr(r, torch.empty(1, dtype=F32, device=dev))
+            NH = self._arr(r, torch.empty(1, dtype=F32, device=dev))
+            SA = self._zeroed(r, G.gdag_scratch_bytes("l2norm", n))
+            SH = self._zeroed(r, G.gdag_scratch_bytes("l2norm", n))
+            cb = G.gdag_scratch_bytes("spmv_csr", n + nnz)
+            CA = self._arr(r, torch.empty(cb, dtype=torch.uint8, device=dev))  # fully written before read
+            CAT = self._arr(r, torch.empty(cb, dtype=torch.uint8, device=dev))
+            ones = self._ones(n)  # a_0 = h_0 = 1: a shared, read-only vector
+            cur = (ones, ones)
+            bufs = [(v["a2"], v["h2"]), (v["a"], v["h"])]
+            for it in range(5):
+                a_in, h_in = cur
+                a_out, h_out = bufs[it % 2]
+                c.launch("spmv_csr", *AT, h_in, PAT, a_out, CAT, n, nnz)
+                c.launch("spmv_csr", *A, a_in, PA, h_out, CA, n, nnz)
+                c.launch("l2norm", a_out, NA, SA, n)
+                c.launch("l2norm", h_out, NH, SH, n)
+                c.launch("scale", a_out, NA, n)
+                c.launch("scale", h_out, NH, n)
+                cur = (a_out, h_out)
+            # 5 iterations end in the first buffer pair (a2, h2)
+            r.resp = (v["a2"], min(4 * n, RESPONSE_BYTES))
+        arr, nb = r.resp
+        c.prefetch_host(arr, 0, nb)
+        r.final = self.ctx.nodes()[-1][0] if self.ctx.options.record_log else None
+        if r.final is None:
+            r.final = self._last_node()
+
+    def _last_node(self):
+        return G.gdag_stats_get(self.ctx.h).nodes - 1
+
+    def _weights(self):
+        if "w" not in self.shared:
+            w5 = W.gaussian_weights(2, 1.0).to(self.device)
+            w9 = W.gaussian_weights(4, 2.0).to(self.device)
+            self.shared["w_t"] = (w5, w9)
+            self.shared["w"] = (self.ctx.array(w5), self.ctx.array(w9))
+        return self.shared["w"]
+
+    def _ones(self, n):
+        key = ("ones", n)
+        if key not in self.shared:
+            t = torch.ones(n, dtype=F32, device=self.device)
+            self.shared[key + ("t",)] = t
+            self.shared[key] = self.ctx.array(t)
+        return self.shared[key]
+
+    def _partitions(self, b, A, AT, n, nnz):
+        if b not in self.partitions:
+            pb = G.gdag_scratch_bytes("spmv_partition", n + nnz)
+            pa = torch.zeros(pb, dtype=torch.uint8, device=self.device)
+            pat = torch.zeros(pb, dtype=torch.uint8, device=self.device)
+            PA, PAT = self.ctx.array(pa), self.ctx.array(pat)
+            self.ctx.launch("spmv_partition", A[0], PA, n, nnz)
+            self.ctx.launch("spmv_partition", AT[0], PAT, n, nnz)
+            self.partitions[b] = (PA, PAT, pa, pat)
+        return self.partitions[b][:2]
+
+    # ------------------------------------------------------------ finish
+    def finish(self, r, now):
+        arr, nb = r.resp
+        self.ctx.read(arr, None, 0, nb)  # served from the completed prefetch
+        r.done_at = now
+        r.resp_view = r.slot[: nb // 4].clone() if nb >= 4 else None
+        for a in r.arrays:
+            self.ctx.unregister(a)
+        r.arrays.clear()
+        r.tensors.clear()
+        for nbytes, t, a in r.scratch:
+            self._scratch_pool[nbytes].append((t, a))
+        r.scratch.clear()
+        self._slots.append(r.slot)
+        r.slot = None
+        self.used -= r.need
+
+    def warm(self, kinds=KINDS):
+        """Build the per-bucket shared state (partitions, weights) once."""
+        for s in self.inp.scales:
+            for k in kinds:
+                if (k, s) in self.inp.data:
+                    r = Request(-1, k, s, 0.0)
+                    self.issue(r)
+                    self.ctx.sync()
+                    self.finish(r, 0.0)
+
+    def run(self, requests, clock=time.perf_counter, spin=True):
+        """Serve a list of requests (sorted by arrival, seconds from start)."""
+        pending = collections.deque()
+        inflight = []
+        i = 0
+        t0 = clock()
+        done = 0
+        while done < len(requests):
+            now = clock() - t0
+            while i < len(requests) and requests[i].arrival <= now:
+                pending.append(requests[i])
+                i += 1
+            while pending:
+                r = pending[0]
+                need = self.working_bytes(r)
+                if inflight and self.used + need > self.budget:
+                    break
+                pending.popleft()
+                r.admitted = now
+                r.need = need  # released on completion: the same figure
+                self.used += need
+                self.issue(r)
+                inflight.append(r)
+            still = []
+            for r in inflight:
+                if self.ctx.done(r.final):
+                    self.finish(r, clock() - t0)
+                    done += 1
+                else:
+                    still.append(r)
+            inflight = still
+            if not inflight and not pending and i < len(requests):
+                # idle until the next arrival
+                wait = requests[i].arrival - (clock() - t0)
+                if wait > 0 and not spin:
+                    time.sleep(wait)
+        return requests
+
+    def close(self):
+        self.ctx.sync()
+        self.ctx.close()
+
+
+def poisson_requests(rate, count, scales, seed=0, kinds=KINDS):
+    """Arrival times of a Poisson stream of `rate` req/s; kinds uniform;
+    scale s ~ U[1/64, 1]."""
+    g = np.random.default_rng(seed)
+    gaps = g.exponential(1.0 / rate, size=count)
+    t = np.cumsum(gaps)
+    out = []
+    for k in range(count):
+        kind = kinds[int(g.integers(0, len(kinds)))]
+        s = float(g.uniform(1.0 / 64, 1.0))
+        out.append(Request(k, kind, s, float(t[k])))
+    return out
+
+
+def latency_summary(reqs):
+    lat = np.array([(r.done_at - r.arrival) * 1e3 for r in reqs])
+    span = max(r.done_at for r in reqs) - min(r.arrival for r in reqs)
+    by = {}
+    for k in sorted({r.kind for r in reqs}):
+        l = np.array([(r.done_at - r.arrival) * 1e3 for r in reqs if r.kind == k])
+        by[k] = {"n": int(l.size), "p50_ms": float(np.percentile(l, 50)), "p99_ms": float(np.percentile(l, 99))}
+    return {"requests": len(reqs), "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "mean_ms": float(lat.mean()), "throughput_req_s": len(reqs) / span, "by_kind": by}

@@ -43,6 +43,9 @@ def test_sum_diff_identities():
     assert out["z"] == n * (n - 1) * (2 * n - 1) // 6
     # sign: sum(x - y), not sum(y - x)
     assert N.sum_diff(np.float32([2.0]), np.float32([1.0])) == 1.0
+    # the condition scale: sum |x - y| (exactly rounded sum by fsum)
+    assert N.sum_abs_diff(x, y) == pytest.approx(
+        math.fsum(abs(float(a) - float(b)) for a, b in zip(x, y)), rel=1e-14)
 
 
 # ------------------------------------------------------------------ B&S

@@ -283,3 +283,55 @@ def test_prefetch_then_read_copies_once():
     p.read(1)
     assert len([o for o in p.ctx.ops() if o[0] == G.GDAG_OP_COPY_D2H]) == 2
     assert D.check_hb(p.ctx.ops(), D.expected_edges(p.elems)) == []
+
+
+def test_capture_and_replay_as_one_element():
+    p = Program(4)
+    # capture a two-branch shape: k0 writes 0, k1 writes 1, k2 reads both, writes 2
+    G.gdag_capture_begin(p.ctx.h)
+    p.kernel({0: D.W})
+    p.kernel({1: D.W})
+    p.kernel({0: D.R, 1: D.R, 2: D.W})
+    g = G.gdag_capture_end(p.ctx.h)
+    n1 = G.gdag_graph_launch(p.ctx.h, g)
+    n2 = G.gdag_graph_launch(p.ctx.h, g)
+    # the replay element writes 0, 1 and 2 (and reads them): replays chain
+    edges = {(s, d) for s, d, _a, _k in p.ctx.edges()}
+    assert (n1, n2) in edges
+    k = G.gdag_launch(p.ctx.h, p.kern[1], G.gdag_dim3(1, 1, 1), G.gdag_dim3(32, 1, 1), 0,
+                      [G.array_arg(p.arrays[2].handle, G.GDAG_MODE_IN)])
+    assert (n2, k) in {(s, d) for s, d, _a, _k in p.ctx.edges()}
+    nodes = dict((i, kind) for i, kind, _s in p.ctx.nodes())
+    assert nodes[n1] == G.GDAG_NODE_GRAPH
+    G.gdag_graph_destroy(p.ctx.h, g)
+    with pytest.raises(G.GdagError):
+        G.gdag_graph_launch(p.ctx.h, g)
+
+
+def test_capture_rejects_host_waits_and_sync_policy():
+    p = Program(2)
+    G.gdag_capture_begin(p.ctx.h)
+    with pytest.raises(G.GdagError) as e:
+        p.ctx.read(p.arrays[0])
+    assert e.value.code == G.GDAG_ERR_INVALID
+    with pytest.raises(G.GdagError):
+        G.gdag_capture_begin(p.ctx.h)  # nested
+    with pytest.raises(G.GdagError):
+        p.ctx.sync()
+    g = G.gdag_capture_end(p.ctx.h)
+    assert g >= 0
+    q = Program(1, policy=G.GDAG_POLICY_SERIAL_SYNC)
+    with pytest.raises(G.GdagError):
+        G.gdag_capture_begin(q.ctx.h)
+
+
+def test_node_query_polls_without_blocking():
+    p = Program(2, fake_complete=False)
+    k = p.kernel({0: D.W})
+    assert G.gdag_node_query(p.ctx.h, k) is False  # still running
+    q = Program(2, fake_complete=True)
+    k = q.kernel({0: D.W})
+    assert G.gdag_node_query(q.ctx.h, k) is True
+    assert q.ctx.stats()["active"] == 0
+    with pytest.raises(G.GdagError):
+        G.gdag_node_query(q.ctx.h, 99)
