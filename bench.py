@@ -45,7 +45,7 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--dags", default="all", choices=["all", "bs"],
                     help="also measure the VEC, IMG, ML and HITS DAGs (rank 0)")
-    ap.add_argument("--profile", default=None, choices=["bs", "vec", "img", "ml", "hits"],
+    ap.add_argument("--profile", default=None, choices=["bs", "vec", "img", "ml", "hits", "dl"],
                     help="run only --steps steps of one DAG through the library (a small, "
                          "single-context command for ncu captures); prints nothing")
     ap.add_argument("--img-size", type=int, default=4096)
@@ -254,6 +254,11 @@ def alg_bytes(name, a):
         return 4 * (n + 1) + 8 * nnz + 4 * n + 4 * n
     if name == "l2norm":
         return 4 * a[3]
+    if name == "conv3x3_relu_pool":
+        n, h, w = a[5], a[6], a[7]
+        return 2 * 3 * n * h * w + 2 * 64 * n * (h // 2) * (w // 2) + 64 * 27 * 2 + 64 * 4
+    if name == "avgpool_global":
+        return 2 * a[2] * a[3] + 4 * a[2]
     return 0
 
 
@@ -405,6 +410,27 @@ class HitsSpec(Spec):
         H.dep(0, 1)
 
 
+class DlSpec(Spec):
+    name = "DL"
+
+    def build(self, ctx):
+        d = self.W.DlDag(ctx)
+        d.load(*self.data["dl"])
+        return d
+
+    def step(self, d):
+        d.launch_all()
+
+    def hand(self, d, ctx, H):
+        n, h, w = d.n, d.h, d.w
+        H.k(0, "conv3x3_relu_pool", d.X1, d.W1, d.B1, d.P1, d.ST, n, h, w)
+        H.k(1, "conv3x3_relu_pool", d.X2, d.W2, d.B2, d.P2, d.ST, n, h, w)
+        H.k(0, "avgpool_global", d.P1, d.E1, n * 64, (h // 2) * (w // 2))
+        H.k(1, "avgpool_global", d.P2, d.E2, n * 64, (h // 2) * (w // 2))
+        H.dep(0, 1)
+        H.k(0, "concat_dense", d.E1, d.E2, d.WD, d.BD, d.LOG, n, 64, d.classes)
+
+
 class Hand:
     """Explicit multi-stream schedule for stream capture: every stream forks
     from the capture stream and joins back into it."""
@@ -450,6 +476,8 @@ def make_data(datagen, which):
         data["ml"] = datagen.ml_inputs(100_000, feats=1024, classes=10, seed=3)
     if "hits" in which:
         data["hits"] = datagen.hits_graph(10_000_000, 50_000_000, seed=4)
+    if "dl" in which:
+        data["dl"] = datagen.dl_inputs(n=16, h=256, w=256, seed=5)[0]
     return data
 
 
@@ -617,7 +645,7 @@ def run_ours(args, rank, world, local_rank):
         if dist:
             dist.barrier()
 
-    which = ["bs"] + (["vec", "img", "ml", "hits"] if args.dags == "all" and rank == 0 else [])
+    which = ["bs"] + (["vec", "img", "ml", "hits", "dl"] if args.dags == "all" and rank == 0 else [])
     data = make_data(datagen, which)
     prices = data["bs"]
     s0 = torch.cuda.Stream()
@@ -694,7 +722,8 @@ def run_ours(args, rank, world, local_rank):
         # ---- every DAG of the suite: policies, hand-built CUDA Graph, bounds
         specs = [BsSpec(G, W, data)]
         if args.dags == "all":
-            specs += [VecSpec(G, W, data), ImgSpec(G, W, data), MlSpec(G, W, data), HitsSpec(G, W, data)]
+            specs += [VecSpec(G, W, data), ImgSpec(G, W, data), MlSpec(G, W, data), HitsSpec(G, W, data),
+                      DlSpec(G, W, data)]
         dags = {}
         for sp in specs:
             dags[sp.name] = measure_dag(torch, G, sp, nsteps_other, hbm, link)
@@ -821,6 +850,10 @@ def run_profile(args):
     elif args.profile == "ml":
         d = W.MlDag(ctx, 100_000)
         d.load(*datagen.ml_inputs(100_000, feats=1024, classes=10, seed=3))
+        step = d.launch_all
+    elif args.profile == "dl":
+        d = W.DlDag(ctx)
+        d.load(*datagen.dl_inputs(n=16, h=256, w=256, seed=5)[0])
         step = d.launch_all
     else:
         d = W.HitsDag(ctx, *datagen.hits_graph(10_000_000, 50_000_000, seed=4))

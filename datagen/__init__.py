@@ -15,6 +15,11 @@ Recipes (the paper, Section IV-A, runs every benchmark on random data):
         to multiples of 1/256 (|k| < 1000), log prior likewise; ridge weights
         ~ N(0, 0.05^2) rounded to multiples of 1/256, intercepts likewise.
         Dyadic tables make every score an exact float32 sum.
+* DL    two image batches n x 3 x h x w ~ U[0, 1), conv weights 64 x 3 x 3 x 3
+        ~ N(0, 0.3^2) and biases ~ N(0, 0.1^2), dense 128 x 10 ~ N(0, 0.1^2) and
+        bias ~ N(0, 0.1^2); images and conv weights rounded to bfloat16 (the
+        values are returned as float32 numbers that bfloat16 holds exactly,
+        with their bfloat16 bit patterns).
 * HITS  directed graph with power-law out-degree (Pareto exponent alpha,
         d = floor(u^(-1/(alpha-1))), capped at n-1), rescaled so the total is
         exactly nnz; destinations uniform, no self-loops, no duplicate edges;
@@ -128,3 +133,31 @@ def hits_graph(n: int, nnz: int, alpha: float = 2.1, seed: int = 4):
     t_rowptr, t_col = transpose_csr(rowptr, col, n)
     val = np.ones(nnz, dtype=np.float32)
     return (rowptr, col, val), (t_rowptr, t_col, val.copy())
+
+
+def to_bf16_bits(a: np.ndarray) -> np.ndarray:
+    """float32 -> bfloat16 bit patterns, round to nearest even."""
+    u = np.ascontiguousarray(a, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    r = (u + 0x7FFF + ((u >> 16) & 1)) >> 16
+    return r.astype(np.uint16)
+
+
+def from_bf16_bits(b: np.ndarray) -> np.ndarray:
+    return (b.astype(np.uint32) << 16).view(np.float32)
+
+
+def dl_inputs(n: int = 16, h: int = 256, w: int = 256, cout: int = 64, classes: int = 10, seed: int = 5):
+    """(x1, x2, w1, b1, w2, b2, wd, bd) as float32 (x and w exactly bf16)
+    plus the bf16 bit patterns of x1, x2, w1, w2."""
+    g = rng(seed)
+    q = lambda a: from_bf16_bits(to_bf16_bits(a))
+    x1 = q(g.random((n, 3, h, w), dtype=np.float32))
+    x2 = q(g.random((n, 3, h, w), dtype=np.float32))
+    w1 = q(g.normal(0, 0.3, (cout, 3, 3, 3)).astype(np.float32))
+    w2 = q(g.normal(0, 0.3, (cout, 3, 3, 3)).astype(np.float32))
+    b1 = g.normal(0, 0.1, cout).astype(np.float32)
+    b2 = g.normal(0, 0.1, cout).astype(np.float32)
+    wd = g.normal(0, 0.1, (2 * cout, classes)).astype(np.float32)
+    bd = g.normal(0, 0.1, classes).astype(np.float32)
+    return (x1, x2, w1, b1, w2, b2, wd, bd), {k: to_bf16_bits(v) for k, v in
+                                              (("x1", x1), ("x2", x2), ("w1", w1), ("w2", w2))}

@@ -300,3 +300,66 @@ void orc_scale(const double *x, double nrm, double *out, int64_t n)
     for (int64_t i = 0; i < n; ++i)
         out[i] = (nrm > 0.0) ? x[i] / nrm : x[i];
 }
+
+/* ------------------------------------------------------------------- DL --
+ * Section IV-B, DL: a convolutional network projects two images to
+ * low-dimensional embeddings and combines them with a dense layer.
+ * Readings (the paper gives no layer sizes): per branch a 3x3 convolution
+ * with 3 input and C output channels, zero padding 1, stride 1, plus bias,
+ * ReLU, and 2x2 max-pooling with stride 2; NCHW layout.                    */
+void orc_conv3x3_relu_pool(const double *x, int64_t n, int64_t cin, int64_t h,
+                           int64_t w, const double *wt, const double *bias,
+                           int64_t cout, double *out)
+{
+    const int64_t ho = h / 2, wo = w / 2;
+    for (int64_t b = 0; b < n; ++b)
+        for (int64_t co = 0; co < cout; ++co)
+            for (int64_t py = 0; py < ho; ++py)
+                for (int64_t px = 0; px < wo; ++px) {
+                    double best = -INFINITY;
+                    for (int64_t sy = 0; sy < 2; ++sy)
+                        for (int64_t sx = 0; sx < 2; ++sx) {
+                            const int64_t y = 2 * py + sy, xx = 2 * px + sx;
+                            double s = bias[co];
+                            for (int64_t ci = 0; ci < cin; ++ci)
+                                for (int64_t dy = -1; dy <= 1; ++dy)
+                                    for (int64_t dx = -1; dx <= 1; ++dx) {
+                                        const int64_t yy = y + dy, xq = xx + dx;
+                                        if (yy < 0 || yy >= h || xq < 0 || xq >= w) continue;
+                                        s += wt[((co * cin + ci) * 3 + (dy + 1)) * 3 + (dx + 1)]
+                                             * x[((b * cin + ci) * h + yy) * w + xq];
+                                    }
+                            const double r = s > 0.0 ? s : 0.0;
+                            if (r > best) best = r;
+                        }
+                    out[((b * cout + co) * ho + py) * wo + px] = best;
+                }
+}
+
+/* Global average pool: e[p] = mean over the hw values of plane p.         */
+void orc_avgpool(const double *x, int64_t planes, int64_t hw, double *e)
+{
+    for (int64_t p = 0; p < planes; ++p) {
+        double s = 0.0;
+        for (int64_t i = 0; i < hw; ++i)
+            s += x[p * hw + i];
+        e[p] = s / (double)hw;
+    }
+}
+
+/* Concatenate two n x c embeddings to n x 2c and apply a dense layer:
+ * out[b][j] = bias[j] + sum_i cat[b][i] wd[i][j], wd row-major 2c x classes. */
+void orc_concat_dense(const double *e1, const double *e2, int64_t n, int64_t c,
+                      const double *wd, const double *bias, int64_t classes,
+                      double *out)
+{
+    for (int64_t b = 0; b < n; ++b)
+        for (int64_t j = 0; j < classes; ++j) {
+            double s = bias[j];
+            for (int64_t i = 0; i < c; ++i)
+                s += e1[b * c + i] * wd[i * classes + j];
+            for (int64_t i = 0; i < c; ++i)
+                s += e2[b * c + i] * wd[(c + i) * classes + j];
+            out[b * classes + j] = s;
+        }
+}

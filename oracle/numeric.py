@@ -63,6 +63,9 @@ _SIGS = {
     "orc_spmv_csr_abs": (None, [_i64, _I64, _I32, _D, _D, _D]),
     "orc_l2norm": (_dbl, [_D, _i64]),
     "orc_scale": (None, [_D, _dbl, _D, _i64]),
+    "orc_conv3x3_relu_pool": (None, [_D, _i64, _i64, _i64, _i64, _D, _D, _i64, _D]),
+    "orc_avgpool": (None, [_D, _i64, _i64, _D]),
+    "orc_concat_dense": (None, [_D, _D, _i64, _i64, _D, _D, _i64, _D]),
 }
 
 
@@ -248,4 +251,33 @@ def scale(x, nrm):
     x = _f64(x)
     out = np.empty_like(x)
     lib().orc_scale(_p(x), float(nrm), _p(out), x.size)
+    return out
+
+
+# ---------------------------------------------------------------- DL
+def conv3x3_relu_pool(x, wt, bias):
+    """x: (n, cin, h, w); wt: (cout, cin, 3, 3); returns (n, cout, h/2, w/2)."""
+    x, wt, bias = _f64(x), _f64(wt), _f64(bias)
+    n, cin, h, w = x.shape
+    cout = wt.shape[0]
+    out = np.empty((n, cout, h // 2, w // 2), dtype=np.float64)
+    lib().orc_conv3x3_relu_pool(_p(x), n, cin, h, w, _p(wt), _p(bias), cout, _p(out))
+    return out
+
+
+def avgpool(x):
+    """x: (n, c, h, w) -> (n, c) means."""
+    x = _f64(x)
+    n, c, h, w = x.shape
+    e = np.empty((n, c), dtype=np.float64)
+    lib().orc_avgpool(_p(x), n * c, h * w, _p(e))
+    return e
+
+
+def concat_dense(e1, e2, wd, bias):
+    e1, e2, wd, bias = _f64(e1), _f64(e2), _f64(wd), _f64(bias)
+    n, c = e1.shape
+    classes = wd.shape[1]
+    out = np.empty((n, classes), dtype=np.float64)
+    lib().orc_concat_dense(_p(e1), _p(e2), n, c, _p(wd), _p(bias), classes, _p(out))
     return out

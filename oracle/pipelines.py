@@ -86,3 +86,15 @@ def hits(csr, csc, iters=5):
                      ("nh", nh), ("a", a), ("h", h)):
             out[k].append(v)
     return out
+
+
+def dl(x1, x2, w1, b1, w2, b2, wd, bd):
+    """DL: two conv3x3 + ReLU + 2x2 max-pool branches, a global average pool
+    of each, the concatenation of the two embeddings and a dense layer."""
+    out = {}
+    out["p1"] = N.conv3x3_relu_pool(x1, w1, b1)
+    out["p2"] = N.conv3x3_relu_pool(x2, w2, b2)
+    out["e1"] = N.avgpool(out["p1"])
+    out["e2"] = N.avgpool(out["p2"])
+    out["logits"] = N.concat_dense(out["e1"], out["e2"], wd, bd)
+    return out

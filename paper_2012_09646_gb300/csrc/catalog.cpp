@@ -12,6 +12,7 @@ void append_bs_kernels(std::vector<KernelEntry> &v);
 void append_img_kernels(std::vector<KernelEntry> &v);
 void append_ml_kernels(std::vector<KernelEntry> &v);
 void append_hits_kernels(std::vector<KernelEntry> &v);
+void append_dl_kernels(std::vector<KernelEntry> &v);
 size_t spmv_part_bytes(int64_t rows_plus_nnz);
 size_t spmv_carry_bytes(int64_t rows_plus_nnz);
 
@@ -25,6 +26,7 @@ const std::vector<KernelEntry> &table()
         append_img_kernels(v);
         append_ml_kernels(v);
         append_hits_kernels(v);
+        append_dl_kernels(v);
         return v;
     }();
     return t;

@@ -281,3 +281,57 @@ class HitsDag:
             for k in cur:
                 self.ctx.read(self.V[k], None, 0, 4 * self.n)
         return cur
+
+
+class DlDag:
+    """DL: two convolution branches (conv3x3 + bias + ReLU + 2x2 max-pool on
+    the tensor cores), a global average pool of each, and a dense layer over
+    the concatenated embeddings.  bf16 NCHW activations, fp32 embeddings and
+    logits; inputs resident, the host reads the logits."""
+
+    def __init__(self, ctx, n=16, h=256, w=256, classes=10, device="cuda"):
+        self.ctx, self.n, self.h, self.w, self.classes = ctx, n, h, w, classes
+        bf = torch.bfloat16
+        self.x1 = torch.zeros((n, 3, h, w), dtype=bf, device=device)
+        self.x2 = torch.zeros((n, 3, h, w), dtype=bf, device=device)
+        self.w1 = torch.zeros((64, 3, 3, 3), dtype=bf, device=device)
+        self.w2 = torch.zeros((64, 3, 3, 3), dtype=bf, device=device)
+        self.b1 = torch.zeros(64, dtype=F32, device=device)
+        self.b2 = torch.zeros(64, dtype=F32, device=device)
+        self.p1 = torch.zeros((n, 64, h // 2, w // 2), dtype=bf, device=device)
+        self.p2 = torch.zeros((n, 64, h // 2, w // 2), dtype=bf, device=device)
+        self.e1 = torch.zeros((n, 64), dtype=F32, device=device)
+        self.e2 = torch.zeros((n, 64), dtype=F32, device=device)
+        self.wd = torch.zeros((128, classes), dtype=F32, device=device)
+        self.bd = torch.zeros(classes, dtype=F32, device=device)
+        self.logits = torch.zeros((n, classes), dtype=F32, device=device)
+        self.status = torch.zeros(1, dtype=torch.int32, device=device)
+        self.h_logits = _pinned((n, classes), F32)
+        A = ctx.array
+        self.X1, self.X2, self.W1, self.W2 = A(self.x1), A(self.x2), A(self.w1), A(self.w2)
+        self.B1, self.B2, self.P1, self.P2 = A(self.b1), A(self.b2), A(self.p1), A(self.p2)
+        self.E1, self.E2, self.WD, self.BD = A(self.e1), A(self.e2), A(self.wd), A(self.bd)
+        self.LOG = A(self.logits, host=self.h_logits)
+        self.ST = A(self.status)
+        torch.cuda.synchronize()
+
+    def load(self, x1, x2, w1, b1, w2, b2, wd, bd):
+        """float32 inputs whose x and w values bfloat16 holds exactly."""
+        for dst, src in ((self.x1, x1), (self.x2, x2), (self.w1, w1), (self.w2, w2)):
+            dst.copy_(torch.as_tensor(src).to(torch.bfloat16))
+        for dst, src in ((self.b1, b1), (self.b2, b2), (self.wd, wd), (self.bd, bd)):
+            dst.copy_(torch.as_tensor(src))
+        torch.cuda.synchronize()
+
+    def launch_all(self):
+        c, n, h, w = self.ctx, self.n, self.h, self.w
+        c.launch("conv3x3_relu_pool", self.X1, self.W1, self.B1, self.P1, self.ST, n, h, w)
+        c.launch("conv3x3_relu_pool", self.X2, self.W2, self.B2, self.P2, self.ST, n, h, w)
+        c.launch("avgpool_global", self.P1, self.E1, n * 64, (h // 2) * (w // 2))
+        c.launch("avgpool_global", self.P2, self.E2, n * 64, (h // 2) * (w // 2))
+        c.launch("concat_dense", self.E1, self.E2, self.WD, self.BD, self.LOG, n, 64, self.classes)
+
+    def step(self, read=True):
+        self.launch_all()
+        if read:
+            self.ctx.read(self.LOG)

@@ -1,0 +1,81 @@
+"""DL nodes and DAG on the GPU through the C ABI (the convolution on the
+tcgen05 tensor cores), against the fp64 oracle.  Tolerance for the bf16
+nodes (stated by the benchmark spec): 2e-2 relative; near zero (the ReLU cut) the
+bound is 2e-2 * max(|ref|, 0.05), a bf16 rounding of values of order 0.1."""
+import numpy as np
+import pytest
+import torch
+
+import datagen
+from oracle import numeric as N
+from oracle import pipelines as P
+from paper_2012_09646_gb300 import gdag as G
+from paper_2012_09646_gb300.workloads import DlDag
+
+pytestmark = pytest.mark.gpu
+TOL = 2e-2
+
+
+def check(got, ref, floor=0.05, what=""):
+    got = np.asarray(got, np.float64)
+    ref = np.asarray(ref, np.float64)
+    err = np.abs(got - ref) / np.maximum(np.abs(ref), floor)
+    assert err.max() <= TOL, (what, float(err.max()))
+
+
+@pytest.mark.parametrize("n,h,w", [(1, 2, 64), (2, 6, 128), (1, 64, 64), (3, 34, 192)])
+def test_conv_nodes_and_dag(n, h, w):
+    inp, _bits = datagen.dl_inputs(n=n, h=h, w=w, seed=n * 100 + h)
+    ref = P.dl(*inp)
+    with G.Context() as ctx:
+        d = DlDag(ctx, n, h, w)
+        d.load(*inp)
+        d.step()
+        ctx.sync()
+        assert int(d.status.item()) == 0
+        p1 = d.p1.float().cpu().numpy()
+        check(p1, ref["p1"], what="conv1")
+        check(d.p2.float().cpu().numpy(), ref["p2"], what="conv2")
+        # pooling of the GPU's own conv output: fp32 mean of bf16 values
+        e1 = d.e1.cpu().numpy()
+        np.testing.assert_allclose(e1, N.avgpool(p1), rtol=1e-5, atol=1e-6)
+        check(d.h_logits.numpy(), ref["logits"], what="logits")
+
+
+def test_conv_exact_on_integer_data():
+    """Small integers: every product and sum is exact in bf16 x bf16 -> fp32,
+    and the pooled maxima are integers that bf16 holds, so the tensor-core
+    result equals the oracle bit for bit."""
+    n, h, w = 2, 8, 64
+    g = np.random.default_rng(3)
+    x = g.integers(-3, 4, (n, 3, h, w)).astype(np.float32)
+    wt = g.integers(-2, 3, (64, 3, 3, 3)).astype(np.float32)
+    b = g.integers(-4, 5, 64).astype(np.float32)
+    with G.Context() as ctx:
+        d = DlDag(ctx, n, h, w)
+        d.load(x, x, wt, b, wt, b, np.zeros((128, 10), np.float32), np.zeros(10, np.float32))
+        d.step()
+        ctx.sync()
+        got = d.p1.float().cpu().numpy()
+    assert np.array_equal(got.astype(np.float64), N.conv3x3_relu_pool(x, wt, b))
+
+
+@pytest.mark.slow
+def test_dl_full_size():
+    """16 x 3 x 256 x 256, the benchmark shape; the pooled maps sampled and
+    the logits in full."""
+    inp, _ = datagen.dl_inputs(n=16, h=256, w=256, seed=5)
+    x1, x2, w1, b1, w2, b2, wd, bd = inp
+    with G.Context() as ctx:
+        d = DlDag(ctx)
+        d.load(*inp)
+        d.step()
+        ctx.sync()
+        assert int(d.status.item()) == 0
+        # the oracle on two images of the batch (each branch)
+        for bi in (0, 15):
+            r1 = N.conv3x3_relu_pool(x1[bi:bi + 1], w1, b1)
+            check(d.p1[bi:bi + 1].float().cpu().numpy(), r1, what="conv1 image %d" % bi)
+        e1 = N.avgpool(d.p1.float().cpu().numpy())
+        e2 = N.avgpool(d.p2.float().cpu().numpy())
+        check(d.h_logits.numpy(), N.concat_dense(e1, e2, wd, bd), what="logits")

@@ -274,3 +274,38 @@ def test_hits_converges_to_principal_eigenvectors():
     a, h = out["a"][-1], out["h"][-1]
     np.testing.assert_allclose(np.abs(a), np.abs(va[:, -1]), atol=1e-9)
     np.testing.assert_allclose(np.abs(h), np.abs(vh[:, -1]), atol=1e-9)
+
+
+# ------------------------------------------------------------------- DL
+def test_conv_relu_pool_matches_library_correlate():
+    (x1, _x2, w1, b1, *_), _ = datagen.dl_inputs(n=2, h=10, w=14, cout=5, seed=1)
+    got = N.conv3x3_relu_pool(x1, w1, b1)
+    n, cin, h, w = x1.shape
+    ref = np.zeros((n, 5, h, w))
+    for b in range(n):
+        for co in range(5):
+            s = np.full((h, w), float(b1[co]))
+            for ci in range(cin):
+                s += scipy.signal.correlate2d(x1[b, ci].astype(np.float64), w1[co, ci].astype(np.float64),
+                                              mode="same", boundary="fill", fillvalue=0.0)
+            ref[b, co] = np.maximum(s, 0.0)
+    pooled = ref.reshape(n, 5, h // 2, 2, w // 2, 2).max(axis=(3, 5))
+    np.testing.assert_allclose(got, pooled, rtol=1e-13, atol=1e-14)
+
+
+def test_avgpool_and_concat_dense_match_library():
+    g = np.random.default_rng(4)
+    p = g.random((3, 4, 6, 8))
+    np.testing.assert_allclose(N.avgpool(p), p.mean(axis=(2, 3)), rtol=1e-14)
+    e1, e2 = g.random((3, 4)), g.random((3, 4))
+    wd, bd = g.normal(size=(8, 5)), g.normal(size=5)
+    np.testing.assert_allclose(N.concat_dense(e1, e2, wd, bd), np.concatenate([e1, e2], axis=1) @ wd + bd,
+                               rtol=1e-13)
+
+
+def test_bf16_rounding_matches_torch():
+    import torch
+    a = np.random.default_rng(0).normal(0, 3, 10000).astype(np.float32)
+    ours = datagen.to_bf16_bits(a)
+    theirs = torch.from_numpy(a).to(torch.bfloat16).view(torch.int16).numpy().view(np.uint16)
+    assert np.array_equal(ours, theirs)
