@@ -33,6 +33,12 @@ BS_PARAMS = (60.0, 0.1, 0.2, 1.0)
 BYTES_PER_OPTION = 8  # 4 read + 4 written
 METRIC = "DAG makespan speedup vs serial stream; kernel HBM GB/s; serve p50/p99 latency"
 UNIT = "DAG/s"
+# DRAM bytes (read + write) of one bs_call launch from one ncu capture
+# (profiles/bs_call_bs_10x1e7.md), valid only for the kernel source it was
+# taken on: a changed k_bs.cu reports null.
+BS_CALL_TRAFFIC = {"bytes": 41337856,
+                   "sha256": "fb0df61d93884e816c318137b136d5db1b56129fd12dfb1f016561c5948dcbc9",
+                   "note": "one launch captured alone: its 40 MB output is still in L2 when the kernel ends"}
 WORKLOAD = "B&S: 10 independent Black-Scholes call nodes, 10 x 1e7 float32 spot prices U[10,100), K=60 r=0.1 sigma=0.2 T=1"
 
 
@@ -130,6 +136,13 @@ class ClockSampler:
         return {"sm_mhz": statistics.median(sm), "sm_min_mhz": min(sm),
                 "sm_max_mhz": max(m for _c, m, _p, _r in self.samples), "reasons": sorted(reasons),
                 "power_w_max": max(pw) if pw else None, "samples": len(sm)}
+
+
+def bs_call_traffic():
+    import hashlib
+    with open(os.path.join(ROOT, "paper_2012_09646_gb300", "csrc", "k_bs.cu"), "rb") as f:
+        h = hashlib.sha256(f.read()).hexdigest()
+    return BS_CALL_TRAFFIC["bytes"] if h == BS_CALL_TRAFFIC["sha256"] else None
 
 
 def measured_peaks():
@@ -608,6 +621,17 @@ def measure_dag(torch, G, spec, steps, peak_gbs, link):
     out["critical_path_bound"] = cp
     out["resource_bound"] = res
     out["sum_solo"] = sum(weights)
+    per_kernel = {}
+    for i, e in enumerate(elems):
+        if i < first or e[0] != "k":
+            continue
+        k = per_kernel.setdefault(e[1], {"launches": 0, "solo_ms": 0.0, "alg_bytes": 0})
+        k["launches"] += 1
+        k["solo_ms"] += weights[i]
+        k["alg_bytes"] += alg_bytes(e[1], [getattr(x, "handle", x) for x in e[2]])
+    for k in per_kernel.values():
+        k["alg_gbs"] = k["alg_bytes"] / (k["solo_ms"] * 1e-3) / 1e9 if k["solo_ms"] > 0 else None
+        k["frac_of_hbm_peak"] = k["alg_gbs"] / peak_gbs if k["alg_gbs"] else None
     lctx.close()
     ctx.close()
     kern = sum(1 for e in elems[first:] if e[0] == "k")
@@ -619,7 +643,7 @@ def measure_dag(torch, G, spec, steps, peak_gbs, link):
         "vs_hand_cuda_graph": out["hand_cuda_graph"] / out["parallel"],
         "library_graph_vs_hand_cuda_graph": out["hand_cuda_graph"] / out["library_graph"],
         "frac_of_cp_bound": cp / out["parallel"], "frac_of_resource_bound": res / out["parallel"],
-        "launches_per_step": kern,
+        "launches_per_step": kern, "per_kernel_solo": per_kernel,
     }
 
 
@@ -799,7 +823,8 @@ def run_ours(args, rank, world, local_rank):
             "frac_of_resource_bound": bsm["resource_bound"] / ms_par,
             "roofline": {"kernel": "bs_call", "bound": "hbm", "achieved": achieved, "peak": hbm,
                          "peak_source": peak_src + " hbm_gbs (burst; kernel timed alone)", "unit": "GB/s",
-                         "frac": achieved / hbm, "traffic": None,
+                         "frac": achieved / hbm, "traffic": bs_call_traffic(),
+                         "traffic_note": BS_CALL_TRAFFIC["note"],
                          "algorithmic_bytes_per_launch": bytes_launch, "launch_ms": ms_solo},
             "e2e": {"value": 1e3 / ms_e2e, "unit": UNIT, "ms_per_step": ms_e2e,
                     "h2d_bytes_per_step": N_VEC * 4 * N_OPTS, "d2h_bytes_per_step": N_VEC * 4 * N_OPTS,

@@ -268,8 +268,55 @@ int gdag_array_prefetch_host(gdag_ctx *ctx, gdag_array a, size_t off,
                              size_t bytes);
 
 /* -------------------------------------------------------------- kernels
- * Built-in sm_103a kernels with their signatures (argument order and modes
- * in the kernel table, README of the package).  Errors: NOT_FOUND. */
+ * Built-in sm_103a kernels (the DAG nodes of the Section IV-B benchmarks).
+ * Arguments in order; modes IN / OUT / INOUT as in Section III-D; scalars
+ * i32 (4 bytes), i64 or f32 as given; arrays are device buffers of the
+ * stated element type, row-major.  A launch whose sizes do not fit its
+ * buffers fails with INVALID before anything is queued.
+ *
+ *  VEC   vec_square      (x INOUT f32[n], n i64)                 x := x*x
+ *        vec_reduce_diff (x IN f32[n], y IN f32[n], z OUT f32[1],
+ *                         scratch INOUT, n i64)                  z = sum(x-y)
+ *  B&S   bs_call         (S IN f32[n], C OUT f32[n], n i64, K f32, r f32,
+ *                         sigma f32, T f32)                      call prices
+ *  IMG   gauss_blur      (img IN f32[rows*cols], out OUT, w IN f32[2R+1],
+ *                         rows i32, cols i32, R i32)    separable, clamped
+ *        sobel           (in IN, out OUT, rows i32, cols i32)    magnitude
+ *        minmax          (x IN f32[n], mm OUT f32[2], scratch INOUT, n i64)
+ *        extend          (x INOUT f32[n], mm IN f32[2], n i64)
+ *                                               x := (x-min)/(max-min) or 0
+ *        unsharp         (img IN, blur IN, out OUT, alpha f32, n i64)
+ *        combine         (s IN, b5 IN, b9 IN, e5 IN, e9 IN, out OUT, n i64)
+ *  ML    dense_scores    (X IN i32[rows*feats], table IN f32[feats*classes],
+ *                         bias IN f32[classes], S OUT f32[rows*classes],
+ *                         rows i32, feats i32, classes i32)  S = X table + b
+ *        row_softmax     (S INOUT f32[rows*classes], rows i32, classes i32)
+ *        argmax_combine  (P1 IN, P2 IN, labels OUT i32[rows], rows i32,
+ *                         classes i32)                 argmax(P1+P2), lowest
+ *  HITS  spmv_partition  (rowptr IN i32[n+1], part OUT, n i32, nnz i32)
+ *        spmv_csr        (rowptr IN, col IN i32[nnz], val IN f32[nnz],
+ *                         x IN f32[n], part IN, y OUT f32[n], carry INOUT,
+ *                         n i32, nnz i32)                         y = A x
+ *        l2norm          (x IN f32[n], norm OUT f32[1], scratch INOUT, n i64)
+ *        scale           (x INOUT f32[n], norm IN f32[1], n i64)
+ *                                                x := x/norm (norm 0: kept)
+ *  DL    conv3x3_relu_pool (x IN bf16[n*3*h*w], wt IN bf16[64*3*3*3],
+ *                         bias IN f32[64], out OUT bf16[n*64*(h/2)*(w/2)],
+ *                         status INOUT i32[1], n i32, h i32, w i32)
+ *                         3x3 conv (zero pad 1) + bias + ReLU + 2x2 max-pool
+ *                         on the tensor cores; h even, w a multiple of 8, x
+ *                         and out 16-byte aligned; status := 1 if a tensor-core
+ *                         or copy wait timed out (the output is then
+ *                         incomplete), 2 if the kernel's shared-memory window
+ *                         was not 128-byte aligned (nothing computed)
+ *        avgpool_global  (p IN bf16[planes*hw], e OUT f32[planes],
+ *                         planes i32, hw i32)               plane means
+ *        concat_dense    (e1 IN f32[n*c], e2 IN f32[n*c],
+ *                         wd IN f32[2c*classes], bd IN f32[classes],
+ *                         out OUT f32[n*classes], n i32, c i32, classes i32)
+ *                                                  out = [e1 e2] wd + bd
+ * Scratch and part/carry sizes come from gdag_scratch_bytes.
+ * Errors: NOT_FOUND. */
 int gdag_kernel_lookup(gdag_ctx *ctx, const char *name, gdag_kernel *out);
 
 /* Number of arguments of kernel k and its signature (spec may be NULL). */

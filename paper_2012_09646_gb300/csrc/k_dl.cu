@@ -6,25 +6,63 @@
 //   avgpool_global     mean of every (image, channel) plane -> f32 embedding
 //   concat_dense       out = [e1 e2] wd + bd, fp32
 //
-// conv3x3_relu_pool is an implicit GEMM: one CTA owns two output rows x 64
-// output columns of one image, i.e. M = 128 pixels, N = 64 channels and
-// K = 27 taps (3 channels x 3 x 3) padded to 32.  The CTA stages its input
-// halo in shared memory, builds the im2col tile A (128 x 32) and the weights B
-// (64 x 32) in the canonical K-major layout without swizzle (8-row x 16-byte
-// core matrices; 128 B between core matrices adjacent in K, 512 B between
-// core matrices adjacent in M or N), and one thread issues two
-// tcgen05.mma.cta_group::1.kind::f16 (K = 16 each) into a 128-lane x 64-column
-// fp32 accumulator in tensor memory.  Completion comes through
-// tcgen05.commit on an mbarrier; the epilogue reads the accumulator with
-// tcgen05.ld (one pixel per thread, 64 channels), takes the 2x2 maximum
-// (horizontal pairs by shuffle, the two rows through shared memory), adds the
-// bias and applies ReLU after the pooling (both commute with the maximum),
-// and writes the pooled bf16 outputs.  Every wait is bounded: past about one
-// second the CTA records status[0] = 1, skips its epilogue, frees its tensor
-// memory and returns.
+// conv3x3_relu_pool is an implicit GEMM on a persistent grid of one
+// 416-thread CTA per SM that holds all 512 tensor-memory columns: two sets of
+// accumulators, so that the tensor cores fill one set while the epilogue
+// drains the other.  A tile is two input rows x 256 input columns of one
+// image; its 512 pixels form four M = 128 operands, one per position in the
+// 2x2 pooling window: accumulator a = 2*dy + p holds the pixels of row y0+dy
+// and column parity p, so row m of every accumulator belongs to pooled column
+// x0/2 + m and the pooling maximum is taken inside one thread, with no
+// exchange.  N = 64 output channels, K = 27 taps padded to 32, fp32
+// accumulation in tensor memory (four 128-lane x 64-column accumulators per
+// set).
+//
+// K order.  A thread builds its im2col row from three aligned 32-bit words of
+// each staged input row: L = columns (2m-2, 2m-1), C = (2m, 2m+1) and
+// R = (2m+2, 2m+3) relative to x0.  The pixel of parity 0 takes taps
+// (hi L, lo C, hi C), the pixel of parity 1 (lo C, hi C, lo R), so for both
+// parities the word C supplies two taps as they are, and the third taps of the
+// nine (channel, tap row) pairs are packed two per word.  K positions 0..17
+// are the nine C words, 18..26 the nine lone taps, 27 and 28 carry the bias
+// (A = 1, B = the bias split into a bf16 high part and a bf16 remainder, so
+// the fp32 accumulator receives it to about 2^-18 relative), 29..31 are zero;
+// the weight operand B_p is laid out in the same order, one per parity.  Operands use
+// the canonical K-major layout without swizzle (8-row x 16-byte core
+// matrices, 128 B between K-adjacent and 512 B between M/N-adjacent ones).
+//
+// Warp roles, per tile t (set s = t % 2):
+//   warp 0 (control, one lane): keeps the halo copies (3 channels x 4 rows x
+//     272 columns per tile, two cp.async.bulk.tensor boxes, zeros outside
+//     the image, box slots padded to 128-byte boundaries) eight tiles ahead
+//     in a ring of buffers, each completing on its own mbarrier; once the
+//     producers have written A set s ("A full") and the epilogue has
+//     drained accumulator set s ("empty", tile t-2), issues eight
+//     tcgen05.mma.cta_group::1.kind::f16 (K = 16 each) and commits them to
+//     the set's "full" mbarrier.
+//   warps 1-4 (producers): wait for the tile's halo and for the MMAs of tile
+//     t-2 to have read A set s, build A set s (thread m writes row m of the
+//     four operands), and arrive on "A full", one arrival per warp.
+//   warps 5-12 (epilogue): wait for "full", read the accumulators with
+//     tcgen05.ld (warp w reads lanes 32*(w%4).. and channels 32*((w-5)/4)..),
+//     signal "empty", take the maximum of the four (bias included; ReLU
+//     commutes with the maximum), convert channel pairs to bf16 with ReLU in
+//     one instruction and stage the pooled tile (64 channels x 128 columns,
+//     double-buffered) in shared memory, from where one thread writes it
+//     with one TMA tensor store (8-byte vector stores by all 256 threads when
+//     a pooled row is not a multiple of 8 values).
+// Every wait is bounded (about one second) and also ends when another role
+// raises the shared abort flag; a warp or role decides to stop with a vote
+// (__all_sync, or a barrier that ANDs its threads' results), so no barrier is
+// left half-arrived.
+// On an abort the CTA records status[0] = 1, lets its copies and MMAs in
+// flight land (bounded), frees its tensor memory and returns.
+#include <cuda.h>  // CUtensorMap and its enums (the encoder comes from the runtime's driver entry point)
 #include <cuda_bf16.h>
 
+#include <cstring>
 #include <initializer_list>
+#include <mutex>
 #include <vector>
 
 #include "catalog.h"
@@ -33,8 +71,36 @@
 namespace gdag {
 
 constexpr int kConvM = 128, kConvN = 64, kConvK = 32, kConvTaps = 27;
-constexpr int kConvCols = 64;  // output columns per CTA
-constexpr int kConvThreads = 128;
+constexpr int kCtlThreads = 32;                      // warp 0: halo copies and MMA issue (one lane)
+constexpr int kProdThreads = 128;                    // warps 1-4: im2col
+constexpr int kEpiThreads = 256;                     // warps 5-12: epilogue and stores
+constexpr int kConvThreads = kCtlThreads + kProdThreads + kEpiThreads;
+constexpr int kTileCols = 256;                       // input columns per tile
+constexpr int kHaloBox = 136;                        // columns per TMA box (two boxes: x0-8 .. x0+263)
+constexpr int kHaloBoxBytes = kHaloBox * 4 * 3 * 2;  // 3 channels x 4 rows, bf16: the bytes one box moves
+constexpr int kHaloBoxStride = (kHaloBoxBytes + 127) / 128 * 128;  // TMA destinations are 128-byte aligned
+constexpr int kHaloBytes = 2 * kHaloBoxStride;       // one halo buffer
+constexpr int kHaloBufs = 8;                         // halo ring depth: copies run this many tiles ahead
+constexpr int kOpABytes = kConvM * kConvK * 2;       // 8 KB per accumulator
+constexpr int kOpASet = 4 * kOpABytes;               // the four A operands of one tile
+constexpr int kOpBBytes = kConvN * kConvK * 2;       // 4 KB per parity
+constexpr int kAccCols = 4 * kConvN;                 // one accumulator set: 256 columns
+constexpr int kTmemCols = 2 * kAccCols;              // two sets: the SM's 512 columns
+constexpr int kStageBytes = kConvN * (kTileCols / 2) * 2;  // pooled tile [64][128] bf16
+constexpr int kOffB = 2 * kOpASet;
+constexpr int kOffHalo = kOffB + 2 * kOpBBytes;
+constexpr int kOffStage = kOffHalo + kHaloBufs * kHaloBytes;
+constexpr int kOffBars = kOffStage + 2 * kStageBytes;
+// halo full x kHaloBufs, A full x2, accumulator full x2, accumulator empty x2
+constexpr int kNumBars = kHaloBufs + 6;
+constexpr size_t kConvSmemUsed = kOffBars + kNumBars * 8 + 16;
+// requested dynamic shared memory: more than half of the SM's 228 KB, so that
+// one CTA (holding all 512 tensor-memory columns) owns an SM
+constexpr size_t kConvSmem = 160 * 1024;
+static_assert(kConvSmemUsed <= kConvSmem, "conv shared memory");
+static_assert(kOffHalo % 128 == 0 && kHaloBoxStride % 128 == 0 && kHaloBytes % 128 == 0 && kOffStage % 128 == 0 &&
+                  kStageBytes % 128 == 0 && (kHaloBox * 2) % 16 == 0,
+              "TMA shared-memory addresses must be 128-byte aligned, box rows multiples of 16 bytes");
 
 __device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -59,184 +125,428 @@ __device__ __forceinline__ uint64_t umma_desc(uint32_t addr)
 constexpr uint32_t kConvIdesc =
     (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kConvN >> 3) << 17) | ((uint32_t)(kConvM >> 4) << 24);
 
-__global__ void __launch_bounds__(kConvThreads) conv3x3_relu_pool_kernel(const __nv_bfloat16 *__restrict__ x,
-                                                                         const __nv_bfloat16 *__restrict__ wt,
-                                                                         const float *__restrict__ bias,
-                                                                         __nv_bfloat16 *__restrict__ out,
-                                                                         int *status, int n, int h, int w)
+// weight index ci*9 + ky*3 + kx held at K position k of parity p's operand,
+// -1 for the bias and zero positions 27..31 (the K order above)
+__host__ __device__ __forceinline__ int conv_tap(int p, int k)
 {
-    __shared__ __align__(128) unsigned char sa[kConvM * kConvK * 2];
-    __shared__ __align__(128) unsigned char sb[kConvN * kConvK * 2];
-    __shared__ __nv_bfloat16 s_in[3][4][kConvCols + 2];
-    __shared__ float s_pool[kConvN][kConvCols / 2 + 1];
-    __shared__ __align__(8) uint64_t mbar;
-    __shared__ uint32_t tmem_base;
-
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int tiles_x = w / kConvCols, rows2 = h / 2;
-    const int bx = blockIdx.x % tiles_x;
-    const int by = (blockIdx.x / tiles_x) % rows2;
-    const int b = blockIdx.x / (tiles_x * rows2);
-    const int y0 = 2 * by, x0 = bx * kConvCols;
-
-    // input halo: channels 0..2, rows y0-1 .. y0+2, columns x0-1 .. x0+64
-    for (int i = tid; i < 3 * 4 * (kConvCols + 2); i += kConvThreads) {
-        const int ch = i / (4 * (kConvCols + 2)), rem = i - ch * 4 * (kConvCols + 2);
-        const int r = rem / (kConvCols + 2), c = rem - r * (kConvCols + 2);
-        const int yy = y0 - 1 + r, xx = x0 - 1 + c;
-        const bool in = yy >= 0 && yy < h && xx >= 0 && xx < w;
-        s_in[ch][r][c] = in ? x[(((size_t)b * 3 + ch) * h + yy) * w + xx] : __float2bfloat16(0.f);
+    const int i = k >> 1, half = k & 1;
+    if (i < 9) return (i / 3) * 9 + (i % 3) * 3 + (p == 0 ? 1 : 0) + half;
+    if (i < 14) {
+        const int q = 2 * (i - 9) + half;
+        return q < 9 ? (q / 3) * 9 + (q % 3) * 3 + (p == 0 ? 0 : 2) : -1;
     }
-    // weights B: row co, column k = ci*9 + dy*3 + dx, zero past 27
-    for (int i = tid; i < kConvN * kConvK; i += kConvThreads) {
-        const int co = i / kConvK, k = i - co * kConvK;
-        *reinterpret_cast<__nv_bfloat16 *>(sb + umma_off(co, k)) =
-            k < kConvTaps ? wt[co * kConvTaps + k] : __float2bfloat16(0.f);
-    }
-    if (tid == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&mbar)));
-        asm volatile("fence.mbarrier_init.release.cluster;");
-    }
-    if (warp == 0) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 64;" ::"r"(smem_addr(&tmem_base)));
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
-    }
-    __syncthreads();
-
-    // im2col row of this thread's pixel: p = r * 64 + c
-    {
-        const int r = tid >> 6, c = tid & 63;
-        __nv_bfloat16 v[kConvK];
-#pragma unroll
-        for (int k = 0; k < kConvK; ++k) {
-            if (k < kConvTaps) {
-                const int ci = k / 9, dy = (k % 9) / 3, dx = k % 3;
-                v[k] = s_in[ci][r + dy][c + dx];
-            } else {
-                v[k] = __float2bfloat16(0.f);
-            }
-        }
-#pragma unroll
-        for (int kc = 0; kc < kConvK / 8; ++kc) {
-            uint4 q;
-            q.x = (uint32_t)__bfloat16_as_ushort(v[8 * kc + 0]) | ((uint32_t)__bfloat16_as_ushort(v[8 * kc + 1]) << 16);
-            q.y = (uint32_t)__bfloat16_as_ushort(v[8 * kc + 2]) | ((uint32_t)__bfloat16_as_ushort(v[8 * kc + 3]) << 16);
-            q.z = (uint32_t)__bfloat16_as_ushort(v[8 * kc + 4]) | ((uint32_t)__bfloat16_as_ushort(v[8 * kc + 5]) << 16);
-            q.w = (uint32_t)__bfloat16_as_ushort(v[8 * kc + 6]) | ((uint32_t)__bfloat16_as_ushort(v[8 * kc + 7]) << 16);
-            *reinterpret_cast<uint4 *>(sa + umma_off(tid, 8 * kc)) = q;
-        }
-    }
-    asm volatile("fence.proxy.async.shared::cta;");  // generic-proxy stores -> tensor core reads
-    __syncthreads();
-    asm volatile("tcgen05.fence::after_thread_sync;");
-    const uint32_t tmem = tmem_base;
-    if (tid == 0) {
-#pragma unroll
-        for (int ks = 0; ks < kConvK / 16; ++ks) {
-            const uint64_t ad = umma_desc(smem_addr(sa) + ks * 256);
-            const uint64_t bd = umma_desc(smem_addr(sb) + ks * 256);
-            asm volatile("{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
-                         " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(tmem),
-                         "l"(ad), "l"(bd), "r"(kConvIdesc), "r"((uint32_t)ks));
-        }
-        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-            smem_addr(&mbar)));
-    }
-    // bounded wait for the accumulator (about 1 s at GB300 clocks)
-    uint32_t ok = 0;
-    const long long t0 = clock64();
-    while (!ok) {
-        asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n selp.u32 %0, 1, 0, p;\n}"
-                     : "=r"(ok)
-                     : "r"(smem_addr(&mbar)));
-        if (!ok && clock64() - t0 > 2000000000LL) break;
-    }
-    ok = __syncthreads_and(ok);
-    asm volatile("tcgen05.fence::after_thread_sync;");
-    if (!ok) {
-        if (tid == 0) atomicExch(status, 1);
-    } else {
-        uint32_t acc[kConvN];
-        const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16);
-        asm volatile(
-            "tcgen05.ld.sync.aligned.32x32b.x64.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-            "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32,%33,%34,%35,%36,%37,%38,%39,"
-            "%40,%41,%42,%43,%44,%45,%46,%47,%48,%49,%50,%51,%52,%53,%54,%55,%56,%57,%58,%59,%60,%61,%62,%63}, [%64];"
-            : "=r"(acc[0]), "=r"(acc[1]), "=r"(acc[2]), "=r"(acc[3]), "=r"(acc[4]), "=r"(acc[5]), "=r"(acc[6]),
-              "=r"(acc[7]), "=r"(acc[8]), "=r"(acc[9]), "=r"(acc[10]), "=r"(acc[11]), "=r"(acc[12]), "=r"(acc[13]),
-              "=r"(acc[14]), "=r"(acc[15]), "=r"(acc[16]), "=r"(acc[17]), "=r"(acc[18]), "=r"(acc[19]),
-              "=r"(acc[20]), "=r"(acc[21]), "=r"(acc[22]), "=r"(acc[23]), "=r"(acc[24]), "=r"(acc[25]),
-              "=r"(acc[26]), "=r"(acc[27]), "=r"(acc[28]), "=r"(acc[29]), "=r"(acc[30]), "=r"(acc[31]),
-              "=r"(acc[32]), "=r"(acc[33]), "=r"(acc[34]), "=r"(acc[35]), "=r"(acc[36]), "=r"(acc[37]),
-              "=r"(acc[38]), "=r"(acc[39]), "=r"(acc[40]), "=r"(acc[41]), "=r"(acc[42]), "=r"(acc[43]),
-              "=r"(acc[44]), "=r"(acc[45]), "=r"(acc[46]), "=r"(acc[47]), "=r"(acc[48]), "=r"(acc[49]),
-              "=r"(acc[50]), "=r"(acc[51]), "=r"(acc[52]), "=r"(acc[53]), "=r"(acc[54]), "=r"(acc[55]),
-              "=r"(acc[56]), "=r"(acc[57]), "=r"(acc[58]), "=r"(acc[59]), "=r"(acc[60]), "=r"(acc[61]),
-              "=r"(acc[62]), "=r"(acc[63])
-            : "r"(taddr));
-        asm volatile("tcgen05.wait::ld.sync.aligned;");
-        // pixel p = warp*32 + lane: row p / 64, column p % 64; pool pairs of
-        // columns (lanes l, l^1), then the two rows (warps w, w+2)
-        float v[kConvN];
-#pragma unroll
-        for (int ch = 0; ch < kConvN; ++ch) {
-            const float a = __uint_as_float(acc[ch]);
-            v[ch] = fmaxf(a, __shfl_xor_sync(0xffffffffu, a, 1));
-        }
-        const int c = (tid & 63), pc = c >> 1;
-        if (warp >= 2 && (lane & 1) == 0) {
-#pragma unroll
-            for (int ch = 0; ch < kConvN; ++ch) s_pool[ch][pc] = v[ch];
-        }
-        __syncthreads();
-        if (warp < 2 && (lane & 1) == 0) {
-            const int ho = h / 2, wo = w / 2;
-            __nv_bfloat16 *o = out + (((size_t)b * kConvN) * ho + by) * wo + (x0 >> 1) + pc;
-#pragma unroll
-            for (int ch = 0; ch < kConvN; ++ch) {
-                const float m = fmaxf(v[ch], s_pool[ch][pc]) + bias[ch];
-                o[(size_t)ch * ho * wo] = __float2bfloat16_rn(fmaxf(m, 0.f));
-            }
-        }
-    }
-    asm volatile("tcgen05.fence::before_thread_sync;");
-    __syncthreads();
-    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 64;" ::"r"(tmem));
+    return -1;
 }
 
-// e[p] = mean of plane p (hw bf16 values): 128-bit loads, fp32 per thread,
-// fixed-order block tree; one block per plane.
+// wait for phase `parity` of the mbarrier at `bar`; false after about one
+// second or once another thread has raised *abort
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity, const volatile int *abort)
+{
+    const long long t0 = clock64();
+    while (true) {
+        uint32_t done;
+        asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+                     : "=r"(done)
+                     : "r"(bar), "r"(parity)
+                     : "memory");
+        if (done) return true;
+        if (*abort || clock64() - t0 > 2000000000LL) return false;
+    }
+}
+
+// named barrier `id` over `n` threads that also ANDs v across them
+__device__ __forceinline__ bool bar_and(int id, int n, bool v)
+{
+    uint32_t r;
+    asm volatile("{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n bar.red.and.pred q, %2, %3, p;\n selp.u32 %0, 1, 0, q;\n}"
+                 : "=r"(r)
+                 : "r"((uint32_t)v), "r"(id), "r"(n)
+                 : "memory");
+    return r != 0;
+}
+
+__device__ __forceinline__ void conv_tile_coords(int tile, int tiles_x, int rows2, int &b, int &y0, int &x0)
+{
+    const int xt = tile % tiles_x;
+    const int r2 = (tile / tiles_x) % rows2;
+    b = tile / (tiles_x * rows2);
+    y0 = 2 * r2;
+    x0 = xt * kTileCols;
+}
+
+// halo of one tile by TMA: two boxes of 136 columns x 4 rows x 3 channels
+// starting at (x0 - 8, y0 - 1, 3b) of the image tensor (columns, rows,
+// image*3 + channel); the hardware fills zeros outside the image, including
+// the negative first column and row.  Issued by one thread; completion is
+// counted in bytes on `bar`.
+__device__ __forceinline__ void conv_issue_halo(const CUtensorMap *tin, unsigned char *dst, uint32_t bar, int tile,
+                                                int tiles_x, int rows2)
+{
+    int b, y0, x0;
+    conv_tile_coords(tile, tiles_x, rows2, b, y0, x0);
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(2 * kHaloBoxBytes) : "memory");
+#pragma unroll
+    for (int half = 0; half < 2; ++half)
+        asm volatile(
+            "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(
+                smem_addr(dst + half * kHaloBoxStride)),
+            "l"(reinterpret_cast<uint64_t>(tin)), "r"(x0 - 8 + half * kHaloBox), "r"(y0 - 1), "r"(3 * b), "r"(bar)
+            : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+__global__ void __launch_bounds__(kConvThreads, 1)
+    conv3x3_relu_pool_kernel(const __grid_constant__ CUtensorMap tin, const __grid_constant__ CUtensorMap tout,
+                             const __nv_bfloat16 *__restrict__ wt, const float *__restrict__ bias,
+                             __nv_bfloat16 *__restrict__ out, int *status, int n, int h, int w, int tma_store)
+{
+    extern __shared__ __align__(1024) unsigned char conv_smem[];
+    unsigned char *sa = conv_smem;                  // two sets of four A operands
+    unsigned char *sb = conv_smem + kOffB;          // two B operands
+    unsigned char *halo = conv_smem + kOffHalo;     // two halo buffers [box][ci][row][136]
+    unsigned char *stage = conv_smem + kOffStage;   // two pooled tiles [64][128]
+    uint64_t *bars = reinterpret_cast<uint64_t *>(conv_smem + kOffBars);
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + kNumBars);
+    volatile int *abort = reinterpret_cast<volatile int *>(tmem_slot + 1);
+
+    // the TMA copies need a 128-byte aligned window: check before any copy
+    // or tensor-memory use (uniform over the CTA)
+    if ((smem_addr(conv_smem) & 127u) != 0) {
+        if (threadIdx.x == 0) atomicExch(status, 2);
+        return;
+    }
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int tiles_x = (w + kTileCols - 1) / kTileCols, rows2 = h / 2;
+    const int ntiles = n * rows2 * tiles_x;
+    const int ho = h / 2, wo = w / 2;
+    const uint32_t halo_bar = smem_addr(&bars[0]);  // + 8 * buffer: the tile's halo landed
+    const uint32_t afull_bar = smem_addr(&bars[kHaloBufs]);      // + 8 * set: A written (and the halo read)
+    const uint32_t full_bar = smem_addr(&bars[kHaloBufs + 2]);   // + 8 * set: MMAs done (A read, accumulators ready)
+    const uint32_t empty_bar = smem_addr(&bars[kHaloBufs + 4]);  // + 8 * set: epilogue done reading the accumulators
+
+    if (warp == 0) {
+        if (lane == 0) {
+            *abort = 0;
+            asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tin)) : "memory");
+            for (int j = 0; j < kHaloBufs; ++j) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(halo_bar + 8 * j));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(afull_bar), "r"(kProdThreads / 32));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(afull_bar + 8), "r"(kProdThreads / 32));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(full_bar));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(full_bar + 8));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(empty_bar), "r"(kEpiThreads / 32));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(empty_bar + 8), "r"(kEpiThreads / 32));
+            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        }
+        __syncwarp();
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(tmem_slot)),
+                     "n"(kTmemCols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();  // barriers initialised, tensor memory allocated
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 0) {
+        // ---- control (one lane): halo copies kHaloBufs tiles ahead, MMA issue
+        int issued_halo = 0, issued_mma = 0;  // tiles of this CTA (in order) whose copies / MMAs were issued
+        if (lane == 0)
+            for (int j = 0; j < kHaloBufs; ++j)
+                if ((int)blockIdx.x + j * (int)gridDim.x < ntiles) {
+                    conv_issue_halo(&tin, halo + j * kHaloBytes, halo_bar + 8 * j, blockIdx.x + j * gridDim.x,
+                                    tiles_x, rows2);
+                    ++issued_halo;
+                }
+        __syncwarp();
+        // the whole warp meets the epilogue warps, which staged the weights
+        asm volatile("bar.sync 3, %0;" ::"n"(kCtlThreads + kEpiThreads) : "memory");
+        if (lane == 0) {
+            uint32_t it = 0;
+            for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
+                const int s = it & 1;
+                // A set s written and halo buffer s read by the producers
+                if (!mbar_wait_bounded(afull_bar + 8 * s, (it >> 1) & 1, abort)) {
+                    *abort = 1;
+                    break;
+                }
+                // halo buffer it % kHaloBufs was read by the producers for this tile
+                const int ahead = tile + kHaloBufs * gridDim.x, hb = it % kHaloBufs;
+                if (ahead < ntiles) {
+                    conv_issue_halo(&tin, halo + hb * kHaloBytes, halo_bar + 8 * hb, ahead, tiles_x, rows2);
+                    ++issued_halo;
+                }
+                // accumulator set s drained by the epilogue of tile it-2
+                if (it >= 2 && !mbar_wait_bounded(empty_bar + 8 * s, ((it >> 1) - 1) & 1, abort)) {
+                    *abort = 1;
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;");
+                const unsigned char *As = sa + s * kOpASet;
+#pragma unroll
+                for (int a = 0; a < 4; ++a)
+#pragma unroll
+                    for (int ks = 0; ks < kConvK / 16; ++ks) {
+                        const uint64_t ad = umma_desc(smem_addr(As + a * kOpABytes) + ks * 256);
+                        const uint64_t bd = umma_desc(smem_addr(sb + (a & 1) * kOpBBytes) + ks * 256);
+                        asm volatile("{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
+                                     " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(
+                                         tmem + s * kAccCols + a * kConvN),
+                                     "l"(ad), "l"(bd), "r"(kConvIdesc), "r"((uint32_t)ks));
+                    }
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                    full_bar + 8 * s));
+                ++issued_mma;
+            }
+            if (*abort) {
+                // let the copies and MMAs in flight land before the CTA frees
+                // its memory (bounded waits that ignore the abort flag)
+                const volatile int no_abort = 0;
+                // the last copy into buffer j was tile index jl = the largest
+                // index below issued_halo that is j modulo kHaloBufs
+                for (int j = 0; j < kHaloBufs && j < issued_halo; ++j) {
+                    const int jl = j + (issued_halo - 1 - j) / kHaloBufs * kHaloBufs;
+                    mbar_wait_bounded(halo_bar + 8 * j, (jl / kHaloBufs) & 1, &no_abort);
+                }
+                if (issued_mma > 0) {
+                    const int last = issued_mma - 1;
+                    mbar_wait_bounded(full_bar + 8 * (last & 1), (last >> 1) & 1, &no_abort);
+                }
+            }
+        }
+        __syncwarp();
+    } else if (warp <= kProdThreads / 32) {
+        // ---- producers: row m of the four A operands of every tile
+        const int m = tid - kCtlThreads;
+        int woff[3];  // byte offsets of halo words m+3, m+4, m+5 (L, C, R), each in its box
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            const int wq = m + 3 + q, box = wq >= kHaloBox / 2;
+            woff[q] = box * kHaloBoxStride + (wq - box * (kHaloBox / 2)) * 4;
+        }
+        uint32_t it = 0;
+        for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
+            const int s = it & 1, hb = it % kHaloBufs;
+            const bool hok = mbar_wait_bounded(halo_bar + 8 * hb, (it / kHaloBufs) & 1, abort);
+            // A set s was last read by the MMAs of tile it-2
+            const bool aok = it < 2 || mbar_wait_bounded(full_bar + 8 * s, ((it >> 1) - 1) & 1, abort);
+            if (!__all_sync(0xffffffffu, hok && aok)) {  // warp-uniform: the warp meets at __syncwarp below
+                if (lane == 0) *abort = 1;
+                break;
+            }
+            const unsigned char *hbuf = halo + hb * kHaloBytes;
+            uint32_t Lw[12], Cw[12], Rw[12];  // [ci][row 0..3]
+#pragma unroll
+            for (int ci = 0; ci < 3; ++ci)
+#pragma unroll
+                for (int r = 0; r < 4; ++r) {
+                    const unsigned char *row = hbuf + (ci * 4 + r) * (kHaloBox * 2);
+                    Lw[ci * 4 + r] = *reinterpret_cast<const uint32_t *>(row + woff[0]);
+                    Cw[ci * 4 + r] = *reinterpret_cast<const uint32_t *>(row + woff[1]);
+                    Rw[ci * 4 + r] = *reinterpret_cast<const uint32_t *>(row + woff[2]);
+                }
+            unsigned char *As = sa + s * kOpASet;
+#pragma unroll
+            for (int dy = 0; dy < 2; ++dy)
+#pragma unroll
+                for (int p = 0; p < 2; ++p) {
+                    uint32_t wd[16];
+#pragma unroll
+                    for (int i = 0; i < 9; ++i) wd[i] = Cw[(i / 3) * 4 + dy + i % 3];
+#pragma unroll
+                    for (int i = 0; i < 5; ++i) {
+                        const int q0 = 2 * i, q1 = 2 * i + 1;
+                        const int r0 = (q0 / 3) * 4 + dy + q0 % 3, r1 = q1 < 9 ? (q1 / 3) * 4 + dy + q1 % 3 : 0;
+                        if (p == 0)
+                            wd[9 + i] = __byte_perm(Lw[r0], q1 < 9 ? Lw[r1] : 0u, 0x7632);
+                        else
+                            wd[9 + i] = __byte_perm(Rw[r0], q1 < 9 ? Rw[r1] : 0u, 0x5410);
+                    }
+                    wd[13] |= 0x3F800000u;  // K 27: 1.0 (bias, high part)
+                    wd[14] = 0x00003F80u;    // K 28: 1.0 (bias, remainder)
+                    wd[15] = 0u;
+                    unsigned char *A = As + (2 * dy + p) * kOpABytes;
+#pragma unroll
+                    for (int kc = 0; kc < 4; ++kc)
+                        *reinterpret_cast<uint4 *>(A + umma_off(m, 8 * kc)) =
+                            make_uint4(wd[4 * kc], wd[4 * kc + 1], wd[4 * kc + 2], wd[4 * kc + 3]);
+                }
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // generic stores -> tensor-core reads
+            __syncwarp();
+            if (lane == 0) mbar_arrive(afull_bar + 8 * s);
+        }
+    } else {
+        // ---- epilogue: stage the weights once, then per tile read TMEM lanes
+        // 32*quad.., channels 32*chalf .. +31, pooled column x0/2 + mo
+        const int etid = tid - kCtlThreads - kProdThreads;
+        {
+            constexpr int kPer = 2 * kConvN * kConvK / kEpiThreads;
+            __nv_bfloat16 wv[kPer];
+#pragma unroll
+            for (int r = 0; r < kPer; ++r) {
+                const int i = etid + r * kEpiThreads;
+                const int p = i / (kConvN * kConvK), co = (i / kConvK) % kConvN, k = i % kConvK;
+                const int tap = conv_tap(p, k);
+                __nv_bfloat16 v = __float2bfloat16(0.f);
+                if (tap >= 0) {
+                    v = wt[co * kConvTaps + tap];
+                } else if (k == 27 || k == 28) {
+                    const float bb = bias[co];
+                    const __nv_bfloat16 hi = __float2bfloat16_rn(bb);
+                    v = k == 27 ? hi : __float2bfloat16_rn(bb - __bfloat162float(hi));
+                }
+                wv[r] = v;
+            }
+#pragma unroll
+            for (int r = 0; r < kPer; ++r) {
+                const int i = etid + r * kEpiThreads;
+                const int p = i / (kConvN * kConvK), co = (i / kConvK) % kConvN, k = i % kConvK;
+                *reinterpret_cast<__nv_bfloat16 *>(sb + p * kOpBBytes + umma_off(co, k)) = wv[r];
+            }
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // B: generic stores -> tensor-core reads
+            asm volatile("bar.sync 3, %0;" ::"n"(kCtlThreads + kEpiThreads) : "memory");
+        }
+        const int ew = warp - (kCtlThreads + kProdThreads) / 32, quad = warp & 3, chalf = ew >> 2;
+        const int mo = quad * 32 + lane;
+        uint32_t it = 0;
+        for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
+            const int s = it & 1;
+            const bool fok = mbar_wait_bounded(full_bar + 8 * s, (it >> 1) & 1, abort);
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            unsigned char *sg = stage + s * kStageBytes;
+#pragma unroll
+            for (int chunk = 0; chunk < 2; ++chunk) {
+                const int c0 = 32 * chalf + 16 * chunk;
+                uint32_t v[4][16];
+#pragma unroll
+                for (int a = 0; a < 4; ++a) {
+                    const uint32_t taddr = tmem + ((uint32_t)(quad * 32) << 16) + s * kAccCols + a * kConvN + c0;
+                    asm volatile(
+                        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                        : "=r"(v[a][0]), "=r"(v[a][1]), "=r"(v[a][2]), "=r"(v[a][3]), "=r"(v[a][4]), "=r"(v[a][5]),
+                          "=r"(v[a][6]), "=r"(v[a][7]), "=r"(v[a][8]), "=r"(v[a][9]), "=r"(v[a][10]), "=r"(v[a][11]),
+                          "=r"(v[a][12]), "=r"(v[a][13]), "=r"(v[a][14]), "=r"(v[a][15])
+                        : "r"(taddr));
+                }
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                if (chunk == 1) {
+                    // this warp is done with accumulator set s
+                    asm volatile("tcgen05.fence::before_thread_sync;");
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(empty_bar + 8 * s);
+                }
+                uint16_t *st = reinterpret_cast<uint16_t *>(sg) + c0 * (kTileCols / 2) + mo;
+#pragma unroll
+                for (int j = 0; j < 16; j += 2) {
+                    float m0, m1;
+                    asm("max.f32 %0, %1, %2, %3;"
+                        : "=f"(m0)
+                        : "f"(__uint_as_float(v[0][j])), "f"(__uint_as_float(v[1][j])), "f"(__uint_as_float(v[2][j])));
+                    asm("max.f32 %0, %1, %2, %3;"
+                        : "=f"(m1)
+                        : "f"(__uint_as_float(v[0][j + 1])), "f"(__uint_as_float(v[1][j + 1])),
+                          "f"(__uint_as_float(v[2][j + 1])));
+                    m0 = fmaxf(m0, __uint_as_float(v[3][j]));
+                    m1 = fmaxf(m1, __uint_as_float(v[3][j + 1]));
+                    uint32_t pk;  // channel c0+j in the low half, c0+j+1 in the high half
+                    asm("cvt.rn.relu.bf16x2.f32 %0, %1, %2;" : "=r"(pk) : "f"(m1), "f"(m0));
+                    st[j * (kTileCols / 2)] = (uint16_t)(pk & 0xFFFFu);
+                    st[(j + 1) * (kTileCols / 2)] = (uint16_t)(pk >> 16);
+                }
+            }
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // staging writes -> TMA store reads
+            // the store of the previous tile must be done reading its staging
+            // buffer before the next tile writes it
+            if (etid == 0 && tma_store) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+            if (!bar_and(2, kEpiThreads, fok && !*abort)) {
+                if (etid == 0) *abort = 1;
+                break;
+            }
+            int b, y0, x0;
+            conv_tile_coords(tile, tiles_x, rows2, b, y0, x0);
+            if (tma_store) {
+                // one TMA store of the 128 x 1 x 64 box at (x0/2, y0/2, 64b);
+                // the hardware drops the columns past the image edge
+                if (etid == 0) {
+                    asm volatile(
+                        "cp.async.bulk.tensor.3d.global.shared::cta.bulk_group [%0, {%1, %2, %3}], [%4];" ::"l"(
+                            reinterpret_cast<uint64_t>(&tout)),
+                        "r"(x0 >> 1), "r"(y0 >> 1), "r"(kConvN * b), "r"(smem_addr(sg))
+                        : "memory");
+                    asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+                }
+            } else {
+                // pooled rows not a multiple of 8 values: 8-byte stores of
+                // whole vectors (the valid width, wo - x0/2 capped at 128, is
+                // a multiple of 4); the next tile writes the other buffer
+                const int valid = min(kTileCols / 2, wo - (x0 >> 1));
+                __nv_bfloat16 *orow = out + (((size_t)b * kConvN) * ho + (y0 >> 1)) * wo + (x0 >> 1);
+                const size_t plane = (size_t)ho * wo;
+                const uint2 *src = reinterpret_cast<const uint2 *>(sg);
+                for (int i = etid; i < kConvN * (kTileCols / 8); i += kEpiThreads) {
+                    const int ch = i / (kTileCols / 8), j = i % (kTileCols / 8);
+                    if (4 * j < valid) *reinterpret_cast<uint2 *>(orow + ch * plane + 4 * j) = src[i];
+                }
+            }
+        }
+        if (etid == 0 && tma_store) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+    }
+    if (tid == 0 && *abort) atomicExch(status, 1);
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "n"(kTmemCols));
+}
+
+// e[p] = mean of plane p (hw bf16 values), fp32 per thread, fixed-order
+// block tree; one block per plane.  128-bit loads when every plane starts on
+// a 16-byte boundary (hw % 8 == 0 and an aligned base), scalar loads
+// otherwise.
 __global__ void __launch_bounds__(256) avgpool_global_kernel(const __nv_bfloat16 *__restrict__ p,
-                                                             float *__restrict__ e, int hw)
+                                                             float *__restrict__ e, int hw, int vec)
 {
     __shared__ double sh[256 / 32];
-    const uint4 *q = reinterpret_cast<const uint4 *>(p + (size_t)blockIdx.x * hw);
     float s = 0.f;
-    for (int i = threadIdx.x; i < hw / 8; i += 256) {
-        const uint4 v = q[i];
-        const uint32_t u[4] = {v.x, v.y, v.z, v.w};
+    if (vec) {
+        const uint4 *q = reinterpret_cast<const uint4 *>(p + (size_t)blockIdx.x * hw);
+#pragma unroll 4
+        for (int i = threadIdx.x; i < hw / 8; i += 256) {
+            const uint4 v = q[i];
+            const uint32_t u[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            s += __uint_as_float(u[k] << 16);
-            s += __uint_as_float(u[k] & 0xFFFF0000u);
+            for (int k = 0; k < 4; ++k) {
+                s += __uint_as_float(u[k] << 16);
+                s += __uint_as_float(u[k] & 0xFFFF0000u);
+            }
         }
+    } else {
+        const __nv_bfloat16 *q = p + (size_t)blockIdx.x * hw;
+        for (int i = threadIdx.x; i < hw; i += 256) s += __bfloat162float(q[i]);
     }
     const double t = block_sum((double)s, sh);
     if (threadIdx.x == 0) e[blockIdx.x] = (float)(t / hw);
 }
 
-// out[b][j] = bd[j] + sum_i e1[b][i] wd[i][j] + sum_i e2[b][i] wd[c+i][j]
-__global__ void concat_dense_kernel(const float *__restrict__ e1, const float *__restrict__ e2,
-                                    const float *__restrict__ wd, const float *__restrict__ bd,
-                                    float *__restrict__ out, int n, int c, int classes)
+// out[b][j] = bd[j] + sum_i e1[b][i] wd[i][j] + sum_i e2[b][i] wd[c+i][j]:
+// one block per image, one warp per class (strided), the 2c products of a
+// logit split over the lanes and summed by a fixed shuffle tree.
+__global__ void __launch_bounds__(256) concat_dense_kernel(const float *__restrict__ e1, const float *__restrict__ e2,
+                                                           const float *__restrict__ wd, const float *__restrict__ bd,
+                                                           float *__restrict__ out, int c, int classes)
 {
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= n * classes) return;
-    const int b = t / classes, j = t - b * classes;
-    float s = bd[j];
-    for (int i = 0; i < c; ++i) s = fmaf(e1[b * c + i], wd[i * classes + j], s);
-    for (int i = 0; i < c; ++i) s = fmaf(e2[b * c + i], wd[(c + i) * classes + j], s);
-    out[t] = s;
+    const int b = blockIdx.x, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int j = warp; j < classes; j += 256 / 32) {
+        float s = 0.f;
+        for (int i = lane; i < 2 * c; i += 32) {
+            const float e = i < c ? e1[(size_t)b * c + i] : e2[(size_t)b * c + (i - c)];
+            s = fmaf(e, wd[(size_t)i * classes + j], s);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) out[(size_t)b * classes + j] = s + bd[j];
+    }
 }
 
 namespace {
@@ -244,41 +554,130 @@ namespace {
 const char *validate_conv(const LaunchArgs &a)
 {
     const int n = a.i32(5), h = a.i32(6), w = a.i32(7);
-    if (n < 1 || h < 2 || w < kConvCols) return "n >= 1, h >= 2, w >= 64 required";
-    if (h % 2 || w % kConvCols) return "h must be even and w a multiple of 64";
-    if ((int64_t)n * (h / 2) * (w / kConvCols) > INT32_MAX) return "too many tiles";
+    if (n < 1 || h < 2 || w < 8) return "n >= 1, h >= 2, w >= 8 required";
+    if (h % 2 || w % 8) return "h must be even and w a multiple of 8";
+    if ((int64_t)n * (h / 2) * ceil_div(w, kTileCols) > INT32_MAX) return "too many tiles";
     if (a.bytes[0] / 2 / 3 / (size_t)h / (size_t)w < (size_t)n) return "x smaller than n x 3 x h x w bf16";
     if (a.bytes[1] < (size_t)kConvN * kConvTaps * 2) return "weights smaller than 64 x 3 x 3 x 3 bf16";
     if (a.bytes[2] < (size_t)kConvN * 4) return "bias smaller than 64 floats";
     if (a.bytes[3] / 2 / kConvN / (size_t)(h / 2) / (size_t)(w / 2) < (size_t)n)
         return "out smaller than n x 64 x h/2 x w/2 bf16";
     if (a.bytes[4] < 4) return "status smaller than one int32";
+    if ((reinterpret_cast<uintptr_t>(a.ptr[0]) & 15) != 0 || (reinterpret_cast<uintptr_t>(a.ptr[3]) & 15) != 0)
+        return "x and out must be 16-byte aligned";
     return nullptr;
 }
+
+using EncodeTiled = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                 const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+// the driver's tensor-map encoder, through the runtime (no link to libcuda)
+EncodeTiled encode_tiled()
+{
+    static EncodeTiled fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiled>(p);
+    }
+    return fn;
+}
+
+// rank-3 bf16 tensor map, dims innermost first, dense; zeros outside
+bool encode_bf16_3d(CUtensorMap *m, void *base, uint64_t d0, uint64_t d1, uint64_t d2, uint32_t b0, uint32_t b1,
+                    uint32_t b2)
+{
+    EncodeTiled fn = encode_tiled();
+    if (!fn) return false;
+    const cuuint64_t dims[3] = {d0, d1, d2};
+    const cuuint64_t strides[2] = {d0 * 2, d0 * d1 * 2};
+    const cuuint32_t box[3] = {b0, b1, b2};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+              CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+struct ConvMaps {
+    const void *x = nullptr, *out = nullptr;
+    int n = 0, h = 0, w = 0;
+    CUtensorMap tin, tout;
+};
 
 int launch_conv(const LaunchArgs &a, void *s)
 {
     const int n = a.i32(5), h = a.i32(6), w = a.i32(7);
-    const unsigned grid = (unsigned)((int64_t)n * (h / 2) * (w / kConvCols));
-    conv3x3_relu_pool_kernel<<<grid, kConvThreads, 0, (cudaStream_t)s>>>(
-        a.p<__nv_bfloat16>(0), a.p<__nv_bfloat16>(1), a.p<float>(2), a.p<__nv_bfloat16>(3), a.p<int>(4), n, h, w);
+    const int wo = w / 2, tma_store = wo % 8 == 0;
+    // per process: raise the dynamic shared-memory limit once (no attribute
+    // calls on later launches, so the launch can be stream-captured), and
+    // keep the tensor maps of the last few (buffer, shape) combinations
+    static std::mutex mu;
+    static bool configured = false;
+    static ConvMaps cache[8];
+    static int cache_next = 0;
+    ConvMaps maps;
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        if (!configured) {
+            cudaError_t e = cudaFuncSetAttribute(conv3x3_relu_pool_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)kConvSmem);
+            if (e != cudaSuccess) return e;
+            configured = true;
+        }
+        int hit = -1;
+        for (int i = 0; i < 8; ++i)
+            if (cache[i].x == a.ptr[0] && cache[i].out == a.ptr[3] && cache[i].n == n && cache[i].h == h &&
+                cache[i].w == w)
+                hit = i;
+        if (hit < 0) {
+            ConvMaps m;
+            m.x = a.ptr[0];
+            m.out = a.ptr[3];
+            m.n = n;
+            m.h = h;
+            m.w = w;
+            std::memset(&m.tin, 0, sizeof m.tin);
+            std::memset(&m.tout, 0, sizeof m.tout);
+            if (!encode_bf16_3d(&m.tin, a.ptr[0], (uint64_t)w, (uint64_t)h, (uint64_t)3 * n, kHaloBox, 4, 3))
+                return cudaErrorNotSupported;
+            if (tma_store && !encode_bf16_3d(&m.tout, a.ptr[3], (uint64_t)wo, (uint64_t)(h / 2), (uint64_t)kConvN * n,
+                                             kTileCols / 2, 1, kConvN))
+                return cudaErrorNotSupported;
+            hit = cache_next;
+            cache[hit] = m;
+            cache_next = (cache_next + 1) % 8;
+        }
+        maps = cache[hit];
+    }
+    const int64_t tiles = (int64_t)n * (h / 2) * ceil_div(w, kTileCols);
+    const unsigned grid = (unsigned)(tiles < sm_count() ? tiles : sm_count());
+    conv3x3_relu_pool_kernel<<<grid, kConvThreads, kConvSmem, (cudaStream_t)s>>>(
+        maps.tin, maps.tout, a.p<__nv_bfloat16>(1), a.p<float>(2), a.p<__nv_bfloat16>(3), a.p<int>(4), n, h, w,
+        tma_store);
     return cudaGetLastError();
 }
 
 const char *validate_avgpool(const LaunchArgs &a)
 {
     const int planes = a.i32(2), hw = a.i32(3);
-    if (planes < 1 || hw < 8 || hw % 8) return "planes >= 1 and hw a positive multiple of 8 required";
+    if (planes < 1 || hw < 1) return "planes >= 1 and hw >= 1 required";
     if (a.bytes[0] / 2 / (size_t)hw < (size_t)planes) return "input smaller than planes x hw bf16";
     if (a.bytes[1] / 4 < (size_t)planes) return "e smaller than planes floats";
-    if ((reinterpret_cast<uintptr_t>(a.ptr[0]) & 15) != 0) return "input must be 16-byte aligned";
     return nullptr;
 }
 
 int launch_avgpool(const LaunchArgs &a, void *s)
 {
-    avgpool_global_kernel<<<(unsigned)a.i32(2), 256, 0, (cudaStream_t)s>>>(a.p<__nv_bfloat16>(0), a.p<float>(1),
-                                                                           a.i32(3));
+    const int hw = a.i32(3);
+    const int vec = hw % 8 == 0 && (reinterpret_cast<uintptr_t>(a.ptr[0]) & 15) == 0;
+    avgpool_global_kernel<<<(unsigned)a.i32(2), 256, 0, (cudaStream_t)s>>>(a.p<__nv_bfloat16>(0), a.p<float>(1), hw,
+                                                                           vec);
     return cudaGetLastError();
 }
 
@@ -297,8 +696,8 @@ const char *validate_dense(const LaunchArgs &a)
 int launch_dense(const LaunchArgs &a, void *s)
 {
     const int n = a.i32(5), k = a.i32(7);
-    concat_dense_kernel<<<(unsigned)ceil_div((int64_t)n * k, 128), 128, 0, (cudaStream_t)s>>>(
-        a.p<float>(0), a.p<float>(1), a.p<float>(2), a.p<float>(3), a.p<float>(4), n, a.i32(6), k);
+    concat_dense_kernel<<<(unsigned)n, 256, 0, (cudaStream_t)s>>>(a.p<float>(0), a.p<float>(1), a.p<float>(2),
+                                                                  a.p<float>(3), a.p<float>(4), a.i32(6), k);
     return cudaGetLastError();
 }
 

@@ -23,7 +23,8 @@ def check(got, ref, floor=0.05, what=""):
     assert err.max() <= TOL, (what, float(err.max()))
 
 
-@pytest.mark.parametrize("n,h,w", [(1, 2, 64), (2, 6, 128), (1, 64, 64), (3, 34, 192)])
+@pytest.mark.parametrize("n,h,w", [(1, 2, 8), (1, 2, 64), (2, 6, 72), (2, 6, 128), (1, 64, 64), (3, 34, 192),
+                                   (1, 4, 264), (1, 2, 520), (2, 10, 1024)])
 def test_conv_nodes_and_dag(n, h, w):
     inp, _bits = datagen.dl_inputs(n=n, h=h, w=w, seed=n * 100 + h)
     ref = P.dl(*inp)
