@@ -57,7 +57,8 @@ def _key(name, args):
 def tune_launch(ctx, name, args, blocks=(128, 256, 512, 1024), waves=(1, 2, 4, 8), reps=5, device="cuda"):
     """Time `name(*args)` for each block size and grid (waves x SMs) and
     return (grid, block) of the fastest; cached per kernel and sizes.  Only
-    for kernels whose launch shape is free (grid-stride kernels)."""
+    for kernels whose launch shape is free (grid-stride kernels); shapes the
+    kernel rejects are skipped."""
     key = _key(name, args)
     if key in _CACHE:
         return _CACHE[key]
@@ -67,8 +68,11 @@ def tune_launch(ctx, name, args, blocks=(128, 256, 512, 1024), waves=(1, 2, 4, 8
     for b in blocks:
         for w in waves:
             g = sms * w * max(1, 1024 // b)
-            for _ in range(2):
+            try:  # a kernel may reject a launch shape (e.g. a block larger than it supports)
                 ctx.launch_raw(name, *args, stream=st.cuda_stream, grid=(g, 1, 1), block=(b, 1, 1))
+            except G.GdagError:
+                continue
+            ctx.launch_raw(name, *args, stream=st.cuda_stream, grid=(g, 1, 1), block=(b, 1, 1))
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(st)
             for _ in range(reps):

@@ -5,23 +5,28 @@
 //
 // N is evaluated through the Mills ratio R(z) = (1 - N(z)) / phi(z):
 // N(x) = phi(x) R(-x) for x < 0 and 1 - phi(x) R(x) for x >= 0, with R a
-// rational function P(z)/Q(z) of degrees 6/7 whose coefficients are all
-// positive (fp32 Horner without cancellation); relative error of R below
-// 8e-9 on [0, 1e5].  The fit is derived in fit_mills_ratio.py (in the
-// variable u = z/4); here the coefficients are rescaled to z and P is
-// pre-multiplied by 1/sqrt(2 pi), the constant of phi.
+// rational function P(z)/Q(z) of degrees 4/5 whose coefficients are all
+// positive (fp32 Horner without cancellation); relative error of R about
+// 4e-8 on [0, 4] and below 1e-6 on [0, 1e5] (beyond 4 the tail it scales is
+// below 3e-5).  The fit is derived in fit_mills_ratio.py, which prints the
+// coefficients rescaled to z with P pre-multiplied by 1/sqrt(2 pi), the
+// constant of phi.
 //
 // GB300 specifics.  The kernel reads 4 and writes 4 bytes per option, so it
 // is HBM-bound only if it stays near 35 instructions per option; therefore:
 //  - d1 and d2 travel as one float2 through the packed fp32x2 FMA/MUL of
 //    sm_100+ (__ffma2_rn, __fmul2_rn): both CDFs cost one Horner chain;
 //  - the transcendentals are single MUFU operations written as PTX:
-//    lg2.approx for the logarithm, ex2.approx for phi, rcp.approx for 1/Q;
+//    lg2.approx for the logarithm, ex2.approx for phi, rcp.approx for
+//    1/(Q(z1) Q(z2)), from which both 1/Q follow by one packed multiply
+//    (Q stays below 1e8 for |d| <= 40, so the product cannot overflow);
 //  - d1 = lg2(S) (ln2 / (sigma sqrt T)) + (drift - ln K) / (sigma sqrt T) is
 //    one FMA, with both constants computed in double on the host.
 // Error: a shift e common to d1 and d2 (the logarithm's error, the rounding
 // of the constants) changes C only to second order, because
-// S phi(d1) = K exp(-rT) phi(d2); what remains is each N's own error.
+// S phi(d1) = K exp(-rT) phi(d2); what remains is each N's own error.  (That
+// is why phi(d2) is evaluated from d2 itself: deriving it from phi(d1) by the
+// same identity would save an ex2 but lose this cancellation.)
 // Conditioning: C is a difference of two terms of size ~S, so for
 // sigma sqrt(T) well below 1e-2 an fp32 price near the strike carries an
 // error of a few ulp of S, whatever the evaluation.
@@ -65,25 +70,22 @@ __device__ __forceinline__ float rcp_approx(float x)
 __device__ __forceinline__ float2 norm_cdf2(float2 d)
 {
     const float2 z = make_float2(fminf(fabsf(d.x), 40.0f), fminf(fabsf(d.y), 40.0f));
-    float2 p = f2(2.272637658e-04f);
-    p = __ffma2_rn(p, z, f2(3.562737228e-03f));
-    p = __ffma2_rn(p, z, f2(2.683402843e-02f));
-    p = __ffma2_rn(p, z, f2(1.214417067e-01f));
-    p = __ffma2_rn(p, z, f2(3.465261792e-01f));
-    p = __ffma2_rn(p, z, f2(5.959146476e-01f));
-    p = __ffma2_rn(p, z, f2(5.000000011e-01f));
-    float2 q = f2(5.696657770e-04f);
-    q = __ffma2_rn(q, z, f2(8.930458472e-03f));
-    q = __ffma2_rn(q, z, f2(6.783256553e-02f));
-    q = __ffma2_rn(q, z, f2(3.133407961e-01f));
-    q = __ffma2_rn(q, z, f2(9.347127516e-01f));
-    q = __ffma2_rn(q, z, f2(1.780614313e+00f));
-    q = __ffma2_rn(q, z, f2(1.989713857e+00f));
+    float2 p = f2(5.286688848e-03f);
+    p = __ffma2_rn(p, z, f2(4.807076126e-02f));
+    p = __ffma2_rn(p, z, f2(2.045669649e-01f));
+    p = __ffma2_rn(p, z, f2(4.659080207e-01f));
+    p = __ffma2_rn(p, z, f2(5.000000162e-01f));
+    float2 q = f2(1.325175100e-02f);
+    q = __ffma2_rn(q, z, f2(1.204967448e-01f));
+    q = __ffma2_rn(q, z, f2(5.259802458e-01f));
+    q = __ffma2_rn(q, z, f2(1.289215420e+00f));
+    q = __ffma2_rn(q, z, f2(1.729702769e+00f));
     q = __ffma2_rn(q, z, f2(1.000000000e+00f));
     const float2 t = __fmul2_rn(__fmul2_rn(z, z), f2(-7.213475204e-01f));  // -z^2 log2(e) / 2
     const float2 e = make_float2(ex2_approx(t.x), ex2_approx(t.y));
-    const float2 rq = make_float2(rcp_approx(q.x), rcp_approx(q.y));
-    const float2 tail = __fmul2_rn(__fmul2_rn(p, rq), e);  // phi(z) R(z)
+    const float rq = rcp_approx(q.x * q.y);                                // 1 / (Q(z1) Q(z2))
+    const float2 inv_q = __fmul2_rn(make_float2(q.y, q.x), f2(rq));
+    const float2 tail = __fmul2_rn(__fmul2_rn(p, inv_q), e);                // phi(z) R(z)
     return make_float2(d.x < 0.f ? tail.x : 1.0f - tail.x, d.y < 0.f ? tail.y : 1.0f - tail.y);
 }
 
@@ -94,12 +96,20 @@ __device__ __forceinline__ float bs_price(float s, const BsConst &c)
     return s * n.x - c.k_disc * n.y;
 }
 
+__device__ __forceinline__ float4 bs_price4(float4 v, const BsConst &c)
+{
+    return make_float4(bs_price(v.x, c), bs_price(v.y, c), bs_price(v.z, c), bs_price(v.w, c));
+}
+
 // 8 bytes of HBM traffic per option (4 in, 4 out); streaming loads/stores
 // (each byte is touched once).  The grid is sized to the resident block
 // count (one wave) and each thread walks float4s with a stride of the whole
-// grid, loading the next float4 before pricing the current one: every block
-// gets the same work to within one float4 per thread, so no tail wave.
-__global__ void __launch_bounds__(1024) bs_call_kernel(const float *__restrict__ S, float *__restrict__ C, int64_t n,
+// grid, two at a time, loading the next two before pricing the current two
+// (32 bytes in flight per thread): every block gets the same work to within
+// one float4 per thread, so there is no tail wave.
+// at most 512 threads a block and at least three blocks an SM: 40 registers,
+// so six 256-thread blocks (32 bytes in flight each thread) fit an SM
+__global__ void __launch_bounds__(512, 3) bs_call_kernel(const float *__restrict__ S, float *__restrict__ C, int64_t n,
                                                        BsConst c)
 {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -107,21 +117,19 @@ __global__ void __launch_bounds__(1024) bs_call_kernel(const float *__restrict__
         const float4 *S4 = reinterpret_cast<const float4 *>(S);
         float4 *C4 = reinterpret_cast<float4 *>(C);
         const int64_t n4 = n >> 2;
+        const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
         int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (i < n4) v = __ldcs(S4 + i);
+        float4 v0 = i < n4 ? __ldcs(S4 + i) : zero;
+        float4 v1 = i + stride < n4 ? __ldcs(S4 + i + stride) : zero;
         while (i < n4) {
-            const int64_t nx = i + stride;
-            float4 w = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (nx < n4) w = __ldcs(S4 + nx);
-            float4 o;
-            o.x = bs_price(v.x, c);
-            o.y = bs_price(v.y, c);
-            o.z = bs_price(v.z, c);
-            o.w = bs_price(v.w, c);
-            __stcs(C4 + i, o);
-            v = w;
-            i = nx;
+            const int64_t j = i + stride, i2 = i + 2 * stride;
+            const float4 w0 = i2 < n4 ? __ldcs(S4 + i2) : zero;
+            const float4 w1 = i2 + stride < n4 ? __ldcs(S4 + i2 + stride) : zero;
+            __stcs(C4 + i, bs_price4(v0, c));
+            if (j < n4) __stcs(C4 + j, bs_price4(v1, c));
+            v0 = w0;
+            v1 = w1;
+            i = i2;
         }
         if (blockIdx.x == 0 && threadIdx.x < (n & 3)) {
             int64_t t = (n4 << 2) + threadIdx.x;
@@ -141,6 +149,7 @@ const char *validate_bs(const LaunchArgs &a)
     if (n < 0) return "n < 0";
     if (a.bytes[0] / 4 < (size_t)n || a.bytes[1] / 4 < (size_t)n) return "S or C smaller than n floats";
     if (!(a.f32(3) > 0.f) || !(a.f32(5) > 0.f) || !(a.f32(6) > 0.f)) return "K, sigma and T must be > 0";
+    if (!a.auto_cfg && (int64_t)a.block[0] * a.block[1] * a.block[2] > 512) return "blocks of at most 512 threads";
     return nullptr;
 }
 
