@@ -51,7 +51,7 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--dags", default="all", choices=["all", "bs"],
                     help="also measure the VEC, IMG, ML and HITS DAGs (rank 0)")
-    ap.add_argument("--profile", default=None, choices=["bs", "vec", "img", "ml", "hits", "dl"],
+    ap.add_argument("--profile", default=None, choices=["bs", "vec", "img", "ml", "hits", "dl", "hits_batch"],
                     help="run only --steps steps of one DAG through the library (a small, "
                          "single-context command for ncu captures); prints nothing")
     ap.add_argument("--img-size", type=int, default=4096)
@@ -267,6 +267,10 @@ def alg_bytes(name, a):
         return 4 * (n + 1) + 8 * nnz + 4 * n + 4 * n
     if name == "l2norm":
         return 4 * a[3]
+    if name == "seg_l2norm":
+        return 4 * a[5] + 4 * (a[4] + 1) + 4 * a[4]
+    if name == "seg_scale":
+        return 8 * a[4] + 4 * (a[3] + 1) + 4 * a[3]
     if name == "conv3x3_relu_pool":
         n, h, w = a[5], a[6], a[7]
         return 2 * 3 * n * h * w + 2 * 64 * n * (h // 2) * (w // 2) + 64 * 27 * 2 + 64 * 4
@@ -423,6 +427,72 @@ class HitsSpec(Spec):
         H.dep(0, 1)
 
 
+class HitsBatchSpec(HitsSpec):
+    """HITS over 64 independent graphs (1e4..1e6 vertices) as one program:
+    block-diagonal SpMV and per-graph segment kernels, six launches per
+    iteration for the whole batch."""
+    name = "HITS-batch"
+
+    def build(self, ctx):
+        d = self.W.HitsBatchDag(ctx, self.data["hits_batch"])
+        d.run(iters=0, read=False)
+        return d
+
+    def hand(self, d, ctx, H):
+        n, nnz, G_ = d.n, d.nnz, d.G
+        cur, nxt = ("a", "h"), ("a2", "h2")
+        for it in range(self.ITERS):
+            if it:
+                H.dep(0, 1)
+                H.dep(1, 0)
+            H.k(0, "spmv_csr", *d.ATA, d.V[cur[1]], d.PAT, d.V[nxt[0]], d.CAT, n, nnz)
+            H.k(1, "spmv_csr", *d.AA, d.V[cur[0]], d.PA, d.V[nxt[1]], d.CA, n, nnz)
+            H.k(0, "seg_l2norm", d.V[nxt[0]], d.SEG, d.NAS, d.SAS, G_, n)
+            H.k(1, "seg_l2norm", d.V[nxt[1]], d.SEG, d.NHS, d.SHS, G_, n)
+            H.k(0, "seg_scale", d.V[nxt[0]], d.SEG, d.NAS, G_, n)
+            H.k(1, "seg_scale", d.V[nxt[1]], d.SEG, d.NHS, G_, n)
+            cur, nxt = nxt, cur
+        H.dep(0, 1)
+
+
+def measure_hits_separate(torch, G, W, graphs, steps, iters=5):
+    """The unfused form of the HITS batch: one HITS program per graph, all
+    issued into one PARALLEL context (the scheduler spreads the independent
+    programs over its streams).  ms per step of `iters` iterations on every
+    graph."""
+    ctx = G.Context()
+    dags = [W.HitsDag(ctx, csr, csc) for csr, csc in graphs]
+    for d in dags:
+        d.run(iters=0, read=False)
+
+    def step():
+        for d in dags:
+            cur, nxt = ("a", "h"), ("a2", "h2")
+            for _ in range(iters):
+                d.iterate(cur[0], cur[1], nxt[0], nxt[1])
+                cur, nxt = nxt, cur
+
+    for _ in range(2):
+        step()
+    ctx.sync()
+    torch.cuda.synchronize()
+    s0 = torch.cuda.Stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0 = time.perf_counter()
+    e0.record(s0)
+    ctx.fork(s0.cuda_stream)
+    for _ in range(steps):
+        step()
+    ctx.wait_all(s0.cuda_stream)
+    e1.record(s0)
+    host_ms = (time.perf_counter() - t0) * 1e3 / steps
+    torch.cuda.synchronize()
+    out = {"makespan_ms": e0.elapsed_time(e1) / steps, "host_issue_ms": host_ms,
+           "launches_per_step": len(dags) * iters * 6, "streams": ctx.stats()["streams"]}
+    ctx.close()
+    return out
+
+
 class DlSpec(Spec):
     name = "DL"
 
@@ -491,6 +561,8 @@ def make_data(datagen, which):
         data["hits"] = datagen.hits_graph(10_000_000, 50_000_000, seed=4)
     if "dl" in which:
         data["dl"] = datagen.dl_inputs(n=16, h=256, w=256, seed=5)[0]
+    if "hits_batch" in which:
+        data["hits_batch"] = datagen.hits_batch(count=64, nmin=10_000, nmax=1_000_000, seed=6)
     return data
 
 
@@ -669,7 +741,7 @@ def run_ours(args, rank, world, local_rank):
         if dist:
             dist.barrier()
 
-    which = ["bs"] + (["vec", "img", "ml", "hits", "dl"] if args.dags == "all" and rank == 0 else [])
+    which = ["bs"] + (["vec", "img", "ml", "hits", "dl", "hits_batch"] if args.dags == "all" and rank == 0 else [])
     data = make_data(datagen, which)
     prices = data["bs"]
     s0 = torch.cuda.Stream()
@@ -747,10 +819,19 @@ def run_ours(args, rank, world, local_rank):
         specs = [BsSpec(G, W, data)]
         if args.dags == "all":
             specs += [VecSpec(G, W, data), ImgSpec(G, W, data), MlSpec(G, W, data), HitsSpec(G, W, data),
-                      DlSpec(G, W, data)]
+                      DlSpec(G, W, data), HitsBatchSpec(G, W, data)]
         dags = {}
         for sp in specs:
             dags[sp.name] = measure_dag(torch, G, sp, nsteps_other, hbm, link)
+        if "HITS-batch" in dags:
+            hb = data["hits_batch"]
+            sep = measure_hits_separate(torch, G, W, hb, max(2, nsteps_other // 4))
+            fused = dags["HITS-batch"]
+            fused["graphs"] = len(hb)
+            fused["vertices"] = int(sum(len(g[0][0]) - 1 for g in hb))
+            fused["edges"] = int(sum(int(g[0][0][-1]) for g in hb))
+            fused["separate_programs"] = sep
+            fused["speedup_vs_separate_programs"] = sep["makespan_ms"] / fused["makespan_ms"]["parallel"]
         bsm = dags["B&S"]["makespan_ms"]
 
         # ---- serving: Poisson streams of DAG requests on one context
@@ -876,6 +957,11 @@ def run_profile(args):
         d = W.MlDag(ctx, 100_000)
         d.load(*datagen.ml_inputs(100_000, feats=1024, classes=10, seed=3))
         step = d.launch_all
+    elif args.profile == "hits_batch":
+        d = W.HitsBatchDag(ctx, datagen.hits_batch(count=64, nmin=10_000, nmax=1_000_000, seed=6))
+        d.run(iters=0, read=False)
+        spec = HitsBatchSpec(G, W, {})
+        step = lambda: spec.step(d)
     elif args.profile == "dl":
         d = W.DlDag(ctx)
         d.load(*datagen.dl_inputs(n=16, h=256, w=256, seed=5)[0])

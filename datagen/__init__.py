@@ -24,6 +24,8 @@ Recipes (the paper, Section IV-A, runs every benchmark on random data):
         d = floor(u^(-1/(alpha-1))), capped at n-1), rescaled so the total is
         exactly nnz; destinations uniform, no self-loops, no duplicate edges;
         unit float32 weights; CSR of A and CSR of A^T (the CSC of A).
+* HITS batch  `count` such graphs, vertex counts log-uniform on [nmin, nmax],
+        `degree` edges per vertex on average (the batched HITS benchmark).
 """
 from __future__ import annotations
 
@@ -133,6 +135,17 @@ def hits_graph(n: int, nnz: int, alpha: float = 2.1, seed: int = 4):
     t_rowptr, t_col = transpose_csr(rowptr, col, n)
     val = np.ones(nnz, dtype=np.float32)
     return (rowptr, col, val), (t_rowptr, t_col, val.copy())
+
+
+def hits_batch(count: int = 64, nmin: int = 10_000, nmax: int = 1_000_000, degree: int = 5,
+               alpha: float = 2.1, seed: int = 6):
+    """`count` independent graphs for a batched HITS: a list of
+    (csr, csc) pairs as hits_graph returns them."""
+    g = rng(seed)
+    sizes = np.exp(g.uniform(np.log(nmin), np.log(nmax), count)).astype(np.int64)
+    sizes = np.maximum(sizes, 2)
+    return [hits_graph(int(n), int(min(degree * n, n * (n - 1))), alpha, seed * 1000 + i)
+            for i, n in enumerate(sizes)]
 
 
 def to_bf16_bits(a: np.ndarray) -> np.ndarray:

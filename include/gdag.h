@@ -300,6 +300,14 @@ int gdag_array_prefetch_host(gdag_ctx *ctx, gdag_array a, size_t off,
  *        l2norm          (x IN f32[n], norm OUT f32[1], scratch INOUT, n i64)
  *        scale           (x INOUT f32[n], norm IN f32[1], n i64)
  *                                                x := x/norm (norm 0: kept)
+ *        seg_l2norm      (x IN f32[n], seg IN i32[G+1], norms OUT f32[G],
+ *                         scratch INOUT, G i32, n i32)
+ *                         norms[g] = ||x[seg[g] .. seg[g+1])||, for a batch
+ *                         of graphs stored block-diagonally; G <= 65535,
+ *                         x 16-byte aligned (also for seg_scale)
+ *        seg_scale       (x INOUT f32[n], seg IN i32[G+1], norms IN f32[G],
+ *                         G i32, n i32)  x := x/norms[g] on segment g
+ *                         (norm 0: kept); segment bounds are clamped to n
  *  DL    conv3x3_relu_pool (x IN bf16[n*3*h*w], wt IN bf16[64*3*3*3],
  *                         bias IN f32[64], out OUT bf16[n*64*(h/2)*(w/2)],
  *                         status INOUT i32[1], n i32, h i32, w i32)
@@ -423,8 +431,9 @@ int gdag_trace_export(gdag_ctx *ctx, gdag_trace_rec *buf, size_t cap,
 int gdag_stats_get(gdag_ctx *ctx, gdag_stats *out);
 
 /* Bytes of scratch the built-in reductions (vec_reduce_diff, minmax, l2norm)
- * and spmv_csr need for `n` elements; the scratch array must be zeroed once
- * before its first use and is left zeroed-counter by every launch. */
+ * and spmv_csr need for `n` elements (for seg_l2norm, n is the number of
+ * segments G); the scratch array must be zeroed once before its first use
+ * and is left zeroed-counter by every launch. */
 size_t gdag_scratch_bytes(const char *kernel, int64_t n);
 
 /* ------------------------------------------------- allocation-free entry

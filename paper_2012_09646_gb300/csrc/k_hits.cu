@@ -4,6 +4,12 @@
 //   spmv_csr        y = A x for CSR A (the transpose is passed as its own CSR)
 //   l2norm          norm[0] = ||x||_2
 //   scale           x := x / norm[0]  (unchanged if norm is 0)
+//   seg_l2norm      norms[g] = ||x[seg[g] .. seg[g+1])||_2 for G segments
+//   seg_scale       x[seg[g] .. seg[g+1]) := ... / norms[g]  (unchanged if 0)
+// The seg_ kernels serve a batch of independent graphs stored
+// block-diagonally (one CSR whose diagonal blocks are the graphs): the SpMV
+// needs nothing new, and the per-graph norms and scaling are one launch each
+// for the whole batch instead of one per graph.
 //
 // spmv_csr balances power-law rows (one row may hold ~1e6 nonzeros) with
 // the merge-path decomposition of Merrill and Garland ("Merge-based parallel
@@ -228,11 +234,13 @@ __global__ void __launch_bounds__(kThreads) l2norm_kernel(const float *__restric
     }
 }
 
-// x := x / norm[0], correctly rounded; a zero norm leaves x unchanged.
+// x := x / norm[0], correctly rounded (div_by); a zero norm leaves x
+// unchanged.
 __global__ void __launch_bounds__(1024) scale_kernel(float *__restrict__ x, const float *__restrict__ norm, int64_t n)
 {
     const float nr = norm[0];
     if (!(nr > 0.f)) return;
+    const float rr = (float)(1.0 / (double)nr);
     if ((reinterpret_cast<uintptr_t>(x) & 15) == 0) {
         float4 *x4 = reinterpret_cast<float4 *>(x);
         const int64_t n4 = n >> 2, bd = blockDim.x, tile = bd * kUnroll;
@@ -247,18 +255,112 @@ __global__ void __launch_bounds__(1024) scale_kernel(float *__restrict__ x, cons
             for (int k = 0; k < kUnroll; ++k) {
                 int64_t i = base + threadIdx.x + k * bd;
                 if (i < n4)
-                    x4[i] = make_float4(__fdiv_rn(v[k].x, nr), __fdiv_rn(v[k].y, nr), __fdiv_rn(v[k].z, nr),
-                                        __fdiv_rn(v[k].w, nr));
+                    x4[i] = make_float4(div_by(v[k].x, nr, rr), div_by(v[k].y, nr, rr), div_by(v[k].z, nr, rr),
+                                        div_by(v[k].w, nr, rr));
             }
         }
         if (blockIdx.x == 0 && threadIdx.x < (n & 3)) {
             int64_t i = (n4 << 2) + threadIdx.x;
-            x[i] = __fdiv_rn(x[i], nr);
+            x[i] = div_by(x[i], nr, rr);
         }
     } else {
         for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-            x[i] = __fdiv_rn(x[i], nr);
+            x[i] = div_by(x[i], nr, rr);
     }
+}
+
+size_t seg_norm_scratch_bytes(int64_t G);
+
+// Segments are cut into kSegSlices equal slices; block (slice, g) handles
+// one slice of segment g.  Segment bounds are clamped to [0, n], so a
+// malformed seg array cannot index outside x.
+constexpr int kSegSlices = 32;
+
+__device__ __forceinline__ void seg_slice(const int *__restrict__ seg, int g, int sl, int n, int &lo, int &hi)
+{
+    int b = seg[g], e = seg[g + 1];
+    b = b < 0 ? 0 : (b > n ? n : b);
+    e = e < b ? b : (e > n ? n : e);
+    const int64_t len = e - b;
+    lo = b + (int)(len * sl / kSegSlices);
+    hi = b + (int)(len * (sl + 1) / kSegSlices);
+}
+
+// norms[g] = sqrt(sum of x_i^2 over segment g): Kahan fp32 per thread, fp64
+// block tree per slice; the last slice of a segment to arrive adds the
+// slices' partials in slice order (the result does not depend on timing) and
+// resets the segment's arrival counter.
+__global__ void __launch_bounds__(kThreads) seg_l2norm_kernel(const float *__restrict__ x, const int *__restrict__ seg,
+                                                              float *__restrict__ norms, double *scratch, int G, int n)
+{
+    __shared__ double sh[kThreads / 32];
+    __shared__ bool last;
+    const int g = blockIdx.y, sl = blockIdx.x;
+    int lo, hi;
+    seg_slice(seg, g, sl, n, lo, hi);
+    Kahan acc;
+    // scalar head up to a 16-byte boundary, float4 body, scalar tail (x
+    // itself is 16-byte aligned: checked on the host)
+    const int a0 = min(hi, (lo + 3) & ~3), a1 = max(a0, hi & ~3);
+    for (int i = lo + threadIdx.x; i < a0; i += kThreads) acc.add(x[i] * x[i]);
+    const float4 *x4 = reinterpret_cast<const float4 *>(x);
+    int j = (a0 >> 2) + threadIdx.x;
+    for (; j + kThreads < (a1 >> 2); j += 2 * kThreads) {
+        const float4 u = x4[j], v = x4[j + kThreads];
+        acc.add(u.x * u.x);
+        acc.add(u.y * u.y);
+        acc.add(u.z * u.z);
+        acc.add(u.w * u.w);
+        acc.add(v.x * v.x);
+        acc.add(v.y * v.y);
+        acc.add(v.z * v.z);
+        acc.add(v.w * v.w);
+    }
+    for (; j < (a1 >> 2); j += kThreads) {
+        const float4 u = x4[j];
+        acc.add(u.x * u.x);
+        acc.add(u.y * u.y);
+        acc.add(u.z * u.z);
+        acc.add(u.w * u.w);
+    }
+    for (int i = a1 + threadIdx.x; i < hi; i += kThreads) acc.add(x[i] * x[i]);
+    const double bs = block_sum(acc.value(), sh);
+    double *part = scratch + (size_t)g * kSegSlices;
+    unsigned *counter = reinterpret_cast<unsigned *>(scratch + (size_t)G * kSegSlices) + g;
+    if (threadIdx.x == 0) part[sl] = bs;
+    __threadfence();  // the partial visible device-wide before the arrival
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicAdd(counter, 1u) == (unsigned)(kSegSlices - 1);
+    __syncthreads();
+    if (!last) return;
+    __threadfence();  // every slice's partial visible
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int k = 0; k < kSegSlices; ++k) t += ((volatile double *)part)[k];
+        norms[g] = (float)sqrt(t);
+        *counter = 0u;
+    }
+}
+
+// x := x / norms[g] over segment g, correctly rounded (div_by); a zero norm
+// leaves the segment unchanged.
+__global__ void __launch_bounds__(kThreads) seg_scale_kernel(float *__restrict__ x, const int *__restrict__ seg,
+                                                             const float *__restrict__ norms, int n)
+{
+    const int g = blockIdx.y, sl = blockIdx.x;
+    const float nr = norms[g];
+    if (!(nr > 0.f)) return;
+    const float rr = (float)(1.0 / (double)nr);
+    int lo, hi;
+    seg_slice(seg, g, sl, n, lo, hi);
+    const int a0 = min(hi, (lo + 3) & ~3), a1 = max(a0, hi & ~3);
+    for (int i = lo + threadIdx.x; i < a0; i += kThreads) x[i] = div_by(x[i], nr, rr);
+    float4 *x4 = reinterpret_cast<float4 *>(x);
+    for (int j = (a0 >> 2) + threadIdx.x; j < (a1 >> 2); j += kThreads) {
+        const float4 u = x4[j];
+        x4[j] = make_float4(div_by(u.x, nr, rr), div_by(u.y, nr, rr), div_by(u.z, nr, rr), div_by(u.w, nr, rr));
+    }
+    for (int i = a1 + threadIdx.x; i < hi; i += kThreads) x[i] = div_by(x[i], nr, rr);
 }
 
 namespace {
@@ -347,6 +449,45 @@ int launch_scale(const LaunchArgs &a, void *s)
     return cudaGetLastError();
 }
 
+const char *validate_seg_common(const LaunchArgs &a, int gi, int ni)
+{
+    const int G = a.i32(gi), n = a.i32(ni);
+    if (G < 0 || n < 0) return "G and n must be >= 0";
+    if (G > 65535) return "at most 65535 segments";
+    if (a.bytes[0] / 4 < (size_t)n) return "x smaller than n floats";
+    if (a.bytes[1] / 4 < (size_t)G + 1) return "seg smaller than G + 1 int32";
+    if (a.bytes[2] / 4 < (size_t)G) return "norms smaller than G floats";
+    if ((reinterpret_cast<uintptr_t>(a.ptr[0]) & 15) != 0) return "x must be 16-byte aligned";
+    return nullptr;
+}
+
+const char *validate_seg_l2norm(const LaunchArgs &a)
+{
+    if (const char *m = validate_seg_common(a, 4, 5)) return m;
+    if (a.bytes[3] < seg_norm_scratch_bytes(a.i32(4))) return "scratch smaller than gdag_scratch_bytes(\"seg_l2norm\", G)";
+    return nullptr;
+}
+
+int launch_seg_l2norm(const LaunchArgs &a, void *s)
+{
+    const int G = a.i32(4);
+    if (G == 0) return cudaSuccess;
+    seg_l2norm_kernel<<<dim3(kSegSlices, G), kThreads, 0, (cudaStream_t)s>>>(a.p<float>(0), a.p<int>(1), a.p<float>(2),
+                                                                           a.p<double>(3), G, a.i32(5));
+    return cudaGetLastError();
+}
+
+const char *validate_seg_scale(const LaunchArgs &a) { return validate_seg_common(a, 3, 4); }
+
+int launch_seg_scale(const LaunchArgs &a, void *s)
+{
+    const int G = a.i32(3);
+    if (G == 0) return cudaSuccess;
+    seg_scale_kernel<<<dim3(kSegSlices, G), kThreads, 0, (cudaStream_t)s>>>(a.p<float>(0), a.p<int>(1), a.p<float>(2),
+                                                                          a.i32(4));
+    return cudaGetLastError();
+}
+
 KernelEntry entry(const char *name, const void *fn, std::initializer_list<gdag_argspec> spec, ValidateFn v,
                   LauncherFn l)
 {
@@ -363,6 +504,7 @@ KernelEntry entry(const char *name, const void *fn, std::initializer_list<gdag_a
 
 }  // namespace
 
+size_t seg_norm_scratch_bytes(int64_t G) { return (size_t)(G > 0 ? G : 0) * (kSegSlices * 8 + 4) + 16; }
 size_t spmv_part_bytes(int64_t rows_plus_nnz) { return (size_t)(ceil_div(rows_plus_nnz > 0 ? rows_plus_nnz : 1, kSpmvTile) + 1) * 8; }
 size_t spmv_carry_bytes(int64_t rows_plus_nnz) { return (size_t)ceil_div(rows_plus_nnz > 0 ? rows_plus_nnz : 1, kSpmvTile) * 4 + 16; }
 
@@ -380,6 +522,12 @@ void append_hits_kernels(std::vector<KernelEntry> &v)
                       launch_l2norm));
     v.push_back(entry("scale", (const void *)scale_kernel, {arr(GDAG_MODE_INOUT), arr(GDAG_MODE_IN), scal(8)},
                       validate_scale, launch_scale));
+    v.push_back(entry("seg_l2norm", (const void *)seg_l2norm_kernel,
+                      {arr(GDAG_MODE_IN), arr(GDAG_MODE_IN), arr(GDAG_MODE_OUT), arr(GDAG_MODE_INOUT), scal(4), scal(4)},
+                      validate_seg_l2norm, launch_seg_l2norm));
+    v.push_back(entry("seg_scale", (const void *)seg_scale_kernel,
+                      {arr(GDAG_MODE_INOUT), arr(GDAG_MODE_IN), arr(GDAG_MODE_IN), scal(4), scal(4)}, validate_seg_scale,
+                      launch_seg_scale));
 }
 
 }  // namespace gdag

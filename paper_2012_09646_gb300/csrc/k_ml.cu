@@ -130,6 +130,168 @@ __global__ void __launch_bounds__(kMlThreads) dense_scores_kernel(const int *__r
     }
 }
 
+// ---- pipelined form (tables that leave room for a staging ring): X is
+// staged in shared memory in slices of kPipeSlice features x kPipeRows rows
+// by cp.async, kPipeStages slices in flight per CTA, so the loads no longer
+// wait in registers.  Four lanes share a row, the eight row groups of a warp
+// share every table read (broadcast), and each lane carries four rows, so
+// one table load serves 32 rows: a 128-bit shared load costs four wavefronts
+// whatever its addresses, and the table loads are what bounds this form.
+// Packed fp32x2 FMA, fixed shuffle tree, deterministic.  Lane q sums the
+// features 32 s + 8 q .. 32 s + 8 q + 7 of every slice s instead of one
+// contiguous quarter, so a general table rounds differently from the form
+// above (a dyadic one, whose partial sums are exact, gives the same bits).
+constexpr int kPipeSlice = 32;                            // features per stage
+constexpr int kPipeThreads = 128;                         // four warps
+constexpr int kPipeRowsPerLane = 4;                       // rows rsub, rsub+8, rsub+16, rsub+24 of a warp
+constexpr int kPipeRows = 8 * kPipeRowsPerLane * (kPipeThreads / 32);  // 128 rows per tile
+constexpr int kPipeRowBytes = kPipeSlice * 4 + 16;        // padded: the lanes' 16-byte reads spread over all banks
+constexpr int kPipeStageBytes = kPipeRows * kPipeRowBytes;
+constexpr int kPipeStages = 3;
+
+// Table layout of the pipelined form: lane q handles features
+// f = 32 s + 8 q + j (index i = 8 s + j of its quarter); the float4 of class
+// group k of quarter q at index i sits at float4 slot (i * NC4 + k) * 4 + q,
+// so the four quarters a warp reads at once share one 64-byte span: one
+// shared-memory wavefront per table load, no bank conflict.
+__host__ __device__ constexpr int pipe_table_floats(int feats, int nc4) { return feats * nc4 * 4; }
+
+__device__ __forceinline__ void cp_async16(void *dst, const void *src, int src_bytes)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
+                 "l"(src), "r"(src_bytes)
+                 : "memory");
+}
+
+template <int NC4>
+__global__ void __launch_bounds__(kPipeThreads, 2)
+    dense_scores_pipe_kernel(const int *__restrict__ X, const float *__restrict__ T, const float *__restrict__ bias,
+                             float *__restrict__ S, int rows, int feats, int classes)
+{
+    extern __shared__ float4 smem4[];
+    unsigned char *xs = reinterpret_cast<unsigned char *>(smem4);
+    float *st = reinterpret_cast<float *>(xs + kPipeStages * kPipeStageBytes);
+    for (int i = threadIdx.x; i < pipe_table_floats(feats, NC4); i += kPipeThreads) {
+        const int c = i % 4, q = (i / 4) % 4, k = (i / 16) % NC4, idx = i / (16 * NC4);
+        const int f = (idx / 8) * kPipeSlice + 8 * q + (idx % 8), cls = 4 * k + c;
+        st[i] = cls < classes ? T[(size_t)f * classes + cls] : 0.f;
+    }
+    const int slices = feats / kPipeSlice;
+    const int ntiles = (rows + kPipeRows - 1) / kPipeRows;
+    const int my_tiles = (int)blockIdx.x < ntiles ? (ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+    const int total = my_tiles * slices;  // steps: (tile, slice) pairs of this CTA, tile-major
+
+    // copy role: thread c copies chunk k = c % 8 of rows c / 8 + 16 j
+    // (j = 0..7) of each slice; the row pointers are set once per tile
+    constexpr int kCopies = kPipeRows * (kPipeSlice / 4) / kPipeThreads;  // 8
+    constexpr int kCopyRowStep = kPipeThreads / (kPipeSlice / 4);        // 16
+    const int ck = threadIdx.x % (kPipeSlice / 4), cr = threadIdx.x / (kPipeSlice / 4);
+    const int *csrc[kCopies];
+    int cbytes[kCopies];
+    int i_tile = 0, i_slice = 0, i_buf = 0, issued = 0;  // next step to issue
+    auto set_rows = [&](int tile_i) {
+        const int tile = (int)blockIdx.x + tile_i * (int)gridDim.x;
+#pragma unroll
+        for (int j = 0; j < kCopies; ++j) {
+            const int row = tile * kPipeRows + cr + j * kCopyRowStep;
+            csrc[j] = X + (size_t)(row < rows ? row : 0) * feats + 4 * ck;
+            cbytes[j] = row < rows ? 16 : 0;
+        }
+    };
+    auto issue_next = [&]() {
+        if (issued < total) {
+            unsigned char *dst = xs + i_buf * kPipeStageBytes + cr * kPipeRowBytes + 16 * ck;
+#pragma unroll
+            for (int j = 0; j < kCopies; ++j)
+                cp_async16(dst + j * kCopyRowStep * kPipeRowBytes, csrc[j] + i_slice * kPipeSlice,
+                           cbytes[j]);
+            ++issued;
+            i_buf = i_buf + 1 == kPipeStages ? 0 : i_buf + 1;
+            if (++i_slice == slices) {
+                i_slice = 0;
+                if (++i_tile < my_tiles) set_rows(i_tile);
+            }
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    };
+
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int q = lane & 3, rsub = lane >> 2;
+    const int r0_l = warp * (8 * kPipeRowsPerLane) + rsub;  // rows r0_l + 8 m, m < kPipeRowsPerLane
+    const float4 *tq = reinterpret_cast<const float4 *>(st) + q;
+    float2 acc[kPipeRowsPerLane][NC4 * 2];
+#pragma unroll
+    for (int m = 0; m < kPipeRowsPerLane; ++m)
+#pragma unroll
+        for (int k = 0; k < NC4 * 2; ++k) acc[m][k] = make_float2(0.f, 0.f);
+    if (my_tiles > 0) set_rows(0);
+    for (int t = 0; t < kPipeStages - 1; ++t) issue_next();
+    int sl = 0, tile_i = 0, buf = 0;  // step being computed
+    for (int t = 0; t < total; ++t) {
+        asm volatile("cp.async.wait_group %0;" ::"n"(kPipeStages - 2) : "memory");
+        __syncthreads();  // step t landed for every thread; step t-1's buffer is free
+        issue_next();
+        const unsigned char *bufp = xs + buf * kPipeStageBytes + r0_l * kPipeRowBytes + 32 * q;
+        const float4 *tsl = tq + 8 * sl * NC4 * 4;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {  // features 4h .. 4h+3 of the lane's eight
+            float x[kPipeRowsPerLane][4];
+#pragma unroll
+            for (int m = 0; m < kPipeRowsPerLane; ++m) {
+                const int4 v = *reinterpret_cast<const int4 *>(bufp + 8 * m * kPipeRowBytes + 16 * h);
+                x[m][0] = __int2float_rn(v.x);
+                x[m][1] = __int2float_rn(v.y);
+                x[m][2] = __int2float_rn(v.z);
+                x[m][3] = __int2float_rn(v.w);
+            }
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const float4 *trow = tsl + (4 * h + j) * NC4 * 4;
+#pragma unroll
+                for (int k = 0; k < NC4; ++k) {
+                    const float4 tv = trow[4 * k];
+                    const float2 t01 = make_float2(tv.x, tv.y), t23 = make_float2(tv.z, tv.w);
+#pragma unroll
+                    for (int m = 0; m < kPipeRowsPerLane; ++m) {
+                        const float2 xx = make_float2(x[m][j], x[m][j]);
+                        acc[m][2 * k] = __ffma2_rn(xx, t01, acc[m][2 * k]);
+                        acc[m][2 * k + 1] = __ffma2_rn(xx, t23, acc[m][2 * k + 1]);
+                    }
+                }
+            }
+        }
+        buf = buf + 1 == kPipeStages ? 0 : buf + 1;
+        if (++sl == slices) {
+            sl = 0;
+            // combine the four quarters, (q0 + q1) + (q2 + q3), and write
+            const int tile = (int)blockIdx.x + tile_i * (int)gridDim.x;
+#pragma unroll
+            for (int m = 0; m < kPipeRowsPerLane; ++m) {
+#pragma unroll
+                for (int k = 0; k < NC4 * 2; ++k) {
+                    acc[m][k].x += __shfl_xor_sync(0xffffffffu, acc[m][k].x, 1);
+                    acc[m][k].y += __shfl_xor_sync(0xffffffffu, acc[m][k].y, 1);
+                    acc[m][k].x += __shfl_xor_sync(0xffffffffu, acc[m][k].x, 2);
+                    acc[m][k].y += __shfl_xor_sync(0xffffffffu, acc[m][k].y, 2);
+                }
+                const int row = tile * kPipeRows + r0_l + 8 * m;
+                if (q == 0 && row < rows) {
+                    float *out = S + (size_t)row * classes;
+#pragma unroll
+                    for (int k = 0; k < NC4 * 2; ++k) {
+                        if (2 * k < classes) out[2 * k] = bias[2 * k] + acc[m][k].x;
+                        if (2 * k + 1 < classes) out[2 * k + 1] = bias[2 * k + 1] + acc[m][k].y;
+                    }
+                }
+#pragma unroll
+                for (int k = 0; k < NC4 * 2; ++k) acc[m][k] = make_float2(0.f, 0.f);
+            }
+            ++tile_i;
+        }
+    }
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+}
+
 // Row softmax in place, one thread per row (classes <= 32), max-subtracted.
 __global__ void __launch_bounds__(256) row_softmax_kernel(float *__restrict__ S, int rows, int classes)
 {
@@ -182,6 +344,14 @@ int nc4_of(int classes) { return (classes + 3) / 4; }
 
 size_t dense_smem(int feats, int classes) { return (size_t)kMlQuarters * ml_quarter_stride(feats, nc4_of(classes)) * 4; }
 
+size_t pipe_smem(int feats, int classes)
+{
+    return (size_t)kPipeStages * kPipeStageBytes + (size_t)pipe_table_floats(feats, nc4_of(classes)) * 4;
+}
+
+// the pipelined form when two CTAs with their staging rings fit an SM
+bool use_pipe(int feats, int classes) { return pipe_smem(feats, classes) <= 110 * 1024; }
+
 const char *validate_scores(const LaunchArgs &a)
 {
     const int rows = a.i32(4), feats = a.i32(5), classes = a.i32(6);
@@ -197,10 +367,31 @@ const char *validate_scores(const LaunchArgs &a)
     return nullptr;
 }
 
+template <int NC4> int scores_pipe_launch(const LaunchArgs &a, cudaStream_t s)
+{
+    const int rows = a.i32(4), feats = a.i32(5), classes = a.i32(6);
+    static bool configured = false;
+    if (!configured) {
+        cudaError_t e = cudaFuncSetAttribute(dense_scores_pipe_kernel<NC4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             110 * 1024);
+        if (e != cudaSuccess) return e;
+        configured = true;
+    }
+    // an equal number of tiles for every CTA (to within one): waves of two
+    // CTAs per SM, then as many CTAs as that many tiles each need
+    const int64_t ntiles = ceil_div(rows, kPipeRows), slots = 2 * (int64_t)sm_count();
+    const int64_t per = ceil_div(ntiles, slots);
+    const int64_t grid = ceil_div(ntiles, per);
+    dense_scores_pipe_kernel<NC4><<<(unsigned)grid, kPipeThreads, pipe_smem(feats, classes), s>>>(
+        a.p<int>(0), a.p<float>(1), a.p<float>(2), a.p<float>(3), rows, feats, classes);
+    return cudaGetLastError();
+}
+
 template <int NC4> int scores_launch(const LaunchArgs &a, cudaStream_t s)
 {
     const int rows = a.i32(4), feats = a.i32(5), classes = a.i32(6);
     if (rows == 0) return cudaSuccess;
+    if (use_pipe(feats, classes)) return scores_pipe_launch<NC4>(a, s);
     const size_t smem = dense_smem(feats, classes);
     // per process: raise the dynamic shared-memory limit once and remember
     // the occupancy of the last table size (no device queries on later

@@ -107,6 +107,22 @@ __device__ __forceinline__ bool arrive_last(unsigned *counter)
     return last;
 }
 
+// x / d rounded to nearest, given r = RN(1/d): Markstein's correction
+// (P. Markstein, "Computation of elementary functions on the IBM RISC
+// System/6000 processor", IBM J. Res. Dev. 34(1), 1990): q = RN(x r) is
+// within an ulp of x/d, the residual x - q d is exact under FMA, and one step
+// q + (x - q d) r rounds to the correctly rounded quotient for normal
+// operands and results.  Three instructions per element instead of a full
+// division; r comes from (float)(1.0 / (double)d), which is RN(1/d) because
+// rounding the correctly rounded double quotient to float cannot double-round
+// (53 >= 2 * 24 + 2).
+__device__ __forceinline__ float div_by(float x, float d, float r)
+{
+    const float q = x * r;
+    const float e = fmaf(-q, d, x);
+    return fmaf(e, r, q);
+}
+
 // Kahan-compensated fp32 accumulation: per-thread sums stay accurate to a
 // few ulp however many elements a thread visits.
 struct Kahan {

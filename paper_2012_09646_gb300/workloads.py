@@ -283,6 +283,63 @@ class HitsDag:
         return cur
 
 
+def block_diag_csr(mats):
+    """Block-diagonal concatenation of square CSR matrices given as
+    (rowptr, col, val): returns the combined (rowptr, col, val) and the
+    segment starts (the first vertex of each matrix, plus the total).  This
+    is input layout only (index offsets), done once when a batch is built."""
+    import numpy as np
+    rps, cols, vals, seg = [], [], [], [0]
+    nv, ne = 0, 0
+    for rp, col, val in mats:
+        rp = np.asarray(rp, dtype=np.int64)
+        rps.append(rp[:-1] + ne)
+        cols.append(np.asarray(col, dtype=np.int64) + nv)
+        vals.append(np.asarray(val, dtype=np.float32))
+        nv += rp.size - 1
+        ne += int(rp[-1])
+        seg.append(nv)
+    if nv + ne >= 2 ** 31:
+        raise ValueError("batch too large for int32 indexing")
+    rowptr = np.concatenate(rps + [np.array([ne], dtype=np.int64)])
+    return (rowptr, np.concatenate(cols), np.concatenate(vals)), np.asarray(seg, dtype=np.int64)
+
+
+class HitsBatchDag(HitsDag):
+    """HITS over a batch of independent graphs in one program: the graphs are
+    stored block-diagonally, so each SpMV covers every graph, and the norms
+    and scaling are per-graph segment kernels -- six launches per iteration
+    for the whole batch (the fused form of one HITS program per graph)."""
+
+    def __init__(self, ctx, graphs, device="cuda"):
+        csr, seg = block_diag_csr([g[0] for g in graphs])
+        csc, seg_t = block_diag_csr([g[1] for g in graphs])
+        assert (seg == seg_t).all()
+        super().__init__(ctx, csr, csc, device=device)
+        self.G = G_ = len(graphs)
+        self.seg_host = seg
+        self.seg = torch.as_tensor(seg).to(dtype=torch.int32).to(device)
+        self.SEG = ctx.array(self.seg, name="seg")
+        self.seg_norms = torch.zeros((2, max(G_, 1)), dtype=F32, device=device)
+        self.NAS = ctx.array(self.seg_norms[0], name="norms_a")
+        self.NHS = ctx.array(self.seg_norms[1], name="norms_h")
+        self._sas, self.SAS = _scratch(ctx, "seg_l2norm", G_, device)
+        self._shs, self.SHS = _scratch(ctx, "seg_l2norm", G_, device)
+        torch.cuda.synchronize()
+
+    def iterate(self, a, h, a_next, h_next):
+        c, n, nnz, G_ = self.ctx, self.n, self.nnz, self.G
+        c.launch("spmv_csr", *self.ATA, self.V[h], self.PAT, self.V[a_next], self.CAT, n, nnz)
+        c.launch("spmv_csr", *self.AA, self.V[a], self.PA, self.V[h_next], self.CA, n, nnz)
+        c.launch("seg_l2norm", self.V[a_next], self.SEG, self.NAS, self.SAS, G_, n)
+        c.launch("seg_l2norm", self.V[h_next], self.SEG, self.NHS, self.SHS, G_, n)
+        c.launch("seg_scale", self.V[a_next], self.SEG, self.NAS, G_, n)
+        c.launch("seg_scale", self.V[h_next], self.SEG, self.NHS, G_, n)
+
+    def segment(self, vec, g):
+        return vec[int(self.seg_host[g]):int(self.seg_host[g + 1])]
+
+
 class DlDag:
     """DL: two convolution branches (conv3x3 + bias + ReLU + 2x2 max-pool on
     the tensor cores), a global average pool of each, and a dense layer over
