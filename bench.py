@@ -176,7 +176,8 @@ def cpu_oracle_rate(seconds, n_per_vec=1_000_000):
 
 
 def run_reference(args, rank):
-    if rank != 0:
+    from paper_2012_09646_gb300 import replicas as RP
+    if not RP.reports(rank):
         return
     n_per_vec = 1_000_000
     import datagen
@@ -729,6 +730,7 @@ def run_ours(args, rank, world, local_rank):
     from paper_2012_09646_gb300 import analysis
     from paper_2012_09646_gb300 import gdag as G
     from paper_2012_09646_gb300 import workloads as W
+    from paper_2012_09646_gb300 import replicas as RP
 
     dev = torch.device("cuda", local_rank)
     torch.cuda.set_device(dev)
@@ -775,14 +777,10 @@ def run_ours(args, rank, world, local_rank):
     ms_par = e0.elapsed_time(e1) / args.steps
     ctx.sync()
     barrier()
-    ms_all = ms_par
-    if dist:
-        t = torch.tensor([ms_par], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_all = float(t.item())
+    ms_all = RP.job_time_ms(dist, ms_par, device=dev)
 
     out = None
-    if rank == 0:
+    if RP.reports(rank):
         nsteps_other = max(5, args.steps // 2)
         # ---- the dominant kernel alone: bs_call, 20 launches back to back
         st = torch.cuda.Stream()
@@ -887,7 +885,7 @@ def run_ours(args, rank, world, local_rank):
         # ---- CPU oracle baseline (bounded sample)
         cpu_val, cpu_samples, cpu_s = cpu_oracle_rate(args.cpu_seconds)
 
-        value = world * 1e3 / ms_all
+        value = RP.job_value(world, 1, ms_all)  # one DAG per rank per step
         gpu_launches = args.steps * N_VEC
         out = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -983,9 +981,8 @@ def main():
     if args.profile:
         run_profile(args)
         return
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    from paper_2012_09646_gb300 import replicas as RP
+    rank, world, local_rank = RP.rank_env()
     if args.impl == "reference":
         run_reference(args, rank)
         return
