@@ -840,13 +840,40 @@ def run_ours(args, rank, world, local_rank):
             inputs = SV.Inputs(datagen, scales, full=data)
             serve_out = {"kinds": list(SV.KINDS), "scale_buckets": scales,
                          "budget_gb": 40, "response_bytes_max": SV.RESPONSE_BYTES, "runs": []}
+            # fusion thresholds from the autotuner: the largest node size at
+            # which one fused element beats the same nodes issued one by one
+            from paper_2012_09646_gb300 import autotune as AT
+            keep = []
+
+            def bs_member(ctx_, n, i):
+                St, Ct = torch.rand(n, device="cuda") * 90 + 10, torch.empty(n, device="cuda")
+                keep.append((St, Ct))
+                return (ctx_.array(St), ctx_.array(Ct), n, 60.0, 0.1, 0.2, 1.0)
+
+            def sq_member(ctx_, n, i):
+                Xt = torch.rand(n, device="cuda")
+                keep.append(Xt)
+                return (ctx_.array(Xt), n)
+            thr_bs, t_bs = AT.tune_fusion("bs_call", bs_member, [int(1e7 * s) for s in scales], group=10, reps=5)
+            thr_sq, t_sq = AT.tune_fusion("vec_square", sq_member, [int(1e6 * s) for s in scales], group=8, reps=5)
+            del keep
+            fuse_max = {"B&S": thr_bs, "VEC": thr_sq}
+            serve_out["fusion"] = {"fuse_max_elems": fuse_max,
+                                   "bs_call_group10_ms": {str(n): {"separate": a, "fused": b}
+                                                          for n, (a, b) in t_bs.items()},
+                                   "vec_square_group8_ms": {str(n): {"separate": a, "fused": b}
+                                                            for n, (a, b) in t_sq.items()}}
             for rate in (2000.0, 1000.0):
-                srv = SV.Server(inputs)
-                srv.warm()
-                reqs = SV.poisson_requests(rate, int(rate * args.serve_seconds), scales, seed=7)
-                srv.run(reqs)
-                srv.close()
-                serve_out["runs"].append(dict(SV.latency_summary(reqs), offered_req_s=rate))
+                for fm in (None, fuse_max):
+                    srv = SV.Server(inputs, fuse_max=fm)
+                    srv.warm()
+                    f0 = srv.ctx.stats()["fused_members"]
+                    reqs = SV.poisson_requests(rate, int(rate * args.serve_seconds), scales, seed=7)
+                    srv.run(reqs)
+                    fused_members = srv.ctx.stats()["fused_members"] - f0
+                    srv.close()
+                    serve_out["runs"].append(dict(SV.latency_summary(reqs), offered_req_s=rate,
+                                                  fusion=bool(fm), fused_members=fused_members))
             del inputs
 
         # ---- e2e through the public API with host buffers

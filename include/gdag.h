@@ -186,6 +186,7 @@ typedef struct {
     int64_t host_waits;     /* host blocking waits                           */
     int32_t streams;        /* streams in the pool                           */
     int32_t active;         /* nodes currently active                        */
+    int64_t fused_members;  /* launches folded into gdag_launch_fused calls  */
 } gdag_stats;
 
 /* ------------------------------------------------------------ lifetime */
@@ -351,6 +352,27 @@ int gdag_kernel_register(gdag_ctx *ctx, const char *name, const void *fn,
 int gdag_launch(gdag_ctx *ctx, gdag_kernel k, gdag_dim3 grid, gdag_dim3 block,
                 size_t smem, const gdag_arg *args, int32_t nargs,
                 int64_t *node_out);
+
+/* Fused launch (kernel consolidation, Section II: merging independent
+ * kernels into one launch raises utilization).  `count` launches of built-in
+ * kernel k, given as count consecutive argument lists of nargs arguments
+ * each (args[m*nargs .. m*nargs+nargs-1] is member m, exactly as it would be
+ * passed to gdag_launch), become ONE DAG element and one persistent kernel
+ * launch that walks every member's work.  The element's accesses are the
+ * union of the members' (a write dominates), so it gets every edge any
+ * member would get and each member's result is what its own gdag_launch
+ * would give, bit for bit (elementwise members trivially; reductions keep
+ * the member's own block partition and combine order).  Members use the
+ * kernel's automatic launch shape.  Kernels with a fused form: vec_square,
+ * vec_reduce_diff, bs_call.  1 <= count <= GDAG_FUSED_MAX; members beyond the
+ * kernel's per-launch table (GDAG_FUSED_TABLE) go to further launches of the
+ * same element, back to back on its stream.  Errors: INVALID (kernel without
+ * a fused form, a member that gdag_launch would reject, or an array written
+ * by one member and used by another), CUDA. */
+#define GDAG_FUSED_MAX   4096
+#define GDAG_FUSED_TABLE 128
+int gdag_launch_fused(gdag_ctx *ctx, gdag_kernel k, const gdag_arg *args,
+                      int32_t nargs, int32_t count, int64_t *node_out);
 
 /* Launch kernel k on the caller's CUDA stream with no dependency tracking
  * (hand-scheduled baselines and graph capture).  Arrays are resolved to their

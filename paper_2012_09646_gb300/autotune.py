@@ -14,6 +14,11 @@ the next step.  This module does both on top of the library's own timing
 ``tune_streams``
     for a DAG program, time its makespan under each stream-pool size and
     return the best (the pool size trades concurrency against contention).
+``tune_fusion``
+    for a kernel with a fused form, time a group of same-kind launches issued
+    one by one (each its own DAG element, spread over streams) against one
+    fused element, per member size; the largest size at which fusing is no
+    slower is the fusion threshold the serving loop uses.
 """
 from __future__ import annotations
 
@@ -111,3 +116,44 @@ def tune_streams(build, step, candidates=(1, 2, 4, 8, 16, 32), steps=10, policy=
         ctx.close()
         del obj
     return min(out, key=out.get), out
+
+
+def tune_fusion(name, make_member, sizes, group=8, reps=5, max_streams=16):
+    """``make_member(ctx, n, i)`` -> the argument tuple of member i of size n
+    (arrays registered on ctx; members must not conflict).  For each n in
+    ``sizes``: ms per group of ``group`` members issued as separate elements
+    (PARALLEL) and as one fused element.  Returns (threshold, {n: (separate
+    ms, fused ms)}), threshold = the largest n at which the fused group is no
+    slower (0 if none)."""
+    out = {}
+    s0 = torch.cuda.Stream()
+    for n in sizes:
+        ms = []
+        for fused in (False, True):
+            ctx = G.Context(max_streams=max_streams)
+            members = [make_member(ctx, n, i) for i in range(group)]
+
+            def issue():
+                if fused:
+                    ctx.launch_fused(name, members)
+                else:
+                    for m in members:
+                        ctx.launch(name, *m)
+            for _ in range(2):
+                issue()
+            ctx.sync()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(s0)
+            ctx.fork(s0.cuda_stream)
+            for _ in range(reps):
+                issue()
+            ctx.wait_all(s0.cuda_stream)
+            e1.record(s0)
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1) / reps)
+            ctx.sync()
+            ctx.close()
+        out[n] = tuple(ms)
+    ok = [n for n, (sep, fu) in out.items() if fu <= sep]
+    return (max(ok) if ok else 0), out

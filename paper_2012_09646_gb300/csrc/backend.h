@@ -37,6 +37,7 @@ class Backend {
     virtual int wait_query_event(void *e) { return event_query(e); }
     virtual int wait_query_stream(void *s) { return stream_query(s); }
     virtual int launch(const KernelEntry &k, const LaunchArgs &a, void *s) = 0;
+    virtual int launch_fused(const KernelEntry &k, const LaunchArgs *a, int count, void *s) = 0;
     virtual int copy_h2d(void *dst, const void *src, size_t bytes, void *s) = 0;
     virtual int copy_d2h(void *dst, const void *src, size_t bytes, void *s) = 0;
     virtual int external(void (*fn)(void *, void *), void *user, void *s) = 0;

@@ -114,6 +114,12 @@ class CudaBackend final : public Backend {
         dim3 g(a.grid[0], a.grid[1], a.grid[2]), b(a.block[0], a.block[1], a.block[2]);
         return chk(cudaLaunchKernel(k.fn, g, b, argp, a.smem, (cudaStream_t)s), k.name.c_str());
     }
+    int launch_fused(const KernelEntry &k, const LaunchArgs *a, int count, void *s) override
+    {
+        cudaError_t e = (cudaError_t)k.fused(a, count, s);
+        if (e == cudaSuccess) e = cudaGetLastError();
+        return chk(e, k.name.c_str());
+    }
     int copy_h2d(void *dst, const void *src, size_t bytes, void *s) override
     {
         return chk(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, (cudaStream_t)s), "cudaMemcpyAsync H2D");
@@ -197,6 +203,7 @@ class FakeBackend final : public Backend {
     }
     int stream_query(void *) override { return complete_ == 1 ? BE_OK : BE_NOT_READY; }
     int launch(const KernelEntry &, const LaunchArgs &, void *) override { return op(); }
+    int launch_fused(const KernelEntry &, const LaunchArgs *, int, void *) override { return op(); }
     int copy_h2d(void *, const void *, size_t, void *) override { return op(); }
     int copy_d2h(void *, const void *, size_t, void *) override { return op(); }
     int external(void (*)(void *, void *), void *, void *) override { return op(); }

@@ -44,6 +44,10 @@ typedef const char *(*ValidateFn)(const LaunchArgs &);
 // Issue the node's kernel launch(es) on `stream` (a cudaStream_t); returns a
 // cudaError_t value.
 typedef int (*LauncherFn)(const LaunchArgs &, void *stream);
+// Issue `count` launches of the kernel (each validated, automatic launch
+// shape) as one persistent launch on `stream` (more than one only when
+// `count` exceeds the kernel's table capacity); returns a cudaError_t value.
+typedef int (*FusedLauncherFn)(const LaunchArgs *members, int count, void *stream);
 
 struct KernelEntry {
     std::string name;
@@ -52,6 +56,7 @@ struct KernelEntry {
     gdag_argspec spec[kMaxArgs];
     ValidateFn validate = nullptr;  // built-ins only
     LauncherFn launcher = nullptr;  // built-ins only
+    FusedLauncherFn fused = nullptr;  // built-ins with a fused form only
 };
 
 // Built-in kernels (defined by the kernel translation units).

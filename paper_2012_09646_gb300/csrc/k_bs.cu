@@ -141,6 +141,63 @@ __global__ void __launch_bounds__(512, 3) bs_call_kernel(const float *__restrict
     }
 }
 
+// Fused form: the work items are chunks of kBsChunk4 float4s (kBsChunk
+// options); member m owns chunks [start[m], start[m+1]), its last chunk also
+// pricing the n & 3 scalar tail (or, when S or C is not 16-byte aligned, the
+// chunk's options one by one).  Every option gets the same arithmetic as in
+// bs_call_kernel, so each member's prices equal its plain launch's.  All
+// four loads of a thread are issued before any pricing (64 bytes in flight
+// per thread).
+constexpr int kBsFusedThreads = 256;
+constexpr int64_t kBsChunk4 = (int64_t)kBsFusedThreads * 4;
+constexpr int64_t kBsChunk = kBsChunk4 * 4;
+
+struct BsFused {
+    int count;
+    int64_t start[kFuseTable + 1];
+    const float *S[kFuseTable];
+    float *C[kFuseTable];
+    int64_t n[kFuseTable];
+    BsConst c[kFuseTable];
+};
+
+__global__ void __launch_bounds__(kBsFusedThreads, 4) bs_call_fused_kernel(const __grid_constant__ BsFused t)
+{
+    const int64_t total = t.start[t.count];
+    for (int64_t it = blockIdx.x; it < total; it += gridDim.x) {
+        const int m = fused_member(t.start, t.count, it);
+        const int64_t local = it - t.start[m];
+        const float *S = t.S[m];
+        float *C = t.C[m];
+        const int64_t n = t.n[m];
+        const BsConst c = t.c[m];
+        if (((reinterpret_cast<uintptr_t>(S) | reinterpret_cast<uintptr_t>(C)) & 15) == 0) {
+            const float4 *S4 = reinterpret_cast<const float4 *>(S);
+            float4 *C4 = reinterpret_cast<float4 *>(C);
+            const int64_t n4 = n >> 2;
+            const int64_t base = local * kBsChunk4 + threadIdx.x;
+            float4 v[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const int64_t i = base + k * kBsFusedThreads;
+                if (i < n4) v[k] = __ldcs(S4 + i);
+            }
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const int64_t i = base + k * kBsFusedThreads;
+                if (i < n4) __stcs(C4 + i, bs_price4(v[k], c));
+            }
+            if (it == t.start[m + 1] - 1 && threadIdx.x < (n & 3)) {
+                const int64_t i = (n4 << 2) + threadIdx.x;
+                C[i] = bs_price(S[i], c);
+            }
+        } else {
+            const int64_t hi = (local + 1) * kBsChunk < n ? (local + 1) * kBsChunk : n;
+            for (int64_t i = local * kBsChunk + threadIdx.x; i < hi; i += kBsFusedThreads) C[i] = bs_price(S[i], c);
+        }
+    }
+}
+
 namespace {
 
 const char *validate_bs(const LaunchArgs &a)
@@ -151,6 +208,19 @@ const char *validate_bs(const LaunchArgs &a)
     if (!(a.f32(3) > 0.f) || !(a.f32(5) > 0.f) || !(a.f32(6) > 0.f)) return "K, sigma and T must be > 0";
     if (!a.auto_cfg && (int64_t)a.block[0] * a.block[1] * a.block[2] > 512) return "blocks of at most 512 threads";
     return nullptr;
+}
+
+// The kernel's constants from (K, r, sigma, T), computed in double.
+BsConst bs_const(const LaunchArgs &a)
+{
+    const double K = a.f32(3), r = a.f32(4), sigma = a.f32(5), T = a.f32(6);
+    const double vol = sigma * std::sqrt(T);
+    BsConst c;
+    c.a = (float)(std::log(2.0) / vol);
+    c.b = (float)(((r + 0.5 * sigma * sigma) * T - std::log(K)) / vol);
+    c.vol = (float)vol;
+    c.k_disc = (float)(K * std::exp(-r * T));
+    return c;
 }
 
 int launch_bs(const LaunchArgs &a, void *s)
@@ -168,15 +238,33 @@ int launch_bs(const LaunchArgs &a, void *s)
         const int64_t wave = (int64_t)sm_count() * per_sm;
         g = (unsigned)(need < wave ? need : wave);
     }
-    const double K = a.f32(3), r = a.f32(4), sigma = a.f32(5), T = a.f32(6);
-    const double vol = sigma * std::sqrt(T);
-    BsConst c;
-    c.a = (float)(std::log(2.0) / vol);
-    c.b = (float)(((r + 0.5 * sigma * sigma) * T - std::log(K)) / vol);
-    c.vol = (float)vol;
-    c.k_disc = (float)(K * std::exp(-r * T));
-    bs_call_kernel<<<g, b, 0, (cudaStream_t)s>>>(a.p<float>(0), a.p<float>(1), n, c);
+    bs_call_kernel<<<g, b, 0, (cudaStream_t)s>>>(a.p<float>(0), a.p<float>(1), n, bs_const(a));
     return cudaGetLastError();
+}
+
+int fused_bs(const LaunchArgs *a, int count, void *s)
+{
+    for (int off = 0; off < count; off += kFuseTable) {
+        BsFused t;
+        t.count = count - off < kFuseTable ? count - off : kFuseTable;
+        t.start[0] = 0;
+        for (int m = 0; m < t.count; ++m) {
+            const LaunchArgs &la = a[off + m];
+            t.S[m] = la.p<float>(0);
+            t.C[m] = la.p<float>(1);
+            t.n[m] = la.i64(2);
+            t.c[m] = bs_const(la);
+            t.start[m + 1] = t.start[m] + ceil_div(t.n[m], kBsChunk);
+        }
+        const int64_t total = t.start[t.count];
+        if (total == 0) continue;
+        static int per_sm = 0;
+        const unsigned g = fused_grid((const void *)bs_call_fused_kernel, kBsFusedThreads, total, per_sm);
+        bs_call_fused_kernel<<<g, kBsFusedThreads, 0, (cudaStream_t)s>>>(t);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 }  // namespace
@@ -196,6 +284,7 @@ void append_bs_kernels(std::vector<KernelEntry> &v)
     e.spec[6] = scal(4);
     e.validate = validate_bs;
     e.launcher = launch_bs;
+    e.fused = fused_bs;
     v.push_back(e);
 }
 

@@ -9,6 +9,30 @@ namespace gdag {
 
 // x := x * x.  HBM-bound: 8 bytes per element.  128-bit loads/stores when x is
 // 16-byte aligned, kUnroll float4 in flight per thread.
+// One tile: float4s [base, base + kThreads*kUnroll) of x4 below n4
+// (blockDim.x == kThreads for the fused form; the plain kernel passes its
+// own block size).
+__device__ __forceinline__ void square_tile(float4 *x4, int64_t n4, int64_t base, int64_t bd)
+{
+    float4 v[kUnroll];
+#pragma unroll
+    for (int k = 0; k < kUnroll; ++k) {
+        int64_t i = base + threadIdx.x + k * bd;
+        if (i < n4) v[k] = x4[i];
+    }
+#pragma unroll
+    for (int k = 0; k < kUnroll; ++k) {
+        int64_t i = base + threadIdx.x + k * bd;
+        if (i < n4) {
+            v[k].x *= v[k].x;
+            v[k].y *= v[k].y;
+            v[k].z *= v[k].z;
+            v[k].w *= v[k].w;
+            x4[i] = v[k];
+        }
+    }
+}
+
 __global__ void __launch_bounds__(1024) vec_square_kernel(float *__restrict__ x, int64_t n)
 {
     if ((reinterpret_cast<uintptr_t>(x) & 15) == 0) {
@@ -16,25 +40,8 @@ __global__ void __launch_bounds__(1024) vec_square_kernel(float *__restrict__ x,
         const int64_t n4 = n >> 2;
         const int64_t bd = blockDim.x;
         const int64_t tile = bd * kUnroll;
-        for (int64_t base = (int64_t)blockIdx.x * tile; base < n4; base += (int64_t)gridDim.x * tile) {
-            float4 v[kUnroll];
-#pragma unroll
-            for (int k = 0; k < kUnroll; ++k) {
-                int64_t i = base + threadIdx.x + k * bd;
-                if (i < n4) v[k] = x4[i];
-            }
-#pragma unroll
-            for (int k = 0; k < kUnroll; ++k) {
-                int64_t i = base + threadIdx.x + k * bd;
-                if (i < n4) {
-                    v[k].x *= v[k].x;
-                    v[k].y *= v[k].y;
-                    v[k].z *= v[k].z;
-                    v[k].w *= v[k].w;
-                    x4[i] = v[k];
-                }
-            }
-        }
+        for (int64_t base = (int64_t)blockIdx.x * tile; base < n4; base += (int64_t)gridDim.x * tile)
+            square_tile(x4, n4, base, bd);
         if (blockIdx.x == 0 && threadIdx.x < (n & 3)) {
             int64_t i = (n4 << 2) + threadIdx.x;
             x[i] = x[i] * x[i];
@@ -45,16 +52,53 @@ __global__ void __launch_bounds__(1024) vec_square_kernel(float *__restrict__ x,
     }
 }
 
+// Fused form: the work items are tiles of kThreads*kUnroll float4s
+// (kFuseElems floats); member m owns tiles [start[m], start[m+1]), its last
+// tile also squaring the n & 3 scalar tail.  One persistent grid walks all
+// tiles of all members.
+constexpr int64_t kFuseElems = (int64_t)kThreads * kUnroll * 4;
+
+struct SquareFused {
+    int count;
+    int64_t start[kFuseTable + 1];
+    float *x[kFuseTable];
+    int64_t n[kFuseTable];
+};
+
+__global__ void __launch_bounds__(kThreads) vec_square_fused_kernel(const __grid_constant__ SquareFused t)
+{
+    const int64_t total = t.start[t.count];
+    for (int64_t it = blockIdx.x; it < total; it += gridDim.x) {
+        const int m = fused_member(t.start, t.count, it);
+        const int64_t local = it - t.start[m];
+        const bool last = it == t.start[m + 1] - 1;
+        float *x = t.x[m];
+        const int64_t n = t.n[m];
+        if ((reinterpret_cast<uintptr_t>(x) & 15) == 0) {
+            const int64_t n4 = n >> 2;
+            square_tile(reinterpret_cast<float4 *>(x), n4, local * (kThreads * kUnroll), kThreads);
+            if (last && threadIdx.x < (n & 3)) {
+                int64_t i = (n4 << 2) + threadIdx.x;
+                x[i] = x[i] * x[i];
+            }
+        } else {
+            const int64_t hi = (local + 1) * kFuseElems < n ? (local + 1) * kFuseElems : n;
+            for (int64_t i = local * kFuseElems + threadIdx.x; i < hi; i += kThreads) x[i] = x[i] * x[i];
+        }
+    }
+}
+
 // z[0] = sum_i (x_i - y_i).  Per thread: Kahan-compensated fp32; per block:
 // fp64 tree; blocks combined in block order by the last block to arrive.
 // scratch: kReduceMaxBlocks doubles + arrival counter (zero on entry, reset
 // to zero on exit).
-__global__ void __launch_bounds__(kThreads) vec_reduce_diff_kernel(const float *__restrict__ x,
-                                                                    const float *__restrict__ y,
-                                                                    float *__restrict__ z, double *scratch,
-                                                                    int64_t n)
+// Block `vb` of a launch of `G` blocks of kThreads threads; the plain kernel
+// passes (blockIdx.x, gridDim.x), the fused one a member's virtual block, so
+// both sum the same elements in the same order.
+__device__ __forceinline__ void reduce_diff_block(const float *__restrict__ x, const float *__restrict__ y,
+                                                  float *__restrict__ z, double *scratch, int64_t n, int64_t vb,
+                                                  int64_t G, double *sh)
 {
-    __shared__ double sh[kThreads / 32];
     Kahan acc;
     const bool aligned = ((reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(y)) & 15) == 0;
     if (aligned) {
@@ -62,7 +106,7 @@ __global__ void __launch_bounds__(kThreads) vec_reduce_diff_kernel(const float *
         const float4 *y4 = reinterpret_cast<const float4 *>(y);
         const int64_t n4 = n >> 2;
         const int64_t tile = (int64_t)kThreads * kUnroll;
-        for (int64_t base = (int64_t)blockIdx.x * tile; base < n4; base += (int64_t)gridDim.x * tile) {
+        for (int64_t base = vb * tile; base < n4; base += G * tile) {
             float4 a[kUnroll], b[kUnroll];
 #pragma unroll
             for (int k = 0; k < kUnroll; ++k) {
@@ -83,24 +127,58 @@ __global__ void __launch_bounds__(kThreads) vec_reduce_diff_kernel(const float *
                 }
             }
         }
-        if (blockIdx.x == 0 && threadIdx.x < (n & 3)) {
+        if (vb == 0 && threadIdx.x < (n & 3)) {
             int64_t i = (n4 << 2) + threadIdx.x;
             acc.add(x[i] - y[i]);
         }
     } else {
-        for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-            acc.add(x[i] - y[i]);
+        for (int64_t i = vb * kThreads + threadIdx.x; i < n; i += G * kThreads) acc.add(x[i] - y[i]);
     }
     double bs = block_sum(acc.value(), sh);
-    if (threadIdx.x == 0) scratch[blockIdx.x] = bs;
+    if (threadIdx.x == 0) scratch[vb] = bs;
     unsigned *counter = reinterpret_cast<unsigned *>(scratch + kReduceMaxBlocks);
-    if (!arrive_last(counter)) return;
+    if (!arrive_last(counter, (unsigned)G)) return;
     double t = 0.0;
-    for (unsigned b = threadIdx.x; b < gridDim.x; b += kThreads) t += ((volatile double *)scratch)[b];
+    for (int64_t b = threadIdx.x; b < G; b += kThreads) t += ((volatile double *)scratch)[b];
     t = block_sum(t, sh);
     if (threadIdx.x == 0) {
         z[0] = (float)t;
         *counter = 0u;
+    }
+}
+
+__global__ void __launch_bounds__(kThreads) vec_reduce_diff_kernel(const float *__restrict__ x,
+                                                                    const float *__restrict__ y,
+                                                                    float *__restrict__ z, double *scratch,
+                                                                    int64_t n)
+{
+    __shared__ double sh[kThreads / 32];
+    reduce_diff_block(x, y, z, scratch, n, blockIdx.x, gridDim.x, sh);
+}
+
+// Fused form: member m runs its own reduce_grid(n >> 2) virtual blocks
+// [start[m], start[m+1]) (the grid its plain launch would use), so its sum
+// is bit-identical to the plain launch's; a persistent grid walks them all.
+// No block waits for another (the last arrival of a member combines), so
+// any physical grid size is safe.
+struct ReduceDiffFused {
+    int count;
+    int64_t start[kFuseTable + 1];
+    const float *x[kFuseTable];
+    const float *y[kFuseTable];
+    float *z[kFuseTable];
+    double *scratch[kFuseTable];
+    int64_t n[kFuseTable];
+};
+
+__global__ void __launch_bounds__(kThreads) vec_reduce_diff_fused_kernel(const __grid_constant__ ReduceDiffFused t)
+{
+    __shared__ double sh[kThreads / 32];
+    const int64_t total = t.start[t.count];
+    for (int64_t it = blockIdx.x; it < total; it += gridDim.x) {
+        const int m = fused_member(t.start, t.count, it);
+        reduce_diff_block(t.x[m], t.y[m], t.z[m], t.scratch[m], t.n[m], it - t.start[m],
+                          t.start[m + 1] - t.start[m], sh);
     }
 }
 
@@ -145,6 +223,54 @@ int launch_reduce_diff(const LaunchArgs &a, void *s)
     return cudaGetLastError();
 }
 
+int fused_square(const LaunchArgs *a, int count, void *s)
+{
+    for (int off = 0; off < count; off += kFuseTable) {
+        SquareFused t;
+        t.count = count - off < kFuseTable ? count - off : kFuseTable;
+        t.start[0] = 0;
+        for (int m = 0; m < t.count; ++m) {
+            const LaunchArgs &la = a[off + m];
+            t.x[m] = la.p<float>(0);
+            t.n[m] = la.i64(1);
+            t.start[m + 1] = t.start[m] + ceil_div(t.n[m], kFuseElems);
+        }
+        const int64_t total = t.start[t.count];
+        if (total == 0) continue;
+        static int per_sm = 0;
+        const unsigned g = fused_grid((const void *)vec_square_fused_kernel, kThreads, total, per_sm);
+        vec_square_fused_kernel<<<g, kThreads, 0, (cudaStream_t)s>>>(t);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+int fused_reduce_diff(const LaunchArgs *a, int count, void *s)
+{
+    for (int off = 0; off < count; off += kFuseTable) {
+        ReduceDiffFused t;
+        t.count = count - off < kFuseTable ? count - off : kFuseTable;
+        t.start[0] = 0;
+        for (int m = 0; m < t.count; ++m) {
+            const LaunchArgs &la = a[off + m];
+            t.x[m] = la.p<float>(0);
+            t.y[m] = la.p<float>(1);
+            t.z[m] = la.p<float>(2);
+            t.scratch[m] = la.p<double>(3);
+            t.n[m] = la.i64(4);
+            t.start[m + 1] = t.start[m] + reduce_grid(t.n[m] >> 2);  // n = 0 still writes z = 0
+        }
+        const int64_t total = t.start[t.count];
+        static int per_sm = 0;
+        const unsigned g = fused_grid((const void *)vec_reduce_diff_fused_kernel, kThreads, total, per_sm);
+        vec_reduce_diff_fused_kernel<<<g, kThreads, 0, (cudaStream_t)s>>>(t);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
 }  // namespace
 
 void append_vec_kernels(std::vector<KernelEntry> &v)
@@ -157,6 +283,7 @@ void append_vec_kernels(std::vector<KernelEntry> &v)
     e.spec[1] = scal(8);
     e.validate = validate_square;
     e.launcher = launch_square;
+    e.fused = fused_square;
     v.push_back(e);
 
     KernelEntry r;
@@ -170,6 +297,7 @@ void append_vec_kernels(std::vector<KernelEntry> &v)
     r.spec[4] = scal(8);
     r.validate = validate_reduce_diff;
     r.launcher = launch_reduce_diff;
+    r.fused = fused_reduce_diff;
     v.push_back(r);
 }
 

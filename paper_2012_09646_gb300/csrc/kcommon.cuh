@@ -6,6 +6,8 @@
 
 #include <cstdint>
 
+#include "gdag.h"
+
 namespace gdag {
 
 // Multiprocessor count of the current device (queried once per process).
@@ -21,6 +23,21 @@ inline int sm_count()
 }
 
 inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+// Members per fused launch (the kernel-parameter table's capacity).
+constexpr int kFuseTable = GDAG_FUSED_TABLE;
+
+// Persistent grid for a fused launch of `threads`-thread blocks: resident
+// blocks of kernel `fn` per SM (queried once, into `per_sm`) x SMs, at most
+// `items`.
+inline unsigned fused_grid(const void *fn, int threads, int64_t items, int &per_sm)
+{
+    if (per_sm < 1 && (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, 0) != cudaSuccess ||
+                       per_sm < 1))
+        per_sm = 1;
+    const int64_t wave = (int64_t)sm_count() * per_sm;
+    return (unsigned)(items < wave ? items : wave);
+}
 
 // Streaming kernels: each block handles tiles of kThreads x kUnroll float4
 // and grid-strides over tiles.  The grid is capped at kBlocksPerSm blocks per
@@ -93,18 +110,34 @@ __device__ __forceinline__ double block_sum(double v, double *sh)
 // Last-block-done: each block publishes its partial(s), then one arrival
 // counter tells the last block to combine all partials in block order.
 // Returns true in the block that arrived last (all threads).
-__device__ __forceinline__ bool arrive_last(unsigned *counter)
+// `blocks` is the number of (virtual) blocks that publish partials.
+__device__ __forceinline__ bool arrive_last(unsigned *counter, unsigned blocks)
 {
     __shared__ bool last;
     __threadfence();  // partials visible device-wide before arrival
     __syncthreads();
     if (threadIdx.x == 0) {
         unsigned prev = atomicAdd(counter, 1u);
-        last = (prev == gridDim.x - 1);
+        last = (prev == blocks - 1);
     }
     __syncthreads();
     if (last) __threadfence();  // see every other block's partials
     return last;
+}
+__device__ __forceinline__ bool arrive_last(unsigned *counter) { return arrive_last(counter, gridDim.x); }
+
+// Fused launches: member m of a table owns the work items
+// [start[m], start[m+1]); returns the member of item `it` (the largest m with
+// start[m] <= it).  Uniform across a block, so the loads are broadcasts.
+__device__ __forceinline__ int fused_member(const int64_t *start, int count, int64_t it)
+{
+    int lo = 0, hi = count;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (start[mid] <= it) lo = mid;
+        else hi = mid;
+    }
+    return lo;
 }
 
 // x / d rounded to nearest, given r = RN(1/d): Markstein's correction

@@ -838,6 +838,72 @@ int gdag_launch(gdag_ctx *c, gdag_kernel k, gdag_dim3 grid, gdag_dim3 block, siz
     return c->finish(id, s);
 }
 
+int gdag_launch_fused(gdag_ctx *c, gdag_kernel k, const gdag_arg *args, int32_t nargs, int32_t count,
+                      int64_t *node_out)
+{
+    if (!c) return GDAG_ERR_INVALID;
+    int r = c->guard();
+    if (r) return r;
+    if (k < 0 || (size_t)k >= c->kernels.size()) return c->fail(GDAG_ERR_INVALID, "unknown kernel %d", k);
+    const KernelEntry &e = c->kernels[(size_t)k];
+    if (!e.fused) return c->fail(GDAG_ERR_INVALID, "%s has no fused form", e.name.c_str());
+    if (count < 1 || count > GDAG_FUSED_MAX)
+        return c->fail(GDAG_ERR_INVALID, "fused launch of %d members (1..%d)", count, GDAG_FUSED_MAX);
+    if (nargs != e.nargs)
+        return c->fail(GDAG_ERR_INVALID, "%s takes %d arguments, got %d", e.name.c_str(), e.nargs, nargs);
+    if (!args) return c->fail(GDAG_ERR_INVALID, "null argument list");
+    const gdag_dim3 autocfg{0, 0, 0};
+    std::vector<LaunchArgs> la((size_t)count);
+    std::vector<Access> acc;
+    for (int32_t m = 0; m < count; ++m) {
+        Access one[gdag::kMaxArgs];
+        int n1;
+        r = resolve(c, k, autocfg, autocfg, 0, args + (size_t)m * (size_t)nargs, nargs, la[(size_t)m], one, &n1);
+        if (r) return r;
+        // the element's accesses: the union of its members' (write dominates)
+        for (int i = 0; i < n1; ++i) {
+            size_t j = 0;
+            while (j < acc.size() && acc[j].array != one[i].array) ++j;
+            if (j == acc.size()) acc.push_back(one[i]);
+            else acc[j].bits |= one[i].bits;
+        }
+    }
+    // an array that a member writes is touched by no other member: inside
+    // one launch the members' order is undefined
+    for (size_t j = 0; j < acc.size(); ++j) {
+        if (!(acc[j].bits & gdag::W_BIT)) continue;
+        int users = 0;
+        for (int32_t m = 0; m < count; ++m) {
+            const gdag_arg *a = args + (size_t)m * (size_t)nargs;
+            bool uses = false;
+            for (int i = 0; i < nargs; ++i) uses = uses || (a[i].kind == GDAG_ARG_ARRAY && a[i].array == acc[j].array);
+            users += uses;
+        }
+        if (users > 1)
+            return c->fail(GDAG_ERR_INVALID, "%s: array %d is written by one member of a fused launch and used by %d",
+                           e.name.c_str(), acc[j].array, users);
+    }
+    c->capture_note(acc.data(), (int)acc.size());
+    int64_t id = c->next_id();
+    c->infer(id, acc.data(), (int)acc.size());
+    for (const Access &x : acc)
+        if (x.bits & gdag::W_BIT) c->arrays[(size_t)x.array].host_valid = false;
+    c->push_node(GDAG_NODE_KERNEL);
+    if (node_out) *node_out = id;
+    int32_t s;
+    r = c->place(id, &s);
+    if (r) {
+        c->retire(id);
+        return r;
+    }
+    c->log_op(GDAG_OP_LAUNCH, s, -1, id);
+    ++c->st.launches;
+    c->st.fused_members += count;
+    r = c->be->launch_fused(c->kernels[(size_t)k], la.data(), count, c->streams[(size_t)s].handle);
+    if (r) return c->abort_node(id, r, "fused launch");
+    return c->finish(id, s);
+}
+
 int gdag_launch_raw(gdag_ctx *c, gdag_kernel k, gdag_dim3 grid, gdag_dim3 block, size_t smem, const gdag_arg *args,
                     int32_t nargs, void *stream)
 {

@@ -44,6 +44,8 @@ GDAG_EDGE_RAW, GDAG_EDGE_WAR, GDAG_EDGE_WAW = 0, 1, 2
 GDAG_NODE_KERNEL, GDAG_NODE_HOST_WRITE, GDAG_NODE_HOST_READ, GDAG_NODE_EXTERNAL, GDAG_NODE_HOST_PREFETCH = 0, 1, 2, 3, 4
 GDAG_NODE_GRAPH = 5
 GDAG_ARG_ARRAY, GDAG_ARG_SCALAR = 0, 1
+GDAG_FUSED_MAX = 4096     # members per gdag_launch_fused call
+GDAG_FUSED_TABLE = 128    # members per persistent launch of a fused element
 (GDAG_OP_LAUNCH, GDAG_OP_COPY_H2D, GDAG_OP_COPY_D2H, GDAG_OP_EXTERNAL, GDAG_OP_RECORD, GDAG_OP_WAIT,
  GDAG_OP_HOST_WAIT, GDAG_OP_STREAM_SYNC, GDAG_OP_HOST_NODE, GDAG_OP_QUERY_DONE) = range(10)
 
@@ -94,7 +96,7 @@ class gdag_trace_rec(ctypes.Structure):
 class gdag_stats(ctypes.Structure):
     _fields_ = [("nodes", ctypes.c_int64), ("edges", ctypes.c_int64), ("waits", ctypes.c_int64),
                 ("launches", ctypes.c_int64), ("copies", ctypes.c_int64), ("host_waits", ctypes.c_int64),
-                ("streams", ctypes.c_int32), ("active", ctypes.c_int32)]
+                ("streams", ctypes.c_int32), ("active", ctypes.c_int32), ("fused_members", ctypes.c_int64)]
 
 
 EXTERNAL_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
@@ -124,6 +126,7 @@ SIGNATURES = {
     "gdag_kernel_register": (ctypes.c_int, [_ctx, ctypes.c_char_p, _vp, _i32, _P(gdag_argspec), _P(_i32)]),
     "gdag_launch": (ctypes.c_int, [_ctx, _i32, gdag_dim3, gdag_dim3, _sz, _P(gdag_arg), _i32, _P(_i64)]),
     "gdag_launch_raw": (ctypes.c_int, [_ctx, _i32, gdag_dim3, gdag_dim3, _sz, _P(gdag_arg), _i32, _vp]),
+    "gdag_launch_fused": (ctypes.c_int, [_ctx, _i32, _P(gdag_arg), _i32, _i32, _P(_i64)]),
     "gdag_launch_external": (ctypes.c_int, [_ctx, EXTERNAL_FN, _vp, _P(_i32), _P(_i32), _i32, _P(_i64)]),
     "gdag_sync": (ctypes.c_int, [_ctx]),
     "gdag_stream_wait_all": (ctypes.c_int, [_ctx, _vp]),
@@ -249,6 +252,14 @@ def gdag_launch(ctx, k, grid, block, smem, args):
     node = _i64()
     arr = (gdag_arg * max(1, len(args)))(*args)
     _check(ctx, lib().gdag_launch(ctx, k, grid, block, smem, arr, len(args), ctypes.byref(node)))
+    return node.value
+
+
+def gdag_launch_fused(ctx, k, args, nargs, count):
+    """args: count * nargs gdag_arg values, member after member."""
+    node = _i64()
+    arr = (gdag_arg * max(1, len(args)))(*args)
+    _check(ctx, lib().gdag_launch_fused(ctx, k, arr, nargs, count, ctypes.byref(node)))
     return node.value
 
 
@@ -483,6 +494,19 @@ class Context:
         g = gdag_dim3(*grid) if grid else gdag_dim3(0, 0, 0)
         b = gdag_dim3(*block) if block else gdag_dim3(0, 0, 0)
         return gdag_launch(self.h, kid, g, b, smem, a)
+
+    def launch_fused(self, name, members):
+        """One DAG element and one persistent launch for several launches of
+        built-in kernel `name`; `members` is a list of argument tuples, each
+        as `launch` would take it."""
+        flat = []
+        kid = None
+        for m in members:
+            kid, a = self._args(name, m)
+            flat.extend(a)
+        if kid is None:
+            raise GdagError(GDAG_ERR_INVALID, "fused launch of no members")
+        return gdag_launch_fused(self.h, kid, flat, len(flat) // len(members), len(members))
 
     def launch_raw(self, name, *args, stream, grid=None, block=None, smem=0):
         kid, a = self._args(name, args)

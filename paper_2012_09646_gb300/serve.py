@@ -15,6 +15,13 @@ they arrive as a Poisson stream.  One dispatcher thread does four things:
 * records each request's latency, from its arrival time to the moment its
   response is on the host.
 
+Requests admitted in the same dispatcher pass are issued together.  With
+fusion on, the small same-kind nodes of a VEC or B&S group (at most
+``fuse_max[kind]`` elements each) become one fused element per node kind
+(``gdag_launch_fused``: one persistent launch for the whole group), so a
+burst of small requests costs a few launches instead of a few per request.
+Each member's result is bit-identical to its unfused launch.
+
 Inputs that a request only reads (price books, images, feature matrices,
 graphs) are resident per scale bucket and shared by every request of that
 bucket.  A response is the head of the request's result (at most
@@ -132,8 +139,11 @@ class Request:
 class Server:
     """One gdag context shared by every request."""
 
-    def __init__(self, inputs, budget_bytes=40 << 30, max_streams=32, device="cuda"):
+    def __init__(self, inputs, budget_bytes=40 << 30, max_streams=32, device="cuda", fuse_max=None):
+        """``fuse_max``: {kind: largest node size (elements) that is fused
+        across requests}; None or {} turns fusion off."""
         self.inp = inputs
+        self.fuse_max = dict(fuse_max or {})
         self.budget = budget_bytes
         self.used = 0
         self.device = device
@@ -288,6 +298,72 @@ class Server:
         if r.final is None:
             r.final = self._last_node()
 
+    def _fusable(self, r):
+        lim = self.fuse_max.get(r.kind)
+        if lim is None or r.kind not in ("VEC", "B&S"):
+            return False
+        return self.inp.data[(r.kind, self.inp.bucket(r.scale))]["n"] <= lim
+
+    def issue_batch(self, rs):
+        """Issue the requests admitted in one pass: fusable VEC and B&S
+        requests as fused groups (when two or more share a kind), the rest
+        one by one."""
+        groups = {"VEC": [], "B&S": []}
+        for r in rs:
+            if self._fusable(r):
+                groups[r.kind].append(r)
+            else:
+                self.issue(r)
+        for kind, g in groups.items():
+            if len(g) == 1:
+                self.issue(g[0])
+            elif g:
+                (self._issue_vec_group if kind == "VEC" else self._issue_bs_group)(g)
+
+    def _issue_vec_group(self, g):
+        c = self.ctx
+        sq, red = [], []
+        for r in g:
+            d = self.inp.data[("VEC", self.inp.bucket(r.scale))]
+            n = d["n"]
+            r.slot = self._slot()
+            X = self._arr(r, torch.empty(n, dtype=F32, device=self.device), host=d["hx"])
+            Y = self._arr(r, torch.empty(n, dtype=F32, device=self.device), host=d["hy"])
+            Z = self._arr(r, torch.empty(1, dtype=F32, device=self.device), host=r.slot)
+            S = self._zeroed(r, G.gdag_scratch_bytes("vec_reduce_diff", n))
+            c.write(X, None, 0, 4 * n)
+            c.write(Y, None, 0, 4 * n)
+            sq += [(X, n), (Y, n)]
+            red.append((X, Y, Z, S, n))
+            r.resp = (Z, 4)
+        c.launch_fused("vec_square", sq)
+        c.launch_fused("vec_reduce_diff", red)
+        for r in g:
+            self._finish_issue(r)
+
+    def _issue_bs_group(self, g):
+        members = []
+        for r in g:
+            b = self.inp.bucket(r.scale)
+            d = self.inp.data[("B&S", b)]
+            n = d["n"]
+            r.slot = self._slot()
+            outs = []
+            for i, St in enumerate(d["S"]):
+                Sa = self._shared(("bs", b, i), St)
+                Ca = self._arr(r, torch.empty(n, dtype=F32, device=self.device), host=r.slot if i == 0 else None)
+                members.append((Sa, Ca, n, 60.0, 0.1, 0.2, 1.0))
+                outs.append(Ca)
+            r.resp = (outs[0], min(4 * n, RESPONSE_BYTES))
+        self.ctx.launch_fused("bs_call", members)
+        for r in g:
+            self._finish_issue(r)
+
+    def _finish_issue(self, r):
+        arr, nb = r.resp
+        self.ctx.prefetch_host(arr, 0, nb)
+        r.final = self._last_node()
+
     def _last_node(self):
         return G.gdag_stats_get(self.ctx.h).nodes - 1
 
@@ -357,17 +433,20 @@ class Server:
             while i < len(requests) and requests[i].arrival <= now:
                 pending.append(requests[i])
                 i += 1
+            batch = []
             while pending:
                 r = pending[0]
                 need = self.working_bytes(r)
-                if inflight and self.used + need > self.budget:
+                if (inflight or batch) and self.used + need > self.budget:
                     break
                 pending.popleft()
                 r.admitted = now
                 r.need = need  # released on completion: the same figure
                 self.used += need
-                self.issue(r)
-                inflight.append(r)
+                batch.append(r)
+            if batch:
+                self.issue_batch(batch)
+                inflight.extend(batch)
             still = []
             for r in inflight:
                 if self.ctx.done(r.final):

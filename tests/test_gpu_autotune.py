@@ -1,6 +1,6 @@
 """Autotuner on the GPU: the tuned launch shape gives the same results as
-the default one, the history picks up traced nodes, and the stream-pool
-search returns a measured candidate."""
+the default one, the history picks up traced nodes, and the stream-pool and
+fusion-threshold searches return measured candidates."""
 import numpy as np
 import pytest
 import torch
@@ -52,3 +52,18 @@ def test_history_and_stream_tuning():
         return d
     best, times = AT.tune_streams(build, lambda d: d.step_resident(), candidates=(1, 4), steps=3)
     assert best in (1, 4) and set(times) == {1, 4}
+
+
+def test_fusion_threshold_search():
+    keep = []
+
+    def member(ctx, n, i):
+        S = torch.rand(n, device="cuda") * 90 + 10
+        C = torch.empty(n, device="cuda")
+        keep.append((S, C))
+        return (ctx.array(S), ctx.array(C), n, 60.0, 0.1, 0.2, 1.0)
+    sizes = (1 << 12, 1 << 16, 1 << 20)
+    thr, times = AT.tune_fusion("bs_call", member, sizes, group=6, reps=3)
+    assert set(times) == set(sizes) and all(a > 0 and b > 0 for a, b in times.values())
+    assert thr in (0,) + sizes
+    assert all(times[n][1] <= times[n][0] for n in sizes if n == thr)

@@ -1,7 +1,8 @@
 """Serving loop: requests of every kind and several scales arriving as a
 Poisson stream on one context give the same response as each request served
-alone (the kernels are deterministic, so the bits match), and a tiny memory
-budget still serves every request (FIFO admission)."""
+alone (the kernels are deterministic, so the bits match), with and without
+fusing small same-kind nodes across requests, and a tiny memory budget still
+serves every request (FIFO admission)."""
 import copy
 
 import numpy as np
@@ -70,3 +71,45 @@ def test_vec_response_matches_oracle(inputs):
     ref = P.vec(d["hx"].numpy(), d["hy"].numpy())
     assert abs(float(r.resp_view[0]) - ref["z"]) <= 1e-5 * ref["z_scale"]
     srv.close()
+
+
+FUSE_ALL = {"VEC": 1 << 30, "B&S": 1 << 30}
+
+
+def _alone(inputs, reqs):
+    srv = SV.Server(inputs)
+    srv.warm()
+    out = {}
+    for r in fresh(reqs):
+        r.arrival = 0.0
+        srv.run([r])
+        out[r.rid] = r
+    srv.close()
+    return out
+
+
+def test_fused_mix_equals_alone(inputs):
+    """A burst (all arriving at once: one admission pass, fused groups) and a
+    Poisson stream, with fusion on, against each request served alone."""
+    burst = [SV.Request(r.rid, r.kind, r.scale, 0.0)
+             for r in SV.poisson_requests(rate=1.0, count=24, scales=SCALES, seed=5)]
+    stream = SV.poisson_requests(rate=20000.0, count=48, scales=SCALES, seed=6)
+    for reqs in (burst, stream):
+        srv = SV.Server(inputs, fuse_max=FUSE_ALL)
+        srv.warm()
+        f0 = srv.ctx.stats()["fused_members"]
+        mixed = srv.run(fresh(reqs))
+        fused = srv.ctx.stats()["fused_members"] - f0
+        srv.close()
+        if reqs is burst:
+            # one admission pass: every VEC/B&S request of a kind that has
+            # two or more goes through the fused elements (VEC: 2 squares +
+            # 1 reduction per request; B&S: 10 prices per request)
+            nv = sum(r.kind == "VEC" for r in reqs)
+            nb = sum(r.kind == "B&S" for r in reqs)
+            assert nv >= 2 and nb >= 2
+            assert fused == 3 * nv + 10 * nb
+        alone = _alone(inputs, reqs)
+        for m in mixed:
+            assert m.done_at is not None
+            assert torch.equal(m.resp_view, alone[m.rid].resp_view), (m.kind, m.scale)
