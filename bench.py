@@ -36,8 +36,8 @@ UNIT = "DAG/s"
 # DRAM bytes (read + write) of one bs_call launch from one ncu capture
 # (profiles/bs_call_bs_10x1e7.md), valid only for the kernel source it was
 # taken on: a changed k_bs.cu reports null.
-BS_CALL_TRAFFIC = {"bytes": 41357568,
-                   "sha256": "e0e1a6855692e06bcd4fe8a1a159530a28d1a0224ec7678f569969c3e1b5c3c9",
+BS_CALL_TRAFFIC = {"bytes": 41512960,
+                   "sha256": "8894957c9c15c28b855b2eed352f6cdef6b0e7e5b47a457a92f597cacb855bcd",
                    "note": "one launch captured alone: its 40 MB output is still in L2 when the kernel ends"}
 WORKLOAD = "B&S: 10 independent Black-Scholes call nodes, 10 x 1e7 float32 spot prices U[10,100), K=60 r=0.1 sigma=0.2 T=1"
 
@@ -143,6 +143,33 @@ def bs_call_traffic():
     with open(os.path.join(ROOT, "paper_2012_09646_gb300", "csrc", "k_bs.cu"), "rb") as f:
         h = hashlib.sha256(f.read()).hexdigest()
     return BS_CALL_TRAFFIC["bytes"] if h == BS_CALL_TRAFFIC["sha256"] else None
+
+
+def time_launches(torch, issue, reps):
+    """Device ms per call of ``issue(stream_handle)`` (which enqueues one
+    kernel on that stream), with the host taken out of the measurement: the
+    calls are captured once into a CUDA graph, and the graph's replay is timed
+    with CUDA events on its stream (launching from Python one by one would
+    time the host's enqueue rate for any kernel shorter than it)."""
+    s = torch.cuda.Stream()
+    for _ in range(2):
+        issue(s.cuda_stream)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        for _ in range(reps):
+            issue(s.cuda_stream)
+    with torch.cuda.stream(s):
+        g.replay()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        g.replay()
+        e1.record(s)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    del g
+    return ms
 
 
 def measured_peaks():
@@ -671,15 +698,8 @@ def measure_dag(torch, G, spec, steps, peak_gbs, link):
         if kind == "k":
             key = (e[1],) + tuple(getattr(x, "handle", x) for x in e[2])
             if key not in solo_cache:
-                for _ in range(2):
-                    lctx.launch_raw(e[1], *e[2], stream=st.cuda_stream)
-                a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                a0.record(st)
-                for _ in range(5):
-                    lctx.launch_raw(e[1], *e[2], stream=st.cuda_stream)
-                a1.record(st)
-                torch.cuda.synchronize()
-                solo_cache[key] = a0.elapsed_time(a1) / 5
+                solo_cache[key] = time_launches(
+                    torch, lambda sh: lctx.launch_raw(e[1], *e[2], stream=sh), 5)
             return solo_cache[key]
         nb = e[2]
         return nb / (link[kind] * 1e9) * 1e3
@@ -783,19 +803,17 @@ def run_ours(args, rank, world, local_rank):
     if RP.reports(rank):
         nsteps_other = max(5, args.steps // 2)
         # ---- the dominant kernel alone: bs_call, 20 launches back to back
-        st = torch.cuda.Stream()
-        for i in range(3):
-            ctx.launch_raw("bs_call", dag.SA[i], dag.CA[i], N_OPTS, K, r, sg, T, stream=st.cuda_stream)
-        torch.cuda.synchronize()
+        # (one per price vector in turn: 800 MB cycled, more than L2),
+        # replayed from a CUDA graph so that the host's launch rate is not
+        # what is timed
         reps = 20
-        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a0.record(st)
-        for i in range(reps):
-            ctx.launch_raw("bs_call", dag.SA[i % N_VEC], dag.CA[i % N_VEC], N_OPTS, K, r, sg, T,
-                           stream=st.cuda_stream)
-        a1.record(st)
-        torch.cuda.synchronize()
-        ms_solo = a0.elapsed_time(a1) / reps
+        turn = [0]
+
+        def one_bs(sh):
+            i = turn[0] % N_VEC
+            turn[0] += 1
+            ctx.launch_raw("bs_call", dag.SA[i], dag.CA[i], N_OPTS, K, r, sg, T, stream=sh)
+        ms_solo = time_launches(torch, one_bs, reps)
         bytes_launch = BYTES_PER_OPTION * N_OPTS
         achieved = bytes_launch / (ms_solo * 1e-3) / 1e9
 
@@ -883,12 +901,17 @@ def run_ours(args, rank, world, local_rank):
         for _ in range(2):
             d2.step_e2e()
         ctx2.sync()
+        # each step ends with its host reads (the step's results are on the
+        # host), so per-step host times are complete; the median of them is
+        # the step time (a shared host link can stall a single step)
         n_e2e = max(5, args.steps // 5)
         torch.cuda.synchronize()
-        t0 = time.perf_counter()
+        step_ms = []
         for _ in range(n_e2e):
+            t0 = time.perf_counter()
             d2.step_e2e()
-        ms_e2e = (time.perf_counter() - t0) * 1e3 / n_e2e
+            step_ms.append((time.perf_counter() - t0) * 1e3)
+        ms_e2e = statistics.median(step_ms)
         ctx2.sync()
         from oracle import numeric as N
         idx = np.arange(0, N_OPTS, 997)
@@ -933,6 +956,7 @@ def run_ours(args, rank, world, local_rank):
                          "traffic_note": BS_CALL_TRAFFIC["note"],
                          "algorithmic_bytes_per_launch": bytes_launch, "launch_ms": ms_solo},
             "e2e": {"value": 1e3 / ms_e2e, "unit": UNIT, "ms_per_step": ms_e2e,
+                    "ms_per_step_min_max": [min(step_ms), max(step_ms)], "steps_timed": n_e2e,
                     "h2d_bytes_per_step": N_VEC * 4 * N_OPTS, "d2h_bytes_per_step": N_VEC * 4 * N_OPTS,
                     "max_rel_err_sampled": e2e_err, "overlap": overlap,
                     "link_gbs": link, "link_bound_ms": N_VEC * 4 * N_OPTS / (min(link.values()) * 1e9) * 1e3},

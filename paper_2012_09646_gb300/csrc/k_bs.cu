@@ -102,54 +102,64 @@ __device__ __forceinline__ float4 bs_price4(float4 v, const BsConst &c)
 }
 
 // 8 bytes of HBM traffic per option (4 in, 4 out); streaming loads/stores
-// (each byte is touched once).  The grid is sized to the resident block
-// count (one wave) and each thread walks float4s with a stride of the whole
-// grid, two at a time, loading the next two before pricing the current two
-// (32 bytes in flight per thread): every block gets the same work to within
-// one float4 per thread, so there is no tail wave.
-// at most 512 threads a block and at least three blocks an SM: 40 registers,
-// so six 256-thread blocks (32 bytes in flight each thread) fit an SM
-__global__ void __launch_bounds__(512, 3) bs_call_kernel(const float *__restrict__ S, float *__restrict__ C, int64_t n,
-                                                       BsConst c)
+// (each byte is touched once).  A block works through chunks of
+// kBsUnroll float4s per thread: all kBsUnroll loads of a thread are issued
+// before any pricing (64 bytes in flight per thread), then the chunk is
+// priced and stored.  At most 256 threads a block and at least four blocks
+// an SM leave 64 registers a thread: enough to keep the rational function's
+// constants (packed pairs) in registers instead of re-materialising them for
+// every option, which at a 40-register cap cost about a quarter of the
+// kernel's time.
+constexpr int kBsThreads = 256;
+constexpr int kBsUnroll = 4;
+
+// Options [base4*4, ...) of one chunk: float4s base4 + threadIdx.x + k*bd
+// for k < kBsUnroll, below n4.
+__device__ __forceinline__ void bs_chunk(const float4 *__restrict__ S4, float4 *__restrict__ C4, int64_t n4,
+                                         int64_t base4, int64_t bd, const BsConst &c)
 {
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    float4 v[kBsUnroll];
+#pragma unroll
+    for (int k = 0; k < kBsUnroll; ++k) {
+        const int64_t i = base4 + threadIdx.x + k * bd;
+        if (i < n4) v[k] = __ldcs(S4 + i);
+    }
+#pragma unroll
+    for (int k = 0; k < kBsUnroll; ++k) {
+        const int64_t i = base4 + threadIdx.x + k * bd;
+        if (i < n4) __stcs(C4 + i, bs_price4(v[k], c));
+    }
+}
+
+// The grid is one resident wave; blocks stride over chunks.
+__global__ void __launch_bounds__(kBsThreads, 4) bs_call_kernel(const float *__restrict__ S, float *__restrict__ C,
+                                                                int64_t n, BsConst c)
+{
+    const int64_t bd = blockDim.x;
     if (((reinterpret_cast<uintptr_t>(S) | reinterpret_cast<uintptr_t>(C)) & 15) == 0) {
-        const float4 *S4 = reinterpret_cast<const float4 *>(S);
-        float4 *C4 = reinterpret_cast<float4 *>(C);
-        const int64_t n4 = n >> 2;
-        const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
-        int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-        float4 v0 = i < n4 ? __ldcs(S4 + i) : zero;
-        float4 v1 = i + stride < n4 ? __ldcs(S4 + i + stride) : zero;
-        while (i < n4) {
-            const int64_t j = i + stride, i2 = i + 2 * stride;
-            const float4 w0 = i2 < n4 ? __ldcs(S4 + i2) : zero;
-            const float4 w1 = i2 + stride < n4 ? __ldcs(S4 + i2 + stride) : zero;
-            __stcs(C4 + i, bs_price4(v0, c));
-            if (j < n4) __stcs(C4 + j, bs_price4(v1, c));
-            v0 = w0;
-            v1 = w1;
-            i = i2;
-        }
+        const int64_t n4 = n >> 2, chunk = bd * kBsUnroll;
+        for (int64_t base = (int64_t)blockIdx.x * chunk; base < n4; base += (int64_t)gridDim.x * chunk)
+            bs_chunk(reinterpret_cast<const float4 *>(S), reinterpret_cast<float4 *>(C), n4, base, bd, c);
         if (blockIdx.x == 0 && threadIdx.x < (n & 3)) {
-            int64_t t = (n4 << 2) + threadIdx.x;
+            const int64_t t = (n4 << 2) + threadIdx.x;
             C[t] = bs_price(S[t], c);
         }
     } else {
-        for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
+        for (int64_t i = (int64_t)blockIdx.x * bd + threadIdx.x; i < n; i += (int64_t)gridDim.x * bd)
             C[i] = bs_price(S[i], c);
     }
 }
 
-// Fused form: the work items are chunks of kBsChunk4 float4s (kBsChunk
-// options); member m owns chunks [start[m], start[m+1]), its last chunk also
-// pricing the n & 3 scalar tail (or, when S or C is not 16-byte aligned, the
-// chunk's options one by one).  Every option gets the same arithmetic as in
-// bs_call_kernel, so each member's prices equal its plain launch's.  All
-// four loads of a thread are issued before any pricing (64 bytes in flight
-// per thread).
-constexpr int kBsFusedThreads = 256;
-constexpr int64_t kBsChunk4 = (int64_t)kBsFusedThreads * 4;
+// Fused form: the work items are chunks of kBsChunk options (one bs_chunk
+// of kBsThreads threads); member m owns chunks [start[m], start[m+1]), its
+// last chunk also pricing the n & 3 scalar tail (or, when S or C is not
+// 16-byte aligned, the chunk's options one by one).  Every option gets the
+// same arithmetic as in bs_call_kernel, so each member's prices equal its
+// plain launch's.  Each block takes one contiguous range of chunks and
+// finds its first member by binary search, then steps to the next member
+// as its range crosses one (the member table lives in parameter memory:
+// one search per block, not per chunk).
+constexpr int64_t kBsChunk4 = (int64_t)kBsThreads * kBsUnroll;
 constexpr int64_t kBsChunk = kBsChunk4 * 4;
 
 struct BsFused {
@@ -161,39 +171,41 @@ struct BsFused {
     BsConst c[kFuseTable];
 };
 
-__global__ void __launch_bounds__(kBsFusedThreads, 4) bs_call_fused_kernel(const __grid_constant__ BsFused t)
+__global__ void __launch_bounds__(kBsThreads, 4) bs_call_fused_kernel(const __grid_constant__ BsFused t)
 {
     const int64_t total = t.start[t.count];
-    for (int64_t it = blockIdx.x; it < total; it += gridDim.x) {
-        const int m = fused_member(t.start, t.count, it);
-        const int64_t local = it - t.start[m];
-        const float *S = t.S[m];
-        float *C = t.C[m];
-        const int64_t n = t.n[m];
-        const BsConst c = t.c[m];
+    const int64_t per = (total + gridDim.x - 1) / gridDim.x;
+    const int64_t it0 = (int64_t)blockIdx.x * per;
+    const int64_t it1 = it0 + per < total ? it0 + per : total;
+    if (it0 >= it1) return;
+    int m = fused_member(t.start, t.count, it0);
+    int64_t first = t.start[m], next = t.start[m + 1];
+    const float *S = t.S[m];
+    float *C = t.C[m];
+    int64_t n = t.n[m];
+    BsConst c = t.c[m];
+    for (int64_t it = it0; it < it1; ++it) {
+        while (it >= next) {  // uniform across the block
+            ++m;
+            first = next;
+            next = t.start[m + 1];
+            S = t.S[m];
+            C = t.C[m];
+            n = t.n[m];
+            c = t.c[m];
+        }
+        const int64_t local = it - first;
         if (((reinterpret_cast<uintptr_t>(S) | reinterpret_cast<uintptr_t>(C)) & 15) == 0) {
-            const float4 *S4 = reinterpret_cast<const float4 *>(S);
-            float4 *C4 = reinterpret_cast<float4 *>(C);
             const int64_t n4 = n >> 2;
-            const int64_t base = local * kBsChunk4 + threadIdx.x;
-            float4 v[4];
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                const int64_t i = base + k * kBsFusedThreads;
-                if (i < n4) v[k] = __ldcs(S4 + i);
-            }
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                const int64_t i = base + k * kBsFusedThreads;
-                if (i < n4) __stcs(C4 + i, bs_price4(v[k], c));
-            }
-            if (it == t.start[m + 1] - 1 && threadIdx.x < (n & 3)) {
+            bs_chunk(reinterpret_cast<const float4 *>(S), reinterpret_cast<float4 *>(C), n4, local * kBsChunk4,
+                     kBsThreads, c);
+            if (it == next - 1 && threadIdx.x < (n & 3)) {
                 const int64_t i = (n4 << 2) + threadIdx.x;
                 C[i] = bs_price(S[i], c);
             }
         } else {
             const int64_t hi = (local + 1) * kBsChunk < n ? (local + 1) * kBsChunk : n;
-            for (int64_t i = local * kBsChunk + threadIdx.x; i < hi; i += kBsFusedThreads) C[i] = bs_price(S[i], c);
+            for (int64_t i = local * kBsChunk + threadIdx.x; i < hi; i += kBsThreads) C[i] = bs_price(S[i], c);
         }
     }
 }
@@ -206,7 +218,7 @@ const char *validate_bs(const LaunchArgs &a)
     if (n < 0) return "n < 0";
     if (a.bytes[0] / 4 < (size_t)n || a.bytes[1] / 4 < (size_t)n) return "S or C smaller than n floats";
     if (!(a.f32(3) > 0.f) || !(a.f32(5) > 0.f) || !(a.f32(6) > 0.f)) return "K, sigma and T must be > 0";
-    if (!a.auto_cfg && (int64_t)a.block[0] * a.block[1] * a.block[2] > 512) return "blocks of at most 512 threads";
+    if (!a.auto_cfg && (int64_t)a.block[0] * a.block[1] * a.block[2] > kBsThreads) return "blocks of at most 256 threads";
     return nullptr;
 }
 
@@ -227,16 +239,12 @@ int launch_bs(const LaunchArgs &a, void *s)
 {
     int64_t n = a.i64(2);
     if (n == 0) return cudaSuccess;
-    unsigned b = a.auto_cfg ? kThreads : a.block[0];
+    unsigned b = a.auto_cfg ? kBsThreads : a.block[0];
     unsigned g = a.grid[0];
     if (a.auto_cfg) {
-        static int per_sm = 0;  // resident blocks of kThreads per SM
-        if (!per_sm && cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, bs_call_kernel, kThreads, 0) != cudaSuccess)
-            per_sm = 4;
-        if (per_sm < 1) per_sm = 1;
-        const int64_t need = ceil_div((n >> 2) > 0 ? (n >> 2) : 1, kThreads);
-        const int64_t wave = (int64_t)sm_count() * per_sm;
-        g = (unsigned)(need < wave ? need : wave);
+        static int per_sm = 0;  // resident blocks of kBsThreads per SM
+        g = fused_grid((const void *)bs_call_kernel, kBsThreads, ceil_div((n >> 2) > 0 ? (n >> 2) : 1, kBsChunk4),
+                       per_sm);
     }
     bs_call_kernel<<<g, b, 0, (cudaStream_t)s>>>(a.p<float>(0), a.p<float>(1), n, bs_const(a));
     return cudaGetLastError();
@@ -259,8 +267,8 @@ int fused_bs(const LaunchArgs *a, int count, void *s)
         const int64_t total = t.start[t.count];
         if (total == 0) continue;
         static int per_sm = 0;
-        const unsigned g = fused_grid((const void *)bs_call_fused_kernel, kBsFusedThreads, total, per_sm);
-        bs_call_fused_kernel<<<g, kBsFusedThreads, 0, (cudaStream_t)s>>>(t);
+        const unsigned g = fused_grid((const void *)bs_call_fused_kernel, kBsThreads, total, per_sm);
+        bs_call_fused_kernel<<<g, kBsThreads, 0, (cudaStream_t)s>>>(t);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }

@@ -85,34 +85,15 @@ __global__ void __launch_bounds__(kSpmvThreads) spmv_merge_kernel(const int *__r
     const int2 p0 = part[b], p1 = part[b + 1];
     const int i0 = p0.x, j0 = p0.y;
     const int tile_rows = p1.x - i0, tile_nnz = p1.y - j0;
-    // Staging.  col, val and rowptr are streamed once (evict-first) and x is
-    // gathered through L2.  Every load of a thread is issued before any is
-    // used (kSpmvIpt col/val/rowptr loads, then kSpmvIpt dependent x
-    // gathers), so a thread keeps up to kSpmvIpt gather chains in flight
-    // instead of one: the gathers are latency-bound, not bandwidth-bound.
-    int cidx[kSpmvIpt], ends[kSpmvIpt];
-    float vv[kSpmvIpt], xv[kSpmvIpt];
-#pragma unroll
-    for (int k = 0; k < kSpmvIpt; ++k) {
-        const int t = threadIdx.x + k * kSpmvThreads;
-        if (t < tile_nnz) {
-            cidx[k] = __ldcs(col + j0 + t);
-            vv[k] = __ldcs(val + j0 + t);
-        }
-        if (t <= tile_rows) ends[k] = i0 + t < nrows ? __ldcs(rowptr + i0 + t + 1) - j0 : INT_MAX;
+    for (int t = threadIdx.x; t <= tile_rows; t += kSpmvThreads) {
+        const int r = i0 + t;
+        s_end[t] = r < nrows ? __ldcs(rowptr + r + 1) - j0 : INT_MAX;
     }
-#pragma unroll
-    for (int k = 0; k < kSpmvIpt; ++k)
-        if (threadIdx.x + k * kSpmvThreads < tile_nnz) xv[k] = __ldg(x + cidx[k]);
-#pragma unroll
-    for (int k = 0; k < kSpmvIpt; ++k) {
-        const int t = threadIdx.x + k * kSpmvThreads;
-        if (t < tile_nnz) s_prod[t] = vv[k] * xv[k];
-        if (t <= tile_rows) s_end[t] = ends[k];
+    // col and val are streamed once (evict-first), x is gathered through L2
+    for (int t = threadIdx.x; t < tile_nnz; t += kSpmvThreads) {
+        const int j = j0 + t;
+        s_prod[t] = __ldcs(val + j) * __ldg(x + __ldcs(col + j));
     }
-    // a tile of kSpmvTile rows and no nonzeros has one more row end
-    if (threadIdx.x == 0 && tile_rows == kSpmvTile)
-        s_end[kSpmvTile] = i0 + kSpmvTile < nrows ? __ldcs(rowptr + i0 + kSpmvTile + 1) - j0 : INT_MAX;
     __syncthreads();
 
     // this thread's start on the tile's merge path

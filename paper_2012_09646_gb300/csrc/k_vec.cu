@@ -67,11 +67,22 @@ struct SquareFused {
 
 __global__ void __launch_bounds__(kThreads) vec_square_fused_kernel(const __grid_constant__ SquareFused t)
 {
+    // one contiguous range of tiles per block; one member search per block
     const int64_t total = t.start[t.count];
-    for (int64_t it = blockIdx.x; it < total; it += gridDim.x) {
-        const int m = fused_member(t.start, t.count, it);
-        const int64_t local = it - t.start[m];
-        const bool last = it == t.start[m + 1] - 1;
+    const int64_t per = (total + gridDim.x - 1) / gridDim.x;
+    const int64_t it0 = (int64_t)blockIdx.x * per;
+    const int64_t it1 = it0 + per < total ? it0 + per : total;
+    if (it0 >= it1) return;
+    int m = fused_member(t.start, t.count, it0);
+    int64_t first = t.start[m], next = t.start[m + 1];
+    for (int64_t it = it0; it < it1; ++it) {
+        while (it >= next) {
+            ++m;
+            first = next;
+            next = t.start[m + 1];
+        }
+        const int64_t local = it - first;
+        const bool last = it == next - 1;
         float *x = t.x[m];
         const int64_t n = t.n[m];
         if ((reinterpret_cast<uintptr_t>(x) & 15) == 0) {
@@ -174,11 +185,21 @@ struct ReduceDiffFused {
 __global__ void __launch_bounds__(kThreads) vec_reduce_diff_fused_kernel(const __grid_constant__ ReduceDiffFused t)
 {
     __shared__ double sh[kThreads / 32];
+    // one contiguous range of virtual blocks per block; one member search
     const int64_t total = t.start[t.count];
-    for (int64_t it = blockIdx.x; it < total; it += gridDim.x) {
-        const int m = fused_member(t.start, t.count, it);
-        reduce_diff_block(t.x[m], t.y[m], t.z[m], t.scratch[m], t.n[m], it - t.start[m],
-                          t.start[m + 1] - t.start[m], sh);
+    const int64_t per = (total + gridDim.x - 1) / gridDim.x;
+    const int64_t it0 = (int64_t)blockIdx.x * per;
+    const int64_t it1 = it0 + per < total ? it0 + per : total;
+    if (it0 >= it1) return;
+    int m = fused_member(t.start, t.count, it0);
+    int64_t first = t.start[m], next = t.start[m + 1];
+    for (int64_t it = it0; it < it1; ++it) {
+        while (it >= next) {
+            ++m;
+            first = next;
+            next = t.start[m + 1];
+        }
+        reduce_diff_block(t.x[m], t.y[m], t.z[m], t.scratch[m], t.n[m], it - first, next - first, sh);
     }
 }
 
