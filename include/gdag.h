@@ -291,6 +291,11 @@ int gdag_array_prefetch_host(gdag_ctx *ctx, gdag_array a, size_t off,
  *  ML    dense_scores    (X IN i32[rows*feats], table IN f32[feats*classes],
  *                         bias IN f32[classes], S OUT f32[rows*classes],
  *                         rows i32, feats i32, classes i32)  S = X table + b
+ *                         classes 1..16, feats a multiple of 32, X 16-byte
+ *                         aligned; feats a multiple of 64 up to 1024 runs on
+ *                         the tensor cores (exact products: X in bf16, the
+ *                         table as three bf16 pieces; 128-row tiles holding
+ *                         any |x| > 256 are recomputed on CUDA cores)
  *        row_softmax     (S INOUT f32[rows*classes], rows i32, classes i32)
  *        argmax_combine  (P1 IN, P2 IN, labels OUT i32[rows], rows i32,
  *                         classes i32)                 argmax(P1+P2), lowest

@@ -67,6 +67,7 @@
 
 #include "catalog.h"
 #include "kcommon.cuh"
+#include "tcgen05.cuh"
 
 namespace gdag {
 
@@ -102,8 +103,6 @@ static_assert(kOffHalo % 128 == 0 && kHaloBoxStride % 128 == 0 && kHaloBytes % 1
                   kStageBytes % 128 == 0 && (kHaloBox * 2) % 16 == 0,
               "TMA shared-memory addresses must be 128-byte aligned, box rows multiples of 16 bytes");
 
-__device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
 // byte offset of (row, k) in the canonical K-major, no-swizzle layout
 __device__ __forceinline__ int umma_off(int row, int k)
 {
@@ -138,33 +137,6 @@ __host__ __device__ __forceinline__ int conv_tap(int p, int k)
     return -1;
 }
 
-// wait for phase `parity` of the mbarrier at `bar`; false after about one
-// second or once another thread has raised *abort
-__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity, const volatile int *abort)
-{
-    const long long t0 = clock64();
-    while (true) {
-        uint32_t done;
-        asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
-                     : "=r"(done)
-                     : "r"(bar), "r"(parity)
-                     : "memory");
-        if (done) return true;
-        if (*abort || clock64() - t0 > 2000000000LL) return false;
-    }
-}
-
-// named barrier `id` over `n` threads that also ANDs v across them
-__device__ __forceinline__ bool bar_and(int id, int n, bool v)
-{
-    uint32_t r;
-    asm volatile("{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n bar.red.and.pred q, %2, %3, p;\n selp.u32 %0, 1, 0, q;\n}"
-                 : "=r"(r)
-                 : "r"((uint32_t)v), "r"(id), "r"(n)
-                 : "memory");
-    return r != 0;
-}
-
 __device__ __forceinline__ void conv_tile_coords(int tile, int tiles_x, int rows2, int &b, int &y0, int &x0)
 {
     const int xt = tile % tiles_x;
@@ -194,10 +166,6 @@ __device__ __forceinline__ void conv_issue_halo(const CUtensorMap *tin, unsigned
             : "memory");
 }
 
-__device__ __forceinline__ void mbar_arrive(uint32_t bar)
-{
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
-}
 
 __global__ void __launch_bounds__(kConvThreads, 1)
     conv3x3_relu_pool_kernel(const __grid_constant__ CUtensorMap tin, const __grid_constant__ CUtensorMap tout,
@@ -568,32 +536,11 @@ const char *validate_conv(const LaunchArgs &a)
     return nullptr;
 }
 
-using EncodeTiled = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
-                                 const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
-                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-
-// the driver's tensor-map encoder, through the runtime (no link to libcuda)
-EncodeTiled encode_tiled()
-{
-    static EncodeTiled fn = nullptr;
-    static bool tried = false;
-    if (!tried) {
-        tried = true;
-        void *p = nullptr;
-        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
-                cudaSuccess &&
-            q == cudaDriverEntryPointSuccess)
-            fn = reinterpret_cast<EncodeTiled>(p);
-    }
-    return fn;
-}
-
 // rank-3 bf16 tensor map, dims innermost first, dense; zeros outside
 bool encode_bf16_3d(CUtensorMap *m, void *base, uint64_t d0, uint64_t d1, uint64_t d2, uint32_t b0, uint32_t b1,
                     uint32_t b2)
 {
-    EncodeTiled fn = encode_tiled();
+    EncodeTiled fn = tma_encoder();
     if (!fn) return false;
     const cuuint64_t dims[3] = {d0, d1, d2};
     const cuuint64_t strides[2] = {d0 * 2, d0 * d1 * 2};

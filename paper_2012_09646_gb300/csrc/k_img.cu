@@ -63,6 +63,46 @@ __device__ __forceinline__ void stage_tile(const float *__restrict__ in, float *
     }
 }
 
+__device__ __forceinline__ void img_cp_async16(float *dst, const float *src)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src)
+                 : "memory");
+}
+
+// The same staged tile as stage_tile, copied asynchronously (cp.async,
+// 16 bytes a copy, completion per thread by cp.async.wait_group) when the
+// tile's columns plus halo lie inside an image whose rows are 16-byte
+// aligned (rows are clamped whole, so only the columns decide); returns
+// false, having issued nothing, for the other tiles, which the caller stages
+// with stage_tile.  Uniform across the block.
+template <int R, int HALO, int IW>
+__device__ __forceinline__ bool stage_tile_async(const float *__restrict__ in, float *s, int rows, int cols, int x0,
+                                                 int y0)
+{
+    constexpr int IH = kTileH + 2 * R;
+    const bool fast = (cols & 3) == 0 && (reinterpret_cast<uintptr_t>(in) & 15) == 0 && x0 >= HALO &&
+                      x0 + kTileW + HALO <= cols;
+    if (!fast) return false;
+    constexpr int V = IW / 4;
+    for (int i = threadIdx.x; i < IH * V; i += kImgThreads) {
+        const int r = i / V, c4 = i - r * V;
+        const int y = clampi(y0 + r - R, 0, rows - 1);
+        img_cp_async16(s + r * IW + 4 * c4, in + (size_t)y * cols + (x0 - HALO) + 4 * c4);
+    }
+    return true;
+}
+
+// Persistent blur blocks walk tiles t = blockIdx.x, + gridDim.x, ...
+// (row-major tile order, so neighbouring tiles share their halos in L2),
+// double-buffering the staged input: tile t+gridDim.x is copied while tile t
+// is computed.  (Sobel, whose tile costs less arithmetic, measured faster
+// with one tile per block and the hardware's block scheduler.)
+__device__ __forceinline__ void tile_origin(int t, int ntx, int &x0, int &y0)
+{
+    x0 = (t % ntx) * kTileW;
+    y0 = (t / ntx) * kTileH;
+}
+
 // Store two rows of four outputs (x .. x+3, rows y, y+1) with bounds checks.
 __device__ __forceinline__ void store_2x4(float *__restrict__ out, int rows, int cols, int x, int y, float4 a, float4 b)
 {
@@ -95,54 +135,76 @@ __global__ void __launch_bounds__(kImgThreads) gauss_blur_kernel(const float *__
 {
     constexpr int HALO = (R + 3) / 4 * 4;
     constexpr int IW = kTileW + 2 * HALO, IH = kTileH + 2 * R;
-    __shared__ __align__(16) float s_in[IH * IW];
+    __shared__ __align__(16) float s_in[2][IH * IW];
     __shared__ __align__(16) float s_h[IH * kTileW];
     float wr[2 * R + 1];
 #pragma unroll
     for (int k = 0; k <= 2 * R; ++k) wr[k] = w[k];
-    const int x0 = blockIdx.x * kTileW, y0 = blockIdx.y * kTileH;
-    stage_tile<R, HALO, IW>(in, s_in, rows, cols, x0, y0);
-    __syncthreads();
-    // horizontal: IH rows x 16 groups of four columns
-    for (int t = threadIdx.x; t < IH * (kTileW / 4); t += kImgThreads) {
-        const int r = t >> 4, g = t & 15;
-        const float *row = s_in + r * IW + 4 * g;  // inputs 4g .. 4g + 4 + 2 HALO
-        float v[4 + 2 * HALO];
-#pragma unroll
-        for (int k = 0; k < (4 + 2 * HALO) / 4; ++k) {
-            const float4 q = reinterpret_cast<const float4 *>(row)[k];
-            v[4 * k] = q.x;
-            v[4 * k + 1] = q.y;
-            v[4 * k + 2] = q.z;
-            v[4 * k + 3] = q.w;
+    const int ntx = (cols + kTileW - 1) / kTileW;
+    const int ntiles = ntx * ((rows + kTileH - 1) / kTileH);
+    int t = blockIdx.x, x0, y0;
+    if (t >= ntiles) return;
+    tile_origin(t, ntx, x0, y0);
+    bool staged = stage_tile_async<R, HALO, IW>(in, s_in[0], rows, cols, x0, y0);
+    asm volatile("cp.async.commit_group;" ::: "memory");
+    for (int buf = 0; t < ntiles; t += gridDim.x, buf ^= 1) {
+        tile_origin(t, ntx, x0, y0);
+        // the next tile's copies go into the other buffer (last read before
+        // the previous tile's second barrier)
+        bool staged_next = false;
+        if (t + (int)gridDim.x < ntiles) {
+            int nx0, ny0;
+            tile_origin(t + gridDim.x, ntx, nx0, ny0);
+            staged_next = stage_tile_async<R, HALO, IW>(in, s_in[buf ^ 1], rows, cols, nx0, ny0);
         }
-        float2 lo = make_float2(0.f, 0.f), hi = lo;  // outputs (0,1) and (2,3)
+        asm volatile("cp.async.commit_group;" ::: "memory");
+        asm volatile("cp.async.wait_group 1;" ::: "memory");  // this tile's copies (this thread's) landed
+        if (!staged) stage_tile<R, HALO, IW>(in, s_in[buf], rows, cols, x0, y0);  // border tile: clamped columns
+        __syncthreads();
+        const float *si = s_in[buf];
+        // horizontal: IH rows x 16 groups of four columns
+        for (int q = threadIdx.x; q < IH * (kTileW / 4); q += kImgThreads) {
+            const int r = q >> 4, g = q & 15;
+            const float *row = si + r * IW + 4 * g;  // inputs 4g .. 4g + 4 + 2 HALO
+            float v[4 + 2 * HALO];
+#pragma unroll
+            for (int k = 0; k < (4 + 2 * HALO) / 4; ++k) {
+                const float4 p = reinterpret_cast<const float4 *>(row)[k];
+                v[4 * k] = p.x;
+                v[4 * k + 1] = p.y;
+                v[4 * k + 2] = p.z;
+                v[4 * k + 3] = p.w;
+            }
+            float2 lo = make_float2(0.f, 0.f), hi = lo;  // outputs (0,1) and (2,3)
+#pragma unroll
+            for (int k = 0; k <= 2 * R; ++k) {
+                const float2 wk = make_float2(wr[k], wr[k]);
+                const int o = HALO - R + k;
+                lo = __ffma2_rn(wk, make_float2(v[o], v[o + 1]), lo);
+                hi = __ffma2_rn(wk, make_float2(v[o + 2], v[o + 3]), hi);
+            }
+            reinterpret_cast<float4 *>(s_h + r * kTileW)[g] = make_float4(lo.x, lo.y, hi.x, hi.y);
+        }
+        __syncthreads();
+        // vertical: 16 column groups x 16 row pairs, one block per thread
+        const int g = threadIdx.x & 15, rp = threadIdx.x >> 4;
+        float4 col[2 + 2 * R];
+#pragma unroll
+        for (int k = 0; k < 2 + 2 * R; ++k) col[k] = reinterpret_cast<const float4 *>(s_h + (2 * rp + k) * kTileW)[g];
+        float2 a01 = make_float2(0.f, 0.f), a23 = a01, b01 = a01, b23 = a01;
 #pragma unroll
         for (int k = 0; k <= 2 * R; ++k) {
             const float2 wk = make_float2(wr[k], wr[k]);
-            const int o = HALO - R + k;
-            lo = __ffma2_rn(wk, make_float2(v[o], v[o + 1]), lo);
-            hi = __ffma2_rn(wk, make_float2(v[o + 2], v[o + 3]), hi);
+            a01 = __ffma2_rn(wk, make_float2(col[k].x, col[k].y), a01);
+            a23 = __ffma2_rn(wk, make_float2(col[k].z, col[k].w), a23);
+            b01 = __ffma2_rn(wk, make_float2(col[k + 1].x, col[k + 1].y), b01);
+            b23 = __ffma2_rn(wk, make_float2(col[k + 1].z, col[k + 1].w), b23);
         }
-        reinterpret_cast<float4 *>(s_h + r * kTileW)[g] = make_float4(lo.x, lo.y, hi.x, hi.y);
+        store_2x4(out, rows, cols, x0 + 4 * g, y0 + 2 * rp, make_float4(a01.x, a01.y, a23.x, a23.y),
+                  make_float4(b01.x, b01.y, b23.x, b23.y));
+        staged = staged_next;
     }
-    __syncthreads();
-    // vertical: 16 column groups x 16 row pairs, one block per thread
-    const int g = threadIdx.x & 15, rp = threadIdx.x >> 4;
-    float4 col[2 + 2 * R];
-#pragma unroll
-    for (int k = 0; k < 2 + 2 * R; ++k) col[k] = reinterpret_cast<const float4 *>(s_h + (2 * rp + k) * kTileW)[g];
-    float2 a01 = make_float2(0.f, 0.f), a23 = a01, b01 = a01, b23 = a01;
-#pragma unroll
-    for (int k = 0; k <= 2 * R; ++k) {
-        const float2 wk = make_float2(wr[k], wr[k]);
-        a01 = __ffma2_rn(wk, make_float2(col[k].x, col[k].y), a01);
-        a23 = __ffma2_rn(wk, make_float2(col[k].z, col[k].w), a23);
-        b01 = __ffma2_rn(wk, make_float2(col[k + 1].x, col[k + 1].y), b01);
-        b23 = __ffma2_rn(wk, make_float2(col[k + 1].z, col[k + 1].w), b23);
-    }
-    store_2x4(out, rows, cols, x0 + 4 * g, y0 + 2 * rp, make_float4(a01.x, a01.y, a23.x, a23.y),
-              make_float4(b01.x, b01.y, b23.x, b23.y));
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
 }
 
 // Sobel magnitude: gx = right column - left column with weights (1, 2, 1),
@@ -406,10 +468,18 @@ const char *validate_blur(const LaunchArgs &a)
     return nullptr;
 }
 
+// one resident wave of persistent blocks (at most one per tile)
+unsigned stencil_grid(const void *fn, int &per_sm, int rows, int cols)
+{
+    const int64_t tiles = ceil_div(cols, kTileW) * ceil_div(rows, kTileH);
+    return fused_grid(fn, kImgThreads, tiles, per_sm);
+}
+
 template <int R> void blur_launch(const LaunchArgs &a, cudaStream_t s)
 {
     int rows = a.i32(3), cols = a.i32(4);
-    dim3 g((unsigned)ceil_div(cols, kTileW), (unsigned)ceil_div(rows, kTileH));
+    static int per_sm = 0;
+    const unsigned g = stencil_grid((const void *)gauss_blur_kernel<R>, per_sm, rows, cols);
     gauss_blur_kernel<R><<<g, kImgThreads, 0, s>>>(a.p<float>(0), a.p<float>(1), a.p<float>(2), rows, cols);
 }
 

@@ -6,9 +6,11 @@
 //   row_softmax     S[i][:] := exp(S[i][:] - max) / sum, in place
 //   argmax_combine  labels[i] = argmax_c (P1[i][c] + P2[i][c]), ties -> lowest c
 //
-// dense_scores streams X once (4 bytes per feature per row) against a table
-// of feats x classes floats kept in shared memory: HBM-bound at
-// rows*feats*4 bytes.  Four lanes share a row, each summing a quarter of the
+// dense_scores runs on the tensor cores (k_ml_tc.cu) when feats is a
+// multiple of 64 up to 1024; the CUDA-core forms below take the other
+// shapes.  Either way it streams X once (4 bytes per feature per row)
+// against a table kept in shared memory: HBM-bound at rows*feats*4 bytes.
+// CUDA-core forms:  Four lanes share a row, each summing a quarter of the
 // features (contiguous 32-byte sectors per lane), the eight rows of a warp
 // read the same table entries (shared-memory broadcast), class pairs are
 // accumulated with the packed fp32x2 FMA of sm_100+, and the quarters are
@@ -338,6 +340,10 @@ __global__ void __launch_bounds__(256) argmax_combine_kernel(const float *__rest
     labels[row] = best;
 }
 
+// the tcgen05 form (k_ml_tc.cu): classes <= 16, feats a multiple of 64 up to 1024
+bool scores_tc_ok(int feats, int classes);
+int launch_scores_tc(const LaunchArgs &a, cudaStream_t s);
+
 namespace {
 
 int nc4_of(int classes) { return (classes + 3) / 4; }
@@ -424,6 +430,7 @@ template <int NC4> int scores_launch(const LaunchArgs &a, cudaStream_t s)
 int launch_scores(const LaunchArgs &a, void *sv)
 {
     cudaStream_t s = (cudaStream_t)sv;
+    if (scores_tc_ok(a.i32(5), a.i32(6))) return launch_scores_tc(a, s);
     switch (nc4_of(a.i32(6))) {
     case 1: return scores_launch<1>(a, s);
     case 2: return scores_launch<2>(a, s);

@@ -146,6 +146,7 @@ SIGNATURES = {
 }
 
 _lib = None
+_LAUNCH = [None]  # gdag_launch, bound once by lib()
 
 
 class GdagError(RuntimeError):
@@ -166,6 +167,7 @@ def lib():
             f = getattr(L, name)
             f.restype = res
             f.argtypes = args
+        _LAUNCH[0] = L.gdag_launch
         _lib = L
     return _lib
 
@@ -412,6 +414,7 @@ class Context:
         self.h = gdag_create(o)
         self._kernels = {}
         self._keep = []
+        self._prepared = {}  # marshalled argument arrays of repeated launches
 
     # lifetime
     def close(self):
@@ -490,10 +493,28 @@ class Context:
         return kid, out
 
     def launch(self, name, *args, grid=None, block=None, smem=0):
-        kid, a = self._args(name, args)
-        g = gdag_dim3(*grid) if grid else gdag_dim3(0, 0, 0)
-        b = gdag_dim3(*block) if block else gdag_dim3(0, 0, 0)
-        return gdag_launch(self.h, kid, g, b, smem, a)
+        # A program issues the same launches step after step: their ctypes
+        # argument arrays are built once and reused (keyed by kernel, launch
+        # shape, array handles, access-mode overrides and typed scalars), so a
+        # repeated launch costs one C call.  The dependency inference, stream
+        # choice and event waits still run on every launch, in the library.
+        key = (name, tuple(grid) if grid else None, tuple(block) if block else None, smem) + tuple(
+            a.handle if a.__class__ is Array else
+            (Mode, a.array.handle, a.mode) if a.__class__ is Mode else (a.__class__, a) for a in args)
+        p = self._prepared.get(key)
+        if p is None:
+            kid, a = self._args(name, args)
+            g = gdag_dim3(*grid) if grid else gdag_dim3(0, 0, 0)
+            b = gdag_dim3(*block) if block else gdag_dim3(0, 0, 0)
+            p = (kid, g, b, smem, (gdag_arg * max(1, len(a)))(*a), len(a), _i64())
+            if len(self._prepared) >= 4096:
+                self._prepared.clear()
+            self._prepared[key] = p
+        kid, g, b, sm, arr, n, node = p
+        r = _LAUNCH[0](self.h, kid, g, b, sm, arr, n, ctypes.byref(node))
+        if r:
+            _check(self.h, r)
+        return node.value
 
     def launch_fused(self, name, members):
         """One DAG element and one persistent launch for several launches of

@@ -33,8 +33,10 @@ def run(rows, feats, classes, seed, inputs=None, scores_only=False):
     return ctx, d, inp
 
 
+# feats a multiple of 64 up to 1024 runs on the tensor cores, the others on
+# CUDA cores
 @pytest.mark.parametrize("rows,feats,classes", [(1, 32, 10), (7, 64, 3), (100, 1024, 10), (1001, 256, 12),
-                                                (333, 96, 1), (64, 32, 16)])
+                                                (333, 96, 1), (64, 32, 16), (129, 1024, 16), (300, 640, 1)])
 def test_scores_bit_exact_with_dyadic_tables(rows, feats, classes):
     ctx, d, (X, T1, b1, T2, b2) = run(rows, feats, classes, seed=rows, scores_only=True)
     s1 = d.S1[:rows].cpu().numpy()
@@ -55,6 +57,39 @@ def test_scores_general_tables_within_tolerance():
     ref = N.scores(X, T, b)
     scale = N.scores_abs(X, T, b)
     assert np.all(np.abs(got - ref) <= TOL * np.maximum(scale, 1.0))
+    ctx.close()
+
+
+def test_scores_out_of_bf16_range_rows_fall_back_exactly():
+    """Feature values beyond +-256 (not exact in bf16) send their 128-row
+    tile to the CUDA-core path: those rows meet the tolerance, every other
+    row stays bit-exact (dyadic tables)."""
+    rows, feats, classes = 1000, 1024, 10
+    X, T1, b1, T2, b2 = datagen.ml_inputs(rows, feats=feats, classes=classes, seed=11)
+    X = X.copy()
+    X[5, 17] = 1000
+    X[300, 3] = -70000
+    X[999, 1023] = 257
+    X[640, 0] = -2147483648
+    ctx, d, _ = run(rows, feats, classes, 0, inputs=(X, T1, b1, T2, b2), scores_only=True)
+    got = d.S1[:rows].cpu().numpy().astype(np.float64)
+    ref = N.scores(X, T1, b1)
+    scale = N.scores_abs(X, T1, b1)
+    assert np.all(np.abs(got - ref) <= TOL * np.maximum(scale, 1.0))
+    clean = np.ones(rows, bool)
+    for r in (5, 300, 999, 640):
+        clean[(r // 128) * 128:(r // 128 + 1) * 128] = False
+    assert np.array_equal(got[clean], ref[clean])
+    ctx.close()
+
+
+def test_scores_full_size_bit_exact():
+    """The benchmark's shape, 100000 x 1024 x 10 (782 tiles over the
+    persistent grid, a 32-row last tile): every score bit-exact."""
+    rows = 100_000
+    ctx, d, (X, T1, b1, T2, b2) = run(rows, 1024, 10, seed=5, scores_only=True)
+    assert np.array_equal(d.S1[:rows].cpu().numpy().astype(np.float64), N.scores(X, T1, b1))
+    assert np.array_equal(d.S2[:rows].cpu().numpy().astype(np.float64), N.scores(X, T2, b2))
     ctx.close()
 
 

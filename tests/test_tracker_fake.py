@@ -335,3 +335,25 @@ def test_node_query_polls_without_blocking():
     assert q.ctx.stats()["active"] == 0
     with pytest.raises(G.GdagError):
         G.gdag_node_query(q.ctx.h, 99)
+
+
+def test_launch_argument_cache_keys_types_and_handles():
+    """Repeated launches reuse their marshalled arguments; an int and a float
+    of equal value are different scalars (different bits), and a handle
+    reused after unregistering resolves to the new array."""
+    ctx = G.Context(backend="fake", record_log=True)
+    a = ctx.array(dev=0x1000, nbytes=400)
+    c = ctx.array(dev=0x2000, nbytes=400)
+    ctx.launch("bs_call", a, c, 100, 60.0, 0.1, 0.2, 1.0)
+    ctx.launch("bs_call", a, c, 100, 60.0, 0.1, 0.2, 1.0)
+    assert len(ctx._prepared) == 1
+    ctx.launch("bs_call", a, c, 100, 60, 0.1, 0.2, 1.0)
+    assert len(ctx._prepared) == 2
+    vals = sorted(p[4][3].value for p in ctx._prepared.values())
+    assert vals[0] == 60 and vals[1] == 0x42700000  # int 60 and float 60.0
+    ctx.sync()
+    ctx.unregister(c)
+    c2 = ctx.array(dev=0x3000, nbytes=40)  # may reuse c's handle
+    with pytest.raises(G.GdagError):  # n = 100 does not fit the new 10-float array
+        ctx.launch("bs_call", a, c2, 100, 60.0, 0.1, 0.2, 1.0)
+    assert len(ctx.nodes()) == 3
