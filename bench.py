@@ -26,6 +26,9 @@ import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
+# one hardware work queue per scheduler stream (see paper_2012_09646_gb300/gdag.py);
+# set before anything creates the CUDA context
+os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
 
 N_OPTS = 10_000_000
 N_VEC = 10
@@ -51,7 +54,7 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--dags", default="all", choices=["all", "bs"],
                     help="also measure the VEC, IMG, ML and HITS DAGs (rank 0)")
-    ap.add_argument("--profile", default=None, choices=["bs", "vec", "img", "ml", "hits", "dl", "hits_batch"],
+    ap.add_argument("--profile", default=None, choices=["bs", "vec", "img", "ml", "hits", "dl", "hits_batch", "bs_fused"],
                     help="run only --steps steps of one DAG through the library (a small, "
                          "single-context command for ncu captures); prints nothing")
     ap.add_argument("--img-size", type=int, default=4096)
@@ -200,6 +203,35 @@ def cpu_oracle_rate(seconds, n_per_vec=1_000_000):
             break
     frac = done * n_per_vec / N_OPTS  # DAGs' worth of work
     return frac / el, done, el
+
+
+def _cpu_oracle_worker(seconds, n_per_vec, seed):
+    """One process of the all-cores baseline: the oracle, as it stands,
+    pricing its own 10 x n_per_vec options repeatedly for `seconds`."""
+    import datagen
+    from oracle import numeric as N
+    prices = datagen.bs_inputs(n_per_vec, count=N_VEC, seed=seed)
+    K, r, s, T = BS_PARAMS
+    N.bs_call(prices[0][:10], K, r, s, T)
+    done, t0 = 0, time.perf_counter()
+    while time.perf_counter() - t0 < seconds:
+        for q in prices:
+            N.bs_call(q, K, r, s, T)
+        done += 1
+    return done * n_per_vec * N_VEC, time.perf_counter() - t0
+
+
+def cpu_oracle_rate_all_cores(seconds, n_per_vec=250_000):
+    """The same oracle on every host core at once: one spawned process per
+    core (the options are independent, so this is the oracle run in
+    parallel, not changed).  Returns (DAG/s, processes, wall seconds)."""
+    import multiprocessing as mp
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
+    with mp.get_context("spawn").Pool(cores) as pool:
+        res = pool.starmap(_cpu_oracle_worker, [(seconds, n_per_vec, 100 + i) for i in range(cores)])
+    options = sum(o for o, _ in res)
+    wall = max(t for _, t in res)
+    return options / (N_OPTS * N_VEC) / wall, cores, wall
 
 
 def run_reference(args, rank):
@@ -882,11 +914,20 @@ def run_ours(args, rank, world, local_rank):
             yg = torch.empty(nnz_h, device=dev)
             ms_g = time_launches(torch, lambda sh: torch.index_select(xg, 0, ig, out=yg), 5)
             del xg, ig, yg
-            pk = dags["HITS"]["per_kernel_solo"]["spmv_csr"]
+            hd = dags["HITS"]
+            pk = hd["per_kernel_solo"]["spmv_csr"]
             per_spmv = pk["solo_ms"] / pk["launches"]
-            dags["HITS"]["gather_bound"] = {
+            # a resource bound that knows the gathers: the SpMVs share one
+            # gather path, so their gather times add up; the other kernels are
+            # bounded by their HBM bytes
+            other_bytes = hd["algorithmic_hbm_bytes"] - pk["alg_bytes"]
+            res_g = max(hd["makespan_ms"]["resource_bound"],
+                        pk["launches"] * ms_g + other_bytes / (hbm * 1e9) * 1e3)
+            hd["gather_bound"] = {
                 "what": "torch.index_select of %d random float32 from a %d-vector (index int64)" % (nnz_h, n_h),
-                "ms": ms_g, "spmv_ms": per_spmv, "spmv_frac_of_gather_bound": ms_g / per_spmv}
+                "ms": ms_g, "spmv_ms": per_spmv, "spmv_frac_of_gather_bound": ms_g / per_spmv,
+                "resource_bound_with_gathers_ms": res_g,
+                "frac_of_resource_bound_with_gathers": res_g / hd["makespan_ms"]["parallel"]}
         if "HITS-batch" in dags:
             hb = data["hits_batch"]
             sep = measure_hits_separate(torch, G, W, hb, max(2, nsteps_other // 4))
@@ -929,10 +970,25 @@ def run_ours(args, rank, world, local_rank):
                                                           for n, (a, b) in t_bs.items()},
                                    "vec_square_group8_ms": {str(n): {"separate": a, "fused": b}
                                                             for n, (a, b) in t_sq.items()}}
+            # the stream pool of the serving context: more streams interleave
+            # more requests (throughput), fewer keep them closer to arrival
+            # order (latency); pick the pool with the lowest p99 at 1000 req/s
+            sweep = {}
+            for ms in (4, 8, 16, 32):
+                srv = SV.Server(inputs, fuse_max=fuse_max, max_streams=ms)
+                srv.warm()
+                reqs = SV.poisson_requests(1000.0, int(1000 * args.serve_seconds), scales, seed=8)
+                srv.run(reqs)
+                srv.close()
+                q = SV.latency_summary(reqs)
+                sweep[ms] = {"p50_ms": q["p50_ms"], "p99_ms": q["p99_ms"], "throughput_req_s": q["throughput_req_s"]}
+            best_ms = min(sweep, key=lambda k: sweep[k]["p99_ms"])
+            serve_out["max_streams_sweep_1000_req_s"] = {str(k): v for k, v in sweep.items()}
+            serve_out["max_streams"] = best_ms
             # the configured rate, two lower ones to locate the knee, and the
             # lowest again without fusion for comparison
             for rate, fm in ((2000.0, fuse_max), (1400.0, fuse_max), (1000.0, fuse_max), (1000.0, None)):
-                srv = SV.Server(inputs, fuse_max=fm)
+                srv = SV.Server(inputs, fuse_max=fm, max_streams=best_ms)
                 srv.warm()
                 f0 = srv.ctx.stats()["fused_members"]
                 reqs = SV.poisson_requests(rate, int(rate * args.serve_seconds), scales, seed=7)
@@ -981,8 +1037,10 @@ def run_ours(args, rank, world, local_rank):
         ctx3.close()
         clocks.__exit__(None, None, None)
 
-        # ---- CPU oracle baseline (bounded sample)
+        # ---- CPU oracle baseline (bounded samples): one thread in program
+        # order, then every host core at once
         cpu_val, cpu_samples, cpu_s = cpu_oracle_rate(args.cpu_seconds)
+        cpu_all, cpu_cores, cpu_all_s = cpu_oracle_rate_all_cores(max(1.0, args.cpu_seconds / 2))
 
         value = RP.job_value(world, 1, ms_all)  # one DAG per rank per step
         gpu_launches = args.steps * N_VEC
@@ -1014,6 +1072,10 @@ def run_ours(args, rank, world, local_rank):
             "cpu_baseline": {"value": cpu_val, "unit": UNIT, "cores": 1, "kind": "oracle",
                              "sample": "%d samples of 10 x 1e6 options (fp64 C oracle, one thread) in %.1f s; "
                                        "scaled to whole DAGs" % (cpu_samples, cpu_s)},
+            "cpu_baseline_all_cores": {"value": cpu_all, "unit": UNIT, "cores": cpu_cores, "kind": "oracle",
+                                       "sample": "%d processes, each pricing 10 x 2.5e5 options repeatedly with the "
+                                                 "fp64 C oracle for %.1f s; scaled to whole DAGs"
+                                                 % (cpu_cores, cpu_all_s)},
             "gpu_launches": gpu_launches,
             "clocks": dict(clocks.summary(), window="warm-up through the last GPU measurement"),
         }
@@ -1042,6 +1104,17 @@ def run_profile(args):
         d = W.BsDag(ctx, N_OPTS, count=N_VEC, host=False)
         d.load_device(datagen.bs_inputs(N_OPTS, count=N_VEC, seed=1))
         step = d.step_resident
+    elif args.profile == "bs_fused":
+        # a serving burst: eight B&S requests of 1/4 scale (10 nodes of
+        # 2.5e6 options each) as one fused element of 80 members
+        n = N_OPTS // 4
+        reqs = [W.BsDag(ctx, n, count=N_VEC, host=False) for _ in range(8)]
+        prices = datagen.bs_inputs(n, count=N_VEC, seed=1)
+        for d in reqs:
+            d.load_device(prices)
+        K, r, sg, T = BS_PARAMS
+        members = [(Sa, Ca, n, K, r, sg, T) for d in reqs for Sa, Ca in zip(d.SA, d.CA)]
+        step = lambda: ctx.launch_fused("bs_call", members)
     elif args.profile == "vec":
         d = W.VecDag(ctx, 1_000_000)
         d.load(*datagen.vec_inputs(1_000_000, seed=0))

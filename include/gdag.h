@@ -201,6 +201,12 @@ void gdag_options_default(gdag_options *o);
  * of a freshly allocated scratch array) is ordered before it.  Errors:
  * INVALID, CUDA, OOM. */
 int gdag_create(gdag_ctx **out, const gdag_options *opts);
+/* Concurrency note: CUDA maps streams onto CUDA_DEVICE_MAX_CONNECTIONS
+ * hardware work queues (8 unless the environment sets it).  Streams that
+ * share a queue are serialised behind each other's cross-stream waits when
+ * the host issues far ahead of the device, so a process using more than 8
+ * pool streams should set CUDA_DEVICE_MAX_CONNECTIONS=32 before it creates
+ * its CUDA context (the Python binding does so at import). */
 
 /* Wait for all work (bounded by timeout_ms), then free every library-owned
  * stream, event and pinned buffer.  Caller-owned memory is not touched. */

@@ -162,16 +162,19 @@ __global__ void __launch_bounds__(kBsThreads, 4) bs_call_kernel(const float *__r
 constexpr int64_t kBsChunk4 = (int64_t)kBsThreads * kBsUnroll;
 constexpr int64_t kBsChunk = kBsChunk4 * 4;
 
-struct BsFused {
+// CAP members at most: the table is a kernel parameter, so a small group
+// launches with a small parameter block (32 members: 1.5 KB; 128: 6 KB)
+template <int CAP> struct BsFused {
     int count;
-    int64_t start[kFuseTable + 1];
-    const float *S[kFuseTable];
-    float *C[kFuseTable];
-    int64_t n[kFuseTable];
-    BsConst c[kFuseTable];
+    int64_t start[CAP + 1];
+    const float *S[CAP];
+    float *C[CAP];
+    int64_t n[CAP];
+    BsConst c[CAP];
 };
 
-__global__ void __launch_bounds__(kBsThreads, 4) bs_call_fused_kernel(const __grid_constant__ BsFused t)
+template <int CAP>
+__global__ void __launch_bounds__(kBsThreads, 4) bs_call_fused_kernel(const __grid_constant__ BsFused<CAP> t)
 {
     const int64_t total = t.start[t.count];
     const int64_t per = (total + gridDim.x - 1) / gridDim.x;
@@ -250,11 +253,11 @@ int launch_bs(const LaunchArgs &a, void *s)
     return cudaGetLastError();
 }
 
-int fused_bs(const LaunchArgs *a, int count, void *s)
+template <int CAP> int fused_bs_cap(const LaunchArgs *a, int count, void *s)
 {
-    for (int off = 0; off < count; off += kFuseTable) {
-        BsFused t;
-        t.count = count - off < kFuseTable ? count - off : kFuseTable;
+    for (int off = 0; off < count; off += CAP) {
+        BsFused<CAP> t;
+        t.count = count - off < CAP ? count - off : CAP;
         t.start[0] = 0;
         for (int m = 0; m < t.count; ++m) {
             const LaunchArgs &la = a[off + m];
@@ -267,12 +270,17 @@ int fused_bs(const LaunchArgs *a, int count, void *s)
         const int64_t total = t.start[t.count];
         if (total == 0) continue;
         static int per_sm = 0;
-        const unsigned g = fused_grid((const void *)bs_call_fused_kernel, kBsThreads, total, per_sm);
-        bs_call_fused_kernel<<<g, kBsThreads, 0, (cudaStream_t)s>>>(t);
+        const unsigned g = fused_grid((const void *)bs_call_fused_kernel<CAP>, kBsThreads, total, per_sm);
+        bs_call_fused_kernel<CAP><<<g, kBsThreads, 0, (cudaStream_t)s>>>(t);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
+}
+
+int fused_bs(const LaunchArgs *a, int count, void *s)
+{
+    return count <= kFuseSmall ? fused_bs_cap<kFuseSmall>(a, count, s) : fused_bs_cap<kFuseTable>(a, count, s);
 }
 
 }  // namespace

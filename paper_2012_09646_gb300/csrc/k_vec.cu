@@ -58,14 +58,15 @@ __global__ void __launch_bounds__(1024) vec_square_kernel(float *__restrict__ x,
 // tiles of all members.
 constexpr int64_t kFuseElems = (int64_t)kThreads * kUnroll * 4;
 
-struct SquareFused {
+template <int CAP> struct SquareFused {
     int count;
-    int64_t start[kFuseTable + 1];
-    float *x[kFuseTable];
-    int64_t n[kFuseTable];
+    int64_t start[CAP + 1];
+    float *x[CAP];
+    int64_t n[CAP];
 };
 
-__global__ void __launch_bounds__(kThreads) vec_square_fused_kernel(const __grid_constant__ SquareFused t)
+template <int CAP>
+__global__ void __launch_bounds__(kThreads) vec_square_fused_kernel(const __grid_constant__ SquareFused<CAP> t)
 {
     // one contiguous range of tiles per block; one member search per block
     const int64_t total = t.start[t.count];
@@ -172,17 +173,18 @@ __global__ void __launch_bounds__(kThreads) vec_reduce_diff_kernel(const float *
 // is bit-identical to the plain launch's; a persistent grid walks them all.
 // No block waits for another (the last arrival of a member combines), so
 // any physical grid size is safe.
-struct ReduceDiffFused {
+template <int CAP> struct ReduceDiffFused {
     int count;
-    int64_t start[kFuseTable + 1];
-    const float *x[kFuseTable];
-    const float *y[kFuseTable];
-    float *z[kFuseTable];
-    double *scratch[kFuseTable];
-    int64_t n[kFuseTable];
+    int64_t start[CAP + 1];
+    const float *x[CAP];
+    const float *y[CAP];
+    float *z[CAP];
+    double *scratch[CAP];
+    int64_t n[CAP];
 };
 
-__global__ void __launch_bounds__(kThreads) vec_reduce_diff_fused_kernel(const __grid_constant__ ReduceDiffFused t)
+template <int CAP>
+__global__ void __launch_bounds__(kThreads) vec_reduce_diff_fused_kernel(const __grid_constant__ ReduceDiffFused<CAP> t)
 {
     __shared__ double sh[kThreads / 32];
     // one contiguous range of virtual blocks per block; one member search
@@ -244,11 +246,11 @@ int launch_reduce_diff(const LaunchArgs &a, void *s)
     return cudaGetLastError();
 }
 
-int fused_square(const LaunchArgs *a, int count, void *s)
+template <int CAP> int fused_square_cap(const LaunchArgs *a, int count, void *s)
 {
-    for (int off = 0; off < count; off += kFuseTable) {
-        SquareFused t;
-        t.count = count - off < kFuseTable ? count - off : kFuseTable;
+    for (int off = 0; off < count; off += CAP) {
+        SquareFused<CAP> t;
+        t.count = count - off < CAP ? count - off : CAP;
         t.start[0] = 0;
         for (int m = 0; m < t.count; ++m) {
             const LaunchArgs &la = a[off + m];
@@ -259,19 +261,24 @@ int fused_square(const LaunchArgs *a, int count, void *s)
         const int64_t total = t.start[t.count];
         if (total == 0) continue;
         static int per_sm = 0;
-        const unsigned g = fused_grid((const void *)vec_square_fused_kernel, kThreads, total, per_sm);
-        vec_square_fused_kernel<<<g, kThreads, 0, (cudaStream_t)s>>>(t);
+        const unsigned g = fused_grid((const void *)vec_square_fused_kernel<CAP>, kThreads, total, per_sm);
+        vec_square_fused_kernel<CAP><<<g, kThreads, 0, (cudaStream_t)s>>>(t);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
 }
 
-int fused_reduce_diff(const LaunchArgs *a, int count, void *s)
+int fused_square(const LaunchArgs *a, int count, void *s)
 {
-    for (int off = 0; off < count; off += kFuseTable) {
-        ReduceDiffFused t;
-        t.count = count - off < kFuseTable ? count - off : kFuseTable;
+    return count <= kFuseSmall ? fused_square_cap<kFuseSmall>(a, count, s) : fused_square_cap<kFuseTable>(a, count, s);
+}
+
+template <int CAP> int fused_reduce_diff_cap(const LaunchArgs *a, int count, void *s)
+{
+    for (int off = 0; off < count; off += CAP) {
+        ReduceDiffFused<CAP> t;
+        t.count = count - off < CAP ? count - off : CAP;
         t.start[0] = 0;
         for (int m = 0; m < t.count; ++m) {
             const LaunchArgs &la = a[off + m];
@@ -284,12 +291,18 @@ int fused_reduce_diff(const LaunchArgs *a, int count, void *s)
         }
         const int64_t total = t.start[t.count];
         static int per_sm = 0;
-        const unsigned g = fused_grid((const void *)vec_reduce_diff_fused_kernel, kThreads, total, per_sm);
-        vec_reduce_diff_fused_kernel<<<g, kThreads, 0, (cudaStream_t)s>>>(t);
+        const unsigned g = fused_grid((const void *)vec_reduce_diff_fused_kernel<CAP>, kThreads, total, per_sm);
+        vec_reduce_diff_fused_kernel<CAP><<<g, kThreads, 0, (cudaStream_t)s>>>(t);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
+}
+
+int fused_reduce_diff(const LaunchArgs *a, int count, void *s)
+{
+    return count <= kFuseSmall ? fused_reduce_diff_cap<kFuseSmall>(a, count, s)
+                               : fused_reduce_diff_cap<kFuseTable>(a, count, s);
 }
 
 }  // namespace

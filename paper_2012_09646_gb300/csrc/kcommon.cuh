@@ -24,8 +24,10 @@ inline int sm_count()
 
 inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
-// Members per fused launch (the kernel-parameter table's capacity).
+// Members per fused launch (the kernel-parameter table's capacity), and the
+// smaller table used for groups that fit it (a smaller parameter block).
 constexpr int kFuseTable = GDAG_FUSED_TABLE;
+constexpr int kFuseSmall = 32;
 
 // Persistent grid for a fused launch of `threads`-thread blocks: resident
 // blocks of kernel `fn` per SM (queried once, into `per_sm`) x SMs, at most

@@ -12,6 +12,16 @@ import ctypes
 import os
 import struct
 
+# The scheduler runs independent nodes on up to max_streams (default 16)
+# streams.  CUDA maps streams onto CUDA_DEVICE_MAX_CONNECTIONS hardware work
+# queues, 8 unless set: streams sharing a queue are serialised behind each
+# other's cross-stream waits once the host issues ahead of the device, which
+# turns a multi-stream DAG back into a partly serial one.  32 (the maximum)
+# gives every pool stream its own queue; it must be set before the process
+# creates its CUDA context, so it is set here, at import, unless the caller
+# chose a value.
+os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
+
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libgdag.so")
 
@@ -370,6 +380,21 @@ def scalar_arg(value, size):
     return gdag_arg(GDAG_ARG_SCALAR, 0, 0, size, bits)
 
 
+_F32 = struct.Struct("<f")
+_U32 = struct.Struct("<I")
+_F64 = struct.Struct("<d")
+_U64 = struct.Struct("<Q")
+_ARG = struct.Struct("<iiiiQ")  # gdag_arg: kind, mode, array, size, value
+assert _ARG.size == ctypes.sizeof(gdag_arg)
+
+
+def _scalar_bits(value, size):
+    """The value field of a scalar argument (as scalar_arg builds it)."""
+    if isinstance(value, float):
+        return _U32.unpack(_F32.pack(value))[0] if size == 4 else _U64.unpack(_F64.pack(value))[0]
+    return int(value) & ((1 << (8 * size)) - 1)
+
+
 class Array:
     """A registered array: a handle plus what it was registered with."""
 
@@ -415,6 +440,7 @@ class Context:
         self._kernels = {}
         self._keep = []
         self._prepared = {}  # marshalled argument arrays of repeated launches
+        self._packed = {}    # packed argument bytes of repeated fused-launch members
 
     # lifetime
     def close(self):
@@ -477,6 +503,41 @@ class Context:
             self._kernels[name] = k
         return k
 
+    def _pack(self, name, args, out):
+        """Append the gdag_arg bytes of one launch of `name` to the bytearray
+        `out` (the same values _args builds, one struct.pack per argument
+        instead of one ctypes structure); returns the kernel handle.  The
+        bytes of a member seen before (same kernel, handles, modes and typed
+        scalars) come from a cache."""
+        key = (name,) + tuple(
+            a.handle if a.__class__ is Array else
+            (Mode, a.array.handle, a.mode) if a.__class__ is Mode else (a.__class__, a) for a in args)
+        hit = self._packed.get(key)
+        if hit is not None:
+            out += hit[1]
+            return hit[0]
+        start = len(out)
+        kid = self._pack_new(name, args, out)
+        if len(self._packed) >= 4096:
+            self._packed.clear()
+        self._packed[key] = (kid, bytes(out[start:]))
+        return kid
+
+    def _pack_new(self, name, args, out):
+        kid, spec = self.kernel(name)
+        if len(args) != len(spec):
+            raise GdagError(GDAG_ERR_INVALID, "%s takes %d arguments, got %d" % (name, len(spec), len(args)))
+        pack = _ARG.pack
+        for sp, v in zip(spec, args):
+            if sp.kind == GDAG_ARG_ARRAY:
+                if v.__class__ is Mode:
+                    out += pack(GDAG_ARG_ARRAY, v.mode, v.array.handle, 0, 0)
+                else:
+                    out += pack(GDAG_ARG_ARRAY, GDAG_MODE_SIGNATURE, v.handle, 0, 0)
+            else:
+                out += pack(GDAG_ARG_SCALAR, 0, 0, sp.size, _scalar_bits(v, sp.size))
+        return kid
+
     def _args(self, name, args):
         kid, spec = self.kernel(name)
         if len(args) != len(spec):
@@ -503,10 +564,13 @@ class Context:
             (Mode, a.array.handle, a.mode) if a.__class__ is Mode else (a.__class__, a) for a in args)
         p = self._prepared.get(key)
         if p is None:
-            kid, a = self._args(name, args)
+            buf = bytearray()
+            kid = self._pack(name, args, buf)
+            n = len(args)
             g = gdag_dim3(*grid) if grid else gdag_dim3(0, 0, 0)
             b = gdag_dim3(*block) if block else gdag_dim3(0, 0, 0)
-            p = (kid, g, b, smem, (gdag_arg * max(1, len(a)))(*a), len(a), _i64())
+            arr = (gdag_arg * max(1, n)).from_buffer_copy(buf) if n else (gdag_arg * 1)()
+            p = (kid, g, b, smem, arr, n, _i64())
             if len(self._prepared) >= 4096:
                 self._prepared.clear()
             self._prepared[key] = p
@@ -520,14 +584,17 @@ class Context:
         """One DAG element and one persistent launch for several launches of
         built-in kernel `name`; `members` is a list of argument tuples, each
         as `launch` would take it."""
-        flat = []
+        if not members:
+            raise GdagError(GDAG_ERR_INVALID, "fused launch of no members")
+        buf = bytearray()
         kid = None
         for m in members:
-            kid, a = self._args(name, m)
-            flat.extend(a)
-        if kid is None:
-            raise GdagError(GDAG_ERR_INVALID, "fused launch of no members")
-        return gdag_launch_fused(self.h, kid, flat, len(flat) // len(members), len(members))
+            kid = self._pack(name, m, buf)
+        nargs = len(members[0])
+        arr = (gdag_arg * (len(buf) // _ARG.size)).from_buffer_copy(buf)
+        node = _i64()
+        _check(self.h, lib().gdag_launch_fused(self.h, kid, arr, nargs, len(members), ctypes.byref(node)))
+        return node.value
 
     def launch_raw(self, name, *args, stream, grid=None, block=None, smem=0):
         kid, a = self._args(name, args)
