@@ -789,6 +789,21 @@ def measure_dag(torch, G, spec, steps, peak_gbs, link):
     lctx.close()
     ctx.close()
     kern = sum(1 for e in elems[first:] if e[0] == "k")
+    # copy/compute overlap of one traced step (Section IV-F): CT, TC, CC, TOT
+    from paper_2012_09646_gb300 import analysis
+    tctx = G.Context(trace=True)
+    tobj = spec.build(tctx)
+    tctx.sync()
+    t_first = G.gdag_stats_get(tctx.h).nodes
+    spec.step(tobj)
+    tctx.sync()
+    tr = [t for t in tctx.trace() if t[0] >= t_first]
+    comp = [(t[3], t[4]) for t in tr if t[1] in (G.GDAG_NODE_KERNEL, G.GDAG_NODE_GRAPH, G.GDAG_NODE_EXTERNAL)]
+    tran = [(t[3], t[4]) for t in tr if t[1] in (G.GDAG_NODE_HOST_WRITE, G.GDAG_NODE_HOST_READ,
+                                                  G.GDAG_NODE_HOST_PREFETCH) and t[4] > t[3]]
+    overlap = analysis.overlap_metrics(comp, tran)
+    tctx.close()
+    del tobj
     return {
         "makespan_ms": out, "nodes": len(elems) - first, "kernels": kern, "streams": streams_used,
         "algorithmic_hbm_bytes": hbm, "h2d_bytes": h2d, "d2h_bytes": d2h,
@@ -798,7 +813,7 @@ def measure_dag(torch, G, spec, steps, peak_gbs, link):
         "library_graph_vs_hand_cuda_graph": out["hand_cuda_graph"] / out["library_graph"],
         "frac_of_cp_bound": cp / out["parallel"], "frac_of_resource_bound": res / out["parallel"],
         "launches_per_step": kern, "per_kernel_solo": per_kernel,
-        "makespan_single_run_ms": single,
+        "makespan_single_run_ms": single, "overlap": overlap,
     }
 
 

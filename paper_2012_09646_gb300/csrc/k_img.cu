@@ -207,6 +207,18 @@ __global__ void __launch_bounds__(kImgThreads) gauss_blur_kernel(const float *__
     asm volatile("cp.async.wait_group 0;" ::: "memory");
 }
 
+// sqrt(gx^2 + gy^2) with the single-instruction approximate square root
+// (relative error about 1e-7, far inside the 1e-5 tolerance; the outputs
+// that are compared bit for bit downstream are min/max of these values
+// themselves); exactly 0 for a flat neighbourhood.
+__device__ __forceinline__ float sobel_mag(float gx, float gy)
+{
+    const float g2 = fmaf(gx, gx, gy * gy);
+    float r;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(g2));
+    return g2 > 0.f ? r : 0.f;
+}
+
 // Sobel magnitude: gx = right column - left column with weights (1, 2, 1),
 // gy = bottom row - top row with weights (1, 2, 1); out = sqrt(gx^2 + gy^2).
 // Each thread makes a 4-column x 2-row block from a 6 x 4 window.
@@ -241,7 +253,7 @@ __global__ void __launch_bounds__(kImgThreads) sobel_kernel(const float *__restr
             const float gg = m[h + 2][c - 1], hh = m[h + 2][c], i = m[h + 2][c + 1];
             const float gx = (cc + 2.f * f + i) - (a + 2.f * d + gg);
             const float gy = (gg + 2.f * hh + i) - (a + 2.f * b + cc);
-            o[h][j] = sqrtf(gx * gx + gy * gy);
+            o[h][j] = sobel_mag(gx, gy);
         }
     store_2x4(out, rows, cols, x0 + 4 * g, y0 + 2 * rp, make_float4(o[0][0], o[0][1], o[0][2], o[0][3]),
               make_float4(o[1][0], o[1][1], o[1][2], o[1][3]));

@@ -20,6 +20,8 @@
 #include <chrono>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdint>
+#include <cstdlib>
 #include <cstring>
 #include <deque>
 #include <memory>
@@ -592,6 +594,22 @@ void gdag_options_default(gdag_options *o)
     o->fake_complete = 0;
     o->fake_fail_sticky = 0;
     o->fake_fail_op = -1;
+    // environment overrides of the defaults (an unset or unparsable value
+    // keeps the default)
+    struct {
+        const char *name;
+        int32_t *field;
+    } env[] = {{"GDAG_POLICY", &o->policy},           {"GDAG_MAX_STREAMS", &o->max_streams},
+               {"GDAG_PREFETCH", &o->prefetch},       {"GDAG_RETIRE_BY_QUERY", &o->retire_by_query},
+               {"GDAG_RECORD_LOG", &o->record_log},   {"GDAG_TRACE", &o->trace},
+               {"GDAG_TIMEOUT_MS", &o->timeout_ms}, {"GDAG_DEVICE", &o->device}};
+    for (const auto &e : env) {
+        const char *v = std::getenv(e.name);
+        if (!v || !*v) continue;
+        char *end = nullptr;
+        const long x = std::strtol(v, &end, 10);
+        if (end && *end == '\0' && x >= INT32_MIN && x <= INT32_MAX) *e.field = (int32_t)x;
+    }
 }
 
 int gdag_create(gdag_ctx **out, const gdag_options *opts)

@@ -652,6 +652,27 @@ class Context:
     def trace(self):
         return [(t.node, t.kind, t.stream, t.start_ms, t.end_ms) for t in gdag_trace_export(self.h)]
 
+    def chrome_trace(self, path, names=None):
+        """Write the timed nodes of a traced context (options.trace = 1) as a
+        Chrome trace (JSON for chrome://tracing or Perfetto): one track per
+        pool stream, one complete event per node, microseconds from context
+        creation.  ``names``: optional {node id: label} (e.g. kernel names);
+        other nodes are labelled by kind.  Returns the number of events."""
+        import json
+        kinds = {GDAG_NODE_KERNEL: "kernel", GDAG_NODE_HOST_WRITE: "h2d", GDAG_NODE_HOST_READ: "read",
+                 GDAG_NODE_EXTERNAL: "external", GDAG_NODE_HOST_PREFETCH: "d2h", GDAG_NODE_GRAPH: "graph"}
+        names = names or {}
+        ev = []
+        for node, kind, stream, t0, t1 in self.trace():
+            cat = kinds.get(kind, "node")
+            ev.append({"name": names.get(node, "%s %d" % (cat, node)), "cat": cat, "ph": "X",
+                       "ts": t0 * 1e3, "dur": max(0.0, t1 - t0) * 1e3, "pid": 0,
+                       "tid": "stream %d" % stream if stream >= 0 else "host",
+                       "args": {"node": node}})
+        with open(path, "w") as f:
+            json.dump({"traceEvents": ev, "displayTimeUnit": "ms"}, f)
+        return len(ev)
+
     def stats(self):
         s = gdag_stats_get(self.h)
         return {f: getattr(s, f) for f, _ in gdag_stats._fields_}

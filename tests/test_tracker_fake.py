@@ -357,3 +357,28 @@ def test_launch_argument_cache_keys_types_and_handles():
     with pytest.raises(G.GdagError):  # n = 100 does not fit the new 10-float array
         ctx.launch("bs_call", a, c2, 100, 60.0, 0.1, 0.2, 1.0)
     assert len(ctx.nodes()) == 3
+
+
+def test_chrome_trace_export(tmp_path):
+    import json
+    p = Program(3, trace=True, fake_complete=True)
+    k0 = p.kernel({0: D.W})
+    p.kernel({1: D.W})
+    p.kernel({0: D.R, 1: D.R, 2: D.W})
+    p.write(0)
+    p.ctx.sync()
+    out = tmp_path / "trace.json"
+    n = p.ctx.chrome_trace(str(out), names={k0: "producer"})
+    doc = json.load(open(out))
+    assert n == len(doc["traceEvents"]) == 4
+    assert {e["cat"] for e in doc["traceEvents"]} == {"kernel", "h2d"}
+    assert doc["traceEvents"][0]["name"] == "producer"
+    assert all(e["ph"] == "X" and e["dur"] >= 0 for e in doc["traceEvents"])
+
+
+def test_option_environment_overrides(monkeypatch):
+    monkeypatch.setenv("GDAG_MAX_STREAMS", "5")
+    monkeypatch.setenv("GDAG_TIMEOUT_MS", "1234")
+    monkeypatch.setenv("GDAG_PREFETCH", "not a number")
+    o = G.gdag_options_default()
+    assert o.max_streams == 5 and o.timeout_ms == 1234 and o.prefetch == 1
