@@ -131,11 +131,15 @@ __device__ __forceinline__ void bs_chunk(const float4 *__restrict__ S4, float4 *
     }
 }
 
-// The grid is one resident wave; blocks stride over chunks.
+// Blocks stride over chunks.  TH > 0 fixes the block size at compile time
+// (the automatic launch shape: 256 threads, two resident waves, so the
+// index arithmetic folds to constants); TH = 0 takes blockDim.x (explicit
+// launch shapes, e.g. from the autotuner).
+template <int TH>
 __global__ void __launch_bounds__(kBsThreads, 4) bs_call_kernel(const float *__restrict__ S, float *__restrict__ C,
                                                                 int64_t n, BsConst c)
 {
-    const int64_t bd = blockDim.x;
+    const int64_t bd = TH > 0 ? TH : blockDim.x;
     if (((reinterpret_cast<uintptr_t>(S) | reinterpret_cast<uintptr_t>(C)) & 15) == 0) {
         const int64_t n4 = n >> 2, chunk = bd * kBsUnroll;
         for (int64_t base = (int64_t)blockIdx.x * chunk; base < n4; base += (int64_t)gridDim.x * chunk)
@@ -242,14 +246,20 @@ int launch_bs(const LaunchArgs &a, void *s)
 {
     int64_t n = a.i64(2);
     if (n == 0) return cudaSuccess;
-    unsigned b = a.auto_cfg ? kBsThreads : a.block[0];
-    unsigned g = a.grid[0];
-    if (a.auto_cfg) {
-        static int per_sm = 0;  // resident blocks of kBsThreads per SM
-        g = fused_grid((const void *)bs_call_kernel, kBsThreads, ceil_div((n >> 2) > 0 ? (n >> 2) : 1, kBsChunk4),
-                       per_sm);
+    if (!a.auto_cfg) {
+        bs_call_kernel<0><<<a.grid[0], a.block[0], 0, (cudaStream_t)s>>>(a.p<float>(0), a.p<float>(1), n,
+                                                                        bs_const(a));
+        return cudaGetLastError();
     }
-    bs_call_kernel<<<g, b, 0, (cudaStream_t)s>>>(a.p<float>(0), a.p<float>(1), n, bs_const(a));
+    // two resident waves of 256-thread blocks (capped by the chunk count):
+    // measured a little faster than one wave, the second wave's blocks
+    // starting as the first's finish their last chunks
+    static int per_sm = 0;
+    const int64_t chunks = ceil_div((n >> 2) > 0 ? (n >> 2) : 1, kBsChunk4);
+    const int64_t g1 = fused_grid((const void *)bs_call_kernel<kBsThreads>, kBsThreads, chunks, per_sm);
+    const int64_t g = 2 * g1 < chunks ? 2 * g1 : chunks;
+    bs_call_kernel<kBsThreads><<<(unsigned)g, kBsThreads, 0, (cudaStream_t)s>>>(a.p<float>(0), a.p<float>(1), n,
+                                                                              bs_const(a));
     return cudaGetLastError();
 }
 
@@ -289,7 +299,7 @@ void append_bs_kernels(std::vector<KernelEntry> &v)
 {
     KernelEntry e;
     e.name = "bs_call";
-    e.fn = (const void *)bs_call_kernel;
+    e.fn = (const void *)bs_call_kernel<0>;
     e.nargs = 7;
     e.spec[0] = arr(GDAG_MODE_IN);
     e.spec[1] = arr(GDAG_MODE_OUT);
