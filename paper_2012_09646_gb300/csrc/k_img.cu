@@ -175,15 +175,29 @@ __global__ void __launch_bounds__(kImgThreads) gauss_blur_kernel(const float *__
                 v[4 * k + 2] = p.z;
                 v[4 * k + 3] = p.w;
             }
-            float2 lo = make_float2(0.f, 0.f), hi = lo;  // outputs (0,1) and (2,3)
+            // outputs (0,1) and (2,3) take the taps whose input offset o is
+            // even: their operand pairs (v[o], v[o+1]) sit in aligned
+            // register pairs.  For odd o the aligned pair is (v[o+1],
+            // v[o+2]), which feeds outputs (1,2); outputs 0 and 3 take that
+            // tap with scalar FMAs.  (Building misaligned pairs would cost two
+            // register moves per pair.)  The parities are compile-time.
+            float2 lo = make_float2(0.f, 0.f), hi = lo, mid = lo;
+            float e0 = 0.f, e3 = 0.f;
 #pragma unroll
             for (int k = 0; k <= 2 * R; ++k) {
-                const float2 wk = make_float2(wr[k], wr[k]);
                 const int o = HALO - R + k;
-                lo = __ffma2_rn(wk, make_float2(v[o], v[o + 1]), lo);
-                hi = __ffma2_rn(wk, make_float2(v[o + 2], v[o + 3]), hi);
+                if ((o & 1) == 0) {
+                    const float2 wk = make_float2(wr[k], wr[k]);
+                    lo = __ffma2_rn(wk, make_float2(v[o], v[o + 1]), lo);
+                    hi = __ffma2_rn(wk, make_float2(v[o + 2], v[o + 3]), hi);
+                } else {
+                    mid = __ffma2_rn(make_float2(wr[k], wr[k]), make_float2(v[o + 1], v[o + 2]), mid);
+                    e0 = fmaf(wr[k], v[o], e0);
+                    e3 = fmaf(wr[k], v[o + 3], e3);
+                }
             }
-            reinterpret_cast<float4 *>(s_h + r * kTileW)[g] = make_float4(lo.x, lo.y, hi.x, hi.y);
+            reinterpret_cast<float4 *>(s_h + r * kTileW)[g] =
+                make_float4(lo.x + e0, lo.y + mid.x, hi.x + mid.y, hi.y + e3);
         }
         __syncthreads();
         // vertical: 16 column groups x 16 row pairs, one block per thread
