@@ -105,7 +105,8 @@ typedef struct {
     int32_t record_log;      /* 1: keep element, edge and op logs for the
                                 export calls; default 0                      */
     int32_t trace;           /* 1: timing events around every node for
-                                gdag_trace_export; default 0                 */
+                                gdag_trace_export, and an NVTX range around
+                                each element's host-side issue; default 0    */
     int32_t timeout_ms;      /* host-wait deadline; default 60000            */
     int32_t fake_complete;   /* FAKE backend: 1 = an event reports complete
                                 when queried; 0 = only after a host wait;

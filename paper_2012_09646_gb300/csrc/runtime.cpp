@@ -29,6 +29,8 @@
 #include <thread>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "backend.h"
 #include "catalog.h"
 #include "gdag.h"
@@ -558,6 +560,21 @@ struct Ctx {
 
 }  // namespace gdag
 
+// With options.trace set, an NVTX range marks the host-side issue of each
+// element (named after its kernel or its kind), so a system profiler shows
+// the library's issue timeline next to the device work.
+struct IssueRange {
+    bool on;
+    IssueRange(const gdag::Ctx *c, const char *name) : on(c && c->opt.trace)
+    {
+        if (on) nvtxRangePushA(name);
+    }
+    ~IssueRange()
+    {
+        if (on) nvtxRangePop();
+    }
+};
+
 using gdag::Access;
 using gdag::ArrayState;
 using gdag::Ctx;
@@ -831,6 +848,7 @@ int gdag_launch(gdag_ctx *c, gdag_kernel k, gdag_dim3 grid, gdag_dim3 block, siz
     if (!c) return GDAG_ERR_INVALID;
     int r = c->guard();
     if (r) return r;
+    IssueRange nvtx(c, (k >= 0 && (size_t)k < c->kernels.size()) ? c->kernels[(size_t)k].name.c_str() : "launch");
     LaunchArgs la;
     Access acc[gdag::kMaxArgs];
     int nacc;
@@ -862,6 +880,7 @@ int gdag_launch_fused(gdag_ctx *c, gdag_kernel k, const gdag_arg *args, int32_t 
     if (!c) return GDAG_ERR_INVALID;
     int r = c->guard();
     if (r) return r;
+    IssueRange nvtx(c, (k >= 0 && (size_t)k < c->kernels.size()) ? c->kernels[(size_t)k].name.c_str() : "fused launch");
     if (k < 0 || (size_t)k >= c->kernels.size()) return c->fail(GDAG_ERR_INVALID, "unknown kernel %d", k);
     const KernelEntry &e = c->kernels[(size_t)k];
     if (!e.fused) return c->fail(GDAG_ERR_INVALID, "%s has no fused form", e.name.c_str());
@@ -945,6 +964,7 @@ int gdag_launch_external(gdag_ctx *c, void (*fn)(void *, void *), void *user, co
     if (!c || !fn || n < 0 || n > gdag::kMaxArgs || (n && (!arrays || !modes))) return GDAG_ERR_INVALID;
     int r = c->guard();
     if (r) return r;
+    IssueRange nvtx(c, "external");
     Access acc[gdag::kMaxArgs];
     int nacc = 0;
     for (int i = 0; i < n; ++i) {
@@ -1004,6 +1024,7 @@ int gdag_array_write(gdag_ctx *c, gdag_array a, const void *src, size_t off, siz
     if (!c) return GDAG_ERR_INVALID;
     int r = c->guard();
     if (r) return r;
+    IssueRange nvtx(c, "host write");
     ArrayState *s = c->arr(a);
     if (!s) return c->fail(GDAG_ERR_INVALID, "unknown array %d", a);
     if (off > s->bytes || bytes > s->bytes - off)
@@ -1048,6 +1069,7 @@ int gdag_array_read(gdag_ctx *c, gdag_array a, void *dst, size_t off, size_t byt
     if (!c) return GDAG_ERR_INVALID;
     int r = c->guard();
     if (r) return r;
+    IssueRange nvtx(c, "host read");
     if (c->capturing) return c->fail(GDAG_ERR_INVALID, "not allowed while capturing");
     ArrayState *s = c->arr(a);
     if (!s) return c->fail(GDAG_ERR_INVALID, "unknown array %d", a);
@@ -1098,6 +1120,7 @@ int gdag_array_prefetch_host(gdag_ctx *c, gdag_array a, size_t off, size_t bytes
     if (!c) return GDAG_ERR_INVALID;
     int r = c->guard();
     if (r) return r;
+    IssueRange nvtx(c, "prefetch to host");
     if (c->capturing) return c->fail(GDAG_ERR_INVALID, "not allowed while capturing");
     ArrayState *s = c->arr(a);
     if (!s) return c->fail(GDAG_ERR_INVALID, "unknown array %d", a);
@@ -1327,6 +1350,7 @@ int gdag_graph_launch(gdag_ctx *c, gdag_graph g, int64_t *node_out)
     if (!c) return GDAG_ERR_INVALID;
     int r = c->guard();
     if (r) return r;
+    IssueRange nvtx(c, "graph replay");
     if (c->capturing) return c->fail(GDAG_ERR_INVALID, "not allowed while capturing");
     if (g < 0 || (size_t)g >= c->graphs.size() || !c->graphs[(size_t)g].live)
         return c->fail(GDAG_ERR_INVALID, "unknown graph %d", g);
