@@ -59,7 +59,7 @@ def parse():
                          "single-context command for ncu captures); prints nothing")
     ap.add_argument("--img-size", type=int, default=4096)
     ap.add_argument("--serve", type=int, default=1, help="run the serving benchmark (with --dags all)")
-    ap.add_argument("--serve-seconds", type=float, default=1.0, help="seconds of Poisson arrivals per rate")
+    ap.add_argument("--serve-seconds", type=float, default=2.0, help="seconds of Poisson arrivals per rate")
     return ap.parse_args()
 
 
@@ -793,6 +793,8 @@ def measure_dag(torch, G, spec, steps, peak_gbs, link):
     from paper_2012_09646_gb300 import analysis
     tctx = G.Context(trace=True)
     tobj = spec.build(tctx)
+    for _ in range(2):  # warm: the traced step is a steady-state one
+        spec.step(tobj)
     tctx.sync()
     t_first = G.gdag_stats_get(tctx.h).nodes
     spec.step(tobj)
