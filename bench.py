@@ -58,6 +58,7 @@ def parse():
                     help="run only --steps steps of one DAG through the library (a small, "
                          "single-context command for ncu captures); prints nothing")
     ap.add_argument("--img-size", type=int, default=4096)
+    ap.add_argument("--vec-n", type=int, default=1_000_000, help="VEC length for --profile vec")
     ap.add_argument("--serve", type=int, default=1, help="run the serving benchmark (with --dags all)")
     ap.add_argument("--serve-seconds", type=float, default=2.0, help="seconds of Poisson arrivals per rate")
     return ap.parse_args()
@@ -1133,8 +1134,8 @@ def run_profile(args):
         members = [(Sa, Ca, n, K, r, sg, T) for d in reqs for Sa, Ca in zip(d.SA, d.CA)]
         step = lambda: ctx.launch_fused("bs_call", members)
     elif args.profile == "vec":
-        d = W.VecDag(ctx, 1_000_000)
-        d.load(*datagen.vec_inputs(1_000_000, seed=0))
+        d = W.VecDag(ctx, args.vec_n)
+        d.load(*datagen.vec_inputs(args.vec_n, seed=0))
         step = d.step
     elif args.profile == "img":
         n = args.img_size

@@ -179,13 +179,30 @@ __global__ void spmv_fixup_kernel(const int2 *__restrict__ part, const float *__
     const int r = part[b + 1].x;
     if (r >= nrows) return;
     if (b > 0 && part[b].x == r) return;  // an earlier tile starts this row's group
+    // A power-law row can span hundreds of tiles: each round trip covers 128
+    // of them (four per lane, row ends and carries loaded together, the
+    // carries speculatively), so a long chain costs a few latencies, not
+    // one per 32 tiles.  The tiles carrying r are a prefix of b, b+1, ...;
+    // each lane sums its tiles in increasing order, then a fixed shuffle
+    // tree combines the lanes: the same sum on every run.
     float sum = 0.f;
-    for (int base = b;; base += 32) {
-        const int bb = base + lane;
-        const bool in = bb < tiles && part[bb + 1].x == r;
-        const unsigned m = __ballot_sync(0xffffffffu, in);
-        if (in) sum += carry[bb];
-        if (m != 0xffffffffu) break;
+    for (int base = b;; base += 128) {
+        int pr[4];
+        float cv[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int bb = base + 32 * k + lane;
+            pr[k] = bb < tiles ? part[bb + 1].x : -1;
+            cv[k] = bb < tiles ? carry[bb] : 0.f;
+        }
+        bool all_in = true;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const bool in = pr[k] == r;
+            if (in) sum += cv[k];
+            all_in = all_in && in;
+        }
+        if (!__all_sync(0xffffffffu, all_in)) break;
     }
     for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
     if (lane == 0) y[r] = sum + y[r];
