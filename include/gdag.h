@@ -291,6 +291,8 @@ int gdag_array_prefetch_host(gdag_ctx *ctx, gdag_array a, size_t off,
  *                         scratch INOUT, n i64)                  z = sum(x-y)
  *  B&S   bs_call         (S IN f32[n], C OUT f32[n], n i64, K f32, r f32,
  *                         sigma f32, T f32)                      call prices
+ *                         K, sigma, T > 0; an explicit launch shape takes
+ *                         blocks of at most 256 threads
  *  IMG   gauss_blur      (img IN f32[rows*cols], out OUT, w IN f32[2R+1],
  *                         rows i32, cols i32, R i32)    separable, clamped
  *        sobel           (in IN, out OUT, rows i32, cols i32)    magnitude
