@@ -55,19 +55,23 @@ class Inputs:
     def __init__(self, datagen, scales, kinds=KINDS, device="cuda", hits_full=(10_000_000, 50_000_000),
                  full=None):
         """``full``: already generated full-scale inputs to reuse for s = 1
-        (keys "bs", "img", "ml", "hits" as the benchmark builds them)."""
+        (keys "bs", "img", "ml", "hits" as the benchmark builds them).
+        ``device="cpu"`` keeps everything in ordinary host memory (for
+        driving the dispatcher on the recording backend, which computes
+        nothing)."""
         self.scales = scales
+        pin = (lambda t: t.pin_memory()) if device != "cpu" else (lambda t: t)
         self.data = {}
         full = full or {}
         for s in scales:
             if s == 1.0 and full:
-                self._from_full(full, kinds, device)
+                self._from_full(full, kinds, device, pin)
                 continue
             if "VEC" in kinds:
                 n = max(1, int(1_000_000 * s))
                 x, y = datagen.vec_inputs(n, seed=10)
-                hx = torch.from_numpy(x).pin_memory()
-                hy = torch.from_numpy(y).pin_memory()
+                hx = pin(torch.from_numpy(x))
+                hy = pin(torch.from_numpy(y))
                 self.data[("VEC", s)] = {"n": n, "hx": hx, "hy": hy}
             if "B&S" in kinds:
                 n = max(4, int(10_000_000 * s))
@@ -91,13 +95,13 @@ class Inputs:
                                           "A": (d(csr[0], i32), d(csr[1], i32), d(csr[2], F32)),
                                           "AT": (d(csc[0], i32), d(csc[1], i32), d(csc[2], F32))}
 
-    def _from_full(self, full, kinds, device):
+    def _from_full(self, full, kinds, device, pin):
         import datagen
         t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(device)
         if "VEC" in kinds:
             x, y = datagen.vec_inputs(1_000_000, seed=10)
-            self.data[("VEC", 1.0)] = {"n": 1_000_000, "hx": torch.from_numpy(x).pin_memory(),
-                                       "hy": torch.from_numpy(y).pin_memory()}
+            self.data[("VEC", 1.0)] = {"n": 1_000_000, "hx": pin(torch.from_numpy(x)),
+                                       "hy": pin(torch.from_numpy(y))}
         if "B&S" in kinds:
             self.data[("B&S", 1.0)] = {"n": full["bs"][0].size, "S": [t(p) for p in full["bs"]]}
         if "IMG+ML" in kinds:
@@ -139,15 +143,19 @@ class Request:
 class Server:
     """One gdag context shared by every request."""
 
-    def __init__(self, inputs, budget_bytes=40 << 30, max_streams=32, device="cuda", fuse_max=None):
+    def __init__(self, inputs, budget_bytes=40 << 30, max_streams=32, device="cuda", fuse_max=None, backend="cuda"):
         """``fuse_max``: {kind: largest node size (elements) that is fused
-        across requests}; None or {} turns fusion off."""
+        across requests}; None or {} turns fusion off.  ``backend="fake"``
+        (with ``device="cpu"``) runs the dispatcher on the recording backend:
+        admission, batching and bookkeeping without a GPU (every node
+        reports complete when queried; nothing is computed)."""
         self.inp = inputs
         self.fuse_max = dict(fuse_max or {})
         self.budget = budget_bytes
         self.used = 0
         self.device = device
-        self.ctx = G.Context(max_streams=max_streams, retire_by_query=True)
+        self.ctx = G.Context(max_streams=max_streams, retire_by_query=True, backend=backend,
+                             fake_complete=backend == "fake")
         self.shared = {}
         self._slots = []  # pinned response buffers, reused
         self._scratch_pool = {}
@@ -183,7 +191,9 @@ class Server:
         return a
 
     def _slot(self):
-        return self._slots.pop() if self._slots else torch.empty(RESPONSE_BYTES // 4, dtype=F32, pin_memory=True)
+        if self._slots:
+            return self._slots.pop()
+        return torch.empty(RESPONSE_BYTES // 4, dtype=F32, pin_memory=self.device != "cpu")
 
     def working_bytes(self, r):
         """Bytes of the private arrays a request will allocate."""

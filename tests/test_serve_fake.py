@@ -1,0 +1,89 @@
+"""The serving dispatcher on the recording backend (CPU only): requests of
+every kind arrive as a Poisson stream or a burst and are all served;
+admission follows arrival order and, under a tiny memory budget, admits one
+request at a time; a burst of small VEC and B&S requests is issued as fused
+groups (3 members per VEC request, 10 per B&S request).  The fake backend
+computes nothing, so this checks the dispatcher's logic, not results (the GPU
+tests check those)."""
+import datagen
+import pytest
+
+from paper_2012_09646_gb300 import serve as SV
+
+SCALES = [1 / 64, 1 / 16]
+HITS_SMALL = (20_000, 100_000)
+
+
+@pytest.fixture(scope="module")
+def inputs():
+    return SV.Inputs(datagen, SCALES, device="cpu", hits_full=HITS_SMALL)
+
+
+def server(inputs, **kw):
+    srv = SV.Server(inputs, device="cpu", backend="fake", **kw)
+    srv.warm()
+    return srv
+
+
+def fresh(reqs):
+    return [SV.Request(r.rid, r.kind, r.scale, r.arrival) for r in reqs]
+
+
+def test_stream_all_served_in_arrival_order(inputs):
+    reqs = SV.poisson_requests(rate=50_000.0, count=40, scales=SCALES, seed=3)
+    srv = server(inputs)
+    out = srv.run(fresh(reqs))
+    assert all(r.done_at is not None and r.done_at >= r.arrival for r in out)
+    adm = [r.admitted for r in out]
+    assert adm == sorted(adm)
+    assert {r.kind for r in out} == set(SV.KINDS)
+    assert srv.used == 0  # every request's memory was released
+    st = srv.ctx.stats()
+    assert st["active"] == 0
+    srv.close()
+
+
+def test_tiny_budget_admits_one_at_a_time(inputs):
+    reqs = SV.poisson_requests(rate=1e6, count=12, scales=SCALES, seed=4)
+    srv = server(inputs, budget_bytes=1)
+    out = srv.run(fresh(reqs))
+    for a, b in zip(out, out[1:]):
+        assert b.admitted >= a.done_at
+    srv.close()
+
+
+def test_burst_issues_fused_groups(inputs):
+    burst = [SV.Request(r.rid, r.kind, r.scale, 0.0)
+             for r in SV.poisson_requests(rate=1.0, count=30, scales=SCALES, seed=5)]
+    nv = sum(r.kind == "VEC" for r in burst)
+    nb = sum(r.kind == "B&S" for r in burst)
+    assert nv >= 2 and nb >= 2
+    srv = server(inputs, fuse_max={"VEC": 1 << 30, "B&S": 1 << 30})
+    f0 = srv.ctx.stats()["fused_members"]
+    out = srv.run(burst)
+    assert all(r.done_at is not None for r in out)
+    assert srv.ctx.stats()["fused_members"] - f0 == 3 * nv + 10 * nb
+    srv.close()
+    # without fusion thresholds nothing is fused
+    srv = server(inputs)
+    f0 = srv.ctx.stats()["fused_members"]
+    srv.run([SV.Request(r.rid, r.kind, r.scale, 0.0) for r in burst])
+    assert srv.ctx.stats()["fused_members"] == f0
+    srv.close()
+
+
+def test_fusion_threshold_excludes_large_nodes(inputs):
+    """Only nodes at most fuse_max elements are fused: a threshold below the
+    smallest bucket fuses nothing."""
+    burst = [SV.Request(i, "B&S", SCALES[i % 2], 0.0) for i in range(6)]
+    small = inputs.data[("B&S", SCALES[0])]["n"]
+    srv = server(inputs, fuse_max={"B&S": small})
+    f0 = srv.ctx.stats()["fused_members"]
+    srv.run(burst)
+    assert srv.ctx.stats()["fused_members"] - f0 == 10 * 3  # the three 1/64 requests
+    srv.close()
+    srv = server(inputs, fuse_max={"B&S": small - 1})
+    f0 = srv.ctx.stats()["fused_members"]
+    srv.run([SV.Request(r.rid, r.kind, r.scale, 0.0) for r in burst])
+    assert srv.ctx.stats()["fused_members"] == f0
+    srv.close()
