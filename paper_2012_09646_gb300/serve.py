@@ -44,11 +44,6 @@ RESPONSE_BYTES = 64 * 1024
 F32 = torch.float32
 
 
-def bucket_scales(levels=7):
-    """Scale buckets 1/64, 1/32, ..., 1: a drawn s is rounded up to one."""
-    return [2.0 ** -k for k in range(levels - 1, -1, -1)]
-
-
 class Inputs:
     """Read-only inputs per (kind, bucket), generated once and resident."""
 
