@@ -168,44 +168,77 @@ __global__ void __launch_bounds__(kSpmvThreads) spmv_merge_kernel(const int *__r
 }
 
 // Rows crossing tiles: tile b carries row part[b+1].x into tile b + 1.  The
-// warp of the first tile carrying a row adds all its carries, in tile order,
-// to the value the finishing tile wrote.
-__global__ void spmv_fixup_kernel(const int2 *__restrict__ part, const float *__restrict__ carry,
-                                  float *__restrict__ y, int nrows, int tiles)
+// first tile carrying a row (its chain head) adds all the chain's carries to
+// the value the finishing tile wrote.  One thread per tile: a head whose
+// chain has at most kFixShort tiles sums it alone, in tile order (almost
+// every chain: a row rarely spans more than a few 896-item tiles).  Longer
+// chains, the power-law rows that span hundreds of tiles, are walked by the
+// head's whole warp, 128 tiles per round trip (four per lane, row ends and
+// carries loaded together), each lane summing its tiles in increasing order
+// and a fixed shuffle tree combining the lanes.  Either way every run gives
+// the same sum.
+constexpr int kFixShort = 4;
+
+__global__ void __launch_bounds__(256) spmv_fixup_kernel(const int2 *__restrict__ part,
+                                                         const float *__restrict__ carry, float *__restrict__ y,
+                                                         int nrows, int tiles)
 {
     const int lane = threadIdx.x & 31;
-    const int b = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (b >= tiles) return;
-    const int r = part[b + 1].x;
-    if (r >= nrows) return;
-    if (b > 0 && part[b].x == r) return;  // an earlier tile starts this row's group
-    // A power-law row can span hundreds of tiles: each round trip covers 128
-    // of them (four per lane, row ends and carries loaded together, the
-    // carries speculatively), so a long chain costs a few latencies, not
-    // one per 32 tiles.  The tiles carrying r are a prefix of b, b+1, ...;
-    // each lane sums its tiles in increasing order, then a fixed shuffle
-    // tree combines the lanes: the same sum on every run.
-    float sum = 0.f;
-    for (int base = b;; base += 128) {
-        int pr[4];
-        float cv[4];
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    int r = -1;
+    bool head = false;
+    if (b < tiles) {
+        r = part[b + 1].x;
+        head = r < nrows && (b == 0 || part[b].x != r);
+    }
+    bool longc = false;
+    if (head) {
+        int pr[kFixShort];
+        float cv[kFixShort];
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const int bb = base + 32 * k + lane;
+        for (int k = 0; k < kFixShort; ++k) {
+            const int bb = b + k;
             pr[k] = bb < tiles ? part[bb + 1].x : -1;
             cv[k] = bb < tiles ? carry[bb] : 0.f;
         }
-        bool all_in = true;
+        float sum = 0.f;
+        bool in = true;
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const bool in = pr[k] == r;
+        for (int k = 0; k < kFixShort; ++k) {
+            in = in && pr[k] == r;
             if (in) sum += cv[k];
-            all_in = all_in && in;
         }
-        if (!__all_sync(0xffffffffu, all_in)) break;
+        longc = in;  // all kFixShort tiles carry r: the chain may go on
+        if (!longc) y[r] = sum + y[r];
     }
-    for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
-    if (lane == 0) y[r] = sum + y[r];
+    // every lane reaches the ballot (no early exit above)
+    unsigned lm = __ballot_sync(0xffffffffu, longc);
+    while (lm) {
+        const int src = __ffs(lm) - 1;
+        lm &= lm - 1;
+        const int hb = __shfl_sync(0xffffffffu, b, src), hr = __shfl_sync(0xffffffffu, r, src);
+        float sum = 0.f;
+        for (int base = hb;; base += 128) {
+            int pr[4];
+            float cv[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const int bb = base + 32 * k + lane;
+                pr[k] = bb < tiles ? part[bb + 1].x : -1;
+                cv[k] = bb < tiles ? carry[bb] : 0.f;
+            }
+            bool all_in = true;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const bool in = pr[k] == hr;
+                if (in) sum += cv[k];
+                all_in = all_in && in;
+            }
+            if (!__all_sync(0xffffffffu, all_in)) break;
+        }
+        for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+        if (lane == src) y[hr] = sum + y[hr];
+    }
 }
 
 // norm[0] = sqrt(sum x_i^2): per thread Kahan fp32, per block fp64 tree,
@@ -432,8 +465,8 @@ int launch_spmv(const LaunchArgs &a, void *sv)
                                                      a.p<int2>(4), a.p<float>(5), a.p<float>(6), nrows);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    spmv_fixup_kernel<<<(unsigned)ceil_div((int64_t)tiles * 32, 256), 256, 0, s>>>(a.p<int2>(4), a.p<float>(6),
-                                                                                   a.p<float>(5), nrows, tiles);
+    spmv_fixup_kernel<<<(unsigned)ceil_div(tiles, 256), 256, 0, s>>>(a.p<int2>(4), a.p<float>(6), a.p<float>(5),
+                                                                      nrows, tiles);
     return cudaGetLastError();
 }
 
