@@ -195,6 +195,27 @@ struct Ctx {
         return GDAG_OK;
     }
 
+    // Mark one active node inactive: its event slot and its stream's share
+    // are released.  Returns false if it was not active.
+    bool deactivate(Node *n)
+    {
+        if (!n || !n->active) return false;
+        n->active = false;
+        --active_count;
+        if (n->event >= 0) {
+            free_events.push_back(n->event);
+            n->event = -1;
+        }
+        if (n->stream >= 0) {
+            StreamState &s = streams[(size_t)n->stream];
+            if (--s.active == 0 && !s.queued) {
+                s.queued = true;
+                free_streams.push_back(n->stream);
+            }
+        }
+        return true;
+    }
+
     // Retire node id and all its active ancestors (their results are
     // complete once the host has observed id's completion).
     void retire(int64_t id)
@@ -204,20 +225,7 @@ struct Ctx {
             int64_t v = stack.back();
             stack.pop_back();
             Node *n = node(v);
-            if (!n || !n->active) continue;
-            n->active = false;
-            --active_count;
-            if (n->event >= 0) {
-                free_events.push_back(n->event);
-                n->event = -1;
-            }
-            if (n->stream >= 0) {
-                StreamState &s = streams[(size_t)n->stream];
-                if (--s.active == 0 && !s.queued) {
-                    s.queued = true;
-                    free_streams.push_back(n->stream);
-                }
-            }
+            if (!deactivate(n)) continue;
             for (uint32_t k = 0; k < n->parent_cnt; ++k) stack.push_back(parent_arena[n->parent_off + k]);
         }
     }
@@ -490,36 +498,76 @@ struct Ctx {
     // After the node's work op: record its event; under SERIAL_SYNC wait.
     int finish(int64_t id, int32_t s)
     {
-        Node *me = node(id);
+        int r = record_end(id, s);
+        if (r) return unrecorded(id, s, r);
+        if (opt.policy == GDAG_POLICY_SERIAL_SYNC) return host_wait(id);
+        return GDAG_OK;
+    }
+
+    int record_end(int64_t id, int32_t s)
+    {
         int r;
         if (opt.trace) {
             void *e;
             r = be->event_create(&e, true);
             if (r) return be_fail(r, "event create");
             tevents.push_back(e);
-            me = node(id);
-            me->tev1 = (int32_t)tevents.size() - 1;
+            node(id)->tev1 = (int32_t)tevents.size() - 1;
             r = be->event_record(e, streams[(size_t)s].handle);
             if (r) return be_fail(r, "event record");
         }
         int32_t slot;
         r = acquire_event(&slot);
         if (r) return r;
-        me = node(id);
-        me->event = slot;
+        node(id)->event = slot;
         log_op(GDAG_OP_RECORD, s, slot, id);
         r = be->event_record(events[(size_t)slot], streams[(size_t)s].handle);
         if (r) return be_fail(r, "event record");
-        if (opt.policy == GDAG_POLICY_SERIAL_SYNC) return host_wait(id);
         return GDAG_OK;
     }
 
-    // A failed work op: the node stays in the DAG as a retired element.
-    int abort_node(int64_t id, int r, const char *what)
+    // The node's work was issued but its event was not recorded, so no
+    // later element could wait for it.  The host waits for its stream
+    // instead (the work and, through the stream's waits, the node's
+    // parents) and retires it; if that wait fails too, only the node is
+    // retired.  The error `rc` and its message are kept.
+    int unrecorded(int64_t id, int32_t s, int rc)
     {
-        retire(id);
-        return be_fail(r, what);
+        const std::string msg = last_error;
+        bool done = capturing || poisoned;
+        if (!done) {
+            log_op(GDAG_OP_STREAM_SYNC, s, -1, -1);
+            ++st.host_waits;
+            done = poll_stream(s) == GDAG_OK;
+        }
+        if (done) retire(id);
+        else deactivate(node(id));
+        last_error = msg;
+        return rc;
     }
+
+    // An element whose placement or work op failed stays in the DAG as a
+    // retired element.  Its work never ran, so nothing it would have ordered
+    // is known to be complete: later elements that conflict with its
+    // parents only through it (a reader of an array it was to overwrite,
+    // say) would get no wait.  So the host first waits for its active
+    // parents (`par` still holds them), which retires them truthfully, and
+    // only then retires the element itself.  If such a wait fails, only the
+    // element is retired.  The error `rc` and its message are kept.
+    int drop_failed(int64_t id, int rc)
+    {
+        const std::string msg = last_error;
+        bool waited = true;
+        if (!capturing && !poisoned) {
+            const std::vector<int64_t> ps(par);
+            for (size_t i = 0; i < ps.size() && waited; ++i) waited = host_wait(ps[i]) == GDAG_OK;
+        }
+        if (waited) retire(id);
+        else deactivate(node(id));
+        last_error = msg;
+        return rc;
+    }
+    int abort_node(int64_t id, int r, const char *what) { return drop_failed(id, be_fail(r, what)); }
 
     // ------------------------------------------------------------ arrays
     ArrayState *arr(int32_t a)
@@ -863,10 +911,7 @@ int gdag_launch(gdag_ctx *c, gdag_kernel k, gdag_dim3 grid, gdag_dim3 block, siz
     if (node_out) *node_out = id;
     int32_t s;
     r = c->place(id, &s);
-    if (r) {
-        c->retire(id);
-        return r;
-    }
+    if (r) return c->drop_failed(id, r);
     c->log_op(GDAG_OP_LAUNCH, s, -1, id);
     ++c->st.launches;
     r = c->be->launch(c->kernels[(size_t)k], la, c->streams[(size_t)s].handle);
@@ -929,10 +974,7 @@ int gdag_launch_fused(gdag_ctx *c, gdag_kernel k, const gdag_arg *args, int32_t 
     if (node_out) *node_out = id;
     int32_t s;
     r = c->place(id, &s);
-    if (r) {
-        c->retire(id);
-        return r;
-    }
+    if (r) return c->drop_failed(id, r);
     c->log_op(GDAG_OP_LAUNCH, s, -1, id);
     ++c->st.launches;
     c->st.fused_members += count;
@@ -986,10 +1028,7 @@ int gdag_launch_external(gdag_ctx *c, void (*fn)(void *, void *), void *user, co
     if (node_out) *node_out = id;
     int32_t s;
     r = c->place(id, &s);
-    if (r) {
-        c->retire(id);
-        return r;
-    }
+    if (r) return c->drop_failed(id, r);
     c->log_op(GDAG_OP_EXTERNAL, s, -1, id);
     r = c->be->external(fn, user, c->streams[(size_t)s].handle);
     if (r) return c->abort_node(id, r, "external call");
@@ -1048,10 +1087,7 @@ int gdag_array_write(gdag_ctx *c, gdag_array a, const void *src, size_t off, siz
     c->push_node(GDAG_NODE_HOST_WRITE);
     int32_t st;
     r = c->place(id, &st);
-    if (r) {
-        c->retire(id);
-        return r;
-    }
+    if (r) return c->drop_failed(id, r);
     c->log_op(GDAG_OP_COPY_H2D, st, -1, id);
     ++c->st.copies;
     r = c->be->copy_h2d(static_cast<char *>(s->dev) + off, view, bytes, c->streams[(size_t)st].handle);
@@ -1094,10 +1130,7 @@ int gdag_array_read(gdag_ctx *c, gdag_array a, void *dst, size_t off, size_t byt
     } else if (!s->host_valid) {
         int32_t st;
         r = c->place(id, &st);
-        if (r) {
-            c->retire(id);
-            return r;
-        }
+        if (r) return c->drop_failed(id, r);
         c->log_op(GDAG_OP_COPY_D2H, st, -1, id);
         ++c->st.copies;
         r = c->be->copy_d2h(view, static_cast<char *>(s->dev) + off, bytes, c->streams[(size_t)st].handle);
@@ -1137,10 +1170,7 @@ int gdag_array_prefetch_host(gdag_ctx *c, gdag_array a, size_t off, size_t bytes
     c->push_node(GDAG_NODE_HOST_PREFETCH);
     int32_t st;
     r = c->place(id, &st);
-    if (r) {
-        c->retire(id);
-        return r;
-    }
+    if (r) return c->drop_failed(id, r);
     c->log_op(GDAG_OP_COPY_D2H, st, -1, id);
     ++c->st.copies;
     r = c->be->copy_d2h(static_cast<char *>(s->host) + off, static_cast<char *>(s->dev) + off, bytes,
@@ -1365,10 +1395,7 @@ int gdag_graph_launch(gdag_ctx *c, gdag_graph g, int64_t *node_out)
     if (node_out) *node_out = id;
     int32_t s;
     r = c->place(id, &s);
-    if (r) {
-        c->retire(id);
-        return r;
-    }
+    if (r) return c->drop_failed(id, r);
     c->log_op(GDAG_OP_LAUNCH, s, -1, id);
     r = c->be->graph_launch(gr.exec, c->streams[(size_t)s].handle);
     if (r) return c->abort_node(id, r, "graph launch");

@@ -382,3 +382,32 @@ def test_option_environment_overrides(monkeypatch):
     monkeypatch.setenv("GDAG_PREFETCH", "not a number")
     o = G.gdag_options_default()
     assert o.max_streams == 5 and o.timeout_ms == 1234 and o.prefetch == 1
+
+
+@pytest.mark.parametrize("fail_op,where", [(4, "wait"), (5, "launch"), (6, "event record")])
+def test_failed_element_keeps_its_parents_ordered(fail_op, where):
+    """Two readers of x run on two streams; a writer of x, whose wait, launch
+    or event record fails, sits between them and a second writer of x.  The
+    second writer conflicts with the readers only through the failed one,
+    so it must still run after both readers: the failure may not retire
+    parents that have not been seen to complete."""
+    ctx = G.Context(backend="fake", record_log=True, fake_fail_op=fail_op)
+    x = ctx.array(dev=0x1000, nbytes=64)
+    k = G.gdag_kernel_register(ctx.h, "k1", None, [SPEC])
+
+    def run(mode):
+        return G.gdag_launch(ctx.h, k, G.gdag_dim3(1, 1, 1), G.gdag_dim3(32, 1, 1), 0,
+                             [G.array_arg(x.handle, mode)])
+
+    r1 = run(G.GDAG_MODE_IN)   # ops 0-1: launch, record (stream 0)
+    r2 = run(G.GDAG_MODE_IN)   # ops 2-3: launch, record (stream 1)
+    with pytest.raises(G.GdagError) as e:
+        run(G.GDAG_MODE_OUT)   # op 4 wait on r2, op 5 launch, op 6 record
+    assert e.value.code == G.GDAG_ERR_CUDA
+    assert "injected failure at op %d" % fail_op in str(e.value)
+    w = run(G.GDAG_MODE_OUT)
+    assert w == 3
+    assert D.check_hb(ctx.ops(), [(r1, w), (r2, w)]) == []
+    ctx.sync()
+    assert ctx.stats()["active"] == 0
+    ctx.close()
