@@ -135,6 +135,10 @@ struct Ctx {
     struct Graph {
         void *exec = nullptr;
         std::vector<Access> access;
+        // each accessed array's device and host pointers and size at capture
+        // time: the graph's copies and launches hold these addresses
+        std::vector<const void *> dev, host;
+        std::vector<size_t> bytes;
         bool live = false;
     };
     std::vector<Graph> graphs;
@@ -1369,6 +1373,12 @@ int gdag_capture_end(gdag_ctx *c, gdag_graph *out)
     Ctx::Graph g;
     g.exec = exec;
     g.access = c->cap_access;
+    for (const Access &a : g.access) {
+        const ArrayState &st = c->arrays[(size_t)a.array];
+        g.dev.push_back(st.dev);
+        g.host.push_back(st.host);
+        g.bytes.push_back(st.bytes);
+    }
     g.live = true;
     c->graphs.push_back(g);
     *out = (gdag_graph)c->graphs.size() - 1;
@@ -1385,8 +1395,14 @@ int gdag_graph_launch(gdag_ctx *c, gdag_graph g, int64_t *node_out)
     if (g < 0 || (size_t)g >= c->graphs.size() || !c->graphs[(size_t)g].live)
         return c->fail(GDAG_ERR_INVALID, "unknown graph %d", g);
     const Ctx::Graph &gr = c->graphs[(size_t)g];
-    for (const auto &a : gr.access)
-        if (!c->arr(a.array)) return c->fail(GDAG_ERR_INVALID, "graph uses unregistered array %d", a.array);
+    for (size_t i = 0; i < gr.access.size(); ++i) {
+        const int32_t a = gr.access[i].array;
+        const ArrayState *st = c->arr(a);
+        if (!st) return c->fail(GDAG_ERR_INVALID, "graph uses unregistered array %d", a);
+        if (st->dev != gr.dev[i] || st->host != gr.host[i] || st->bytes != gr.bytes[i])
+            return c->fail(GDAG_ERR_INVALID, "array %d was registered again at another address since graph %d was captured",
+                           a, g);
+    }
     int64_t id = c->next_id();
     c->infer(id, gr.access.data(), (int)gr.access.size());
     for (const auto &a : gr.access)

@@ -308,6 +308,33 @@ def test_capture_and_replay_as_one_element():
         G.gdag_graph_launch(p.ctx.h, g)
 
 
+def test_replay_refuses_arrays_registered_again_elsewhere():
+    """A graph holds the addresses its arrays had at capture: after one of
+    them is unregistered and its handle reused for memory elsewhere, the
+    replay is refused; at the same address and size it is allowed."""
+    p = Program(2)
+    G.gdag_capture_begin(p.ctx.h)
+    p.kernel({0: D.R, 1: D.W})
+    g = G.gdag_capture_end(p.ctx.h)
+    G.gdag_graph_launch(p.ctx.h, g)
+    p.ctx.sync()
+    dev1 = 0x10000 * 2
+    p.ctx.unregister(p.arrays[1])
+    with pytest.raises(G.GdagError) as e:
+        G.gdag_graph_launch(p.ctx.h, g)
+    assert e.value.code == G.GDAG_ERR_INVALID
+    b = p.ctx.array(dev=0x90000, nbytes=64)  # takes the freed handle
+    assert b.handle == p.arrays[1].handle
+    with pytest.raises(G.GdagError) as e:
+        G.gdag_graph_launch(p.ctx.h, g)
+    assert e.value.code == G.GDAG_ERR_INVALID and "another address" in p.ctx.last_error
+    p.ctx.unregister(b)
+    c = p.ctx.array(dev=dev1, nbytes=64)  # the captured address again
+    assert c.handle == p.arrays[1].handle
+    G.gdag_graph_launch(p.ctx.h, g)
+    p.ctx.sync()
+
+
 def test_capture_rejects_host_waits_and_sync_policy():
     p = Program(2)
     G.gdag_capture_begin(p.ctx.h)
