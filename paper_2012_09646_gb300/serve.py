@@ -12,8 +12,11 @@ they arrive as a Poisson stream.  One dispatcher thread does four things:
 * polls in-flight requests with a non-blocking node query, reads the response
   of each one that finished (served from the prefetched host view), and
   releases its memory;
-* records each request's latency, from its arrival time to the moment its
-  response is on the host.
+* records each request's latency, from its arrival time to the moment all
+  of its work has completed and its response is on the host.  A request is
+  complete when its sinks are: the response prefetch plus every node of the
+  request that is not an ancestor of it (the other nine B&S outputs, the ML
+  branch beside the image, the last hub update of HITS).
 
 Requests admitted in the same dispatcher pass are issued together.  With
 fusion on, the small same-kind nodes of a VEC or B&S group (at most
@@ -119,14 +122,14 @@ class Inputs:
 
 
 class Request:
-    __slots__ = ("rid", "kind", "scale", "arrival", "admitted", "done_at", "bytes", "final", "tensors", "arrays",
+    __slots__ = ("rid", "kind", "scale", "arrival", "admitted", "done_at", "bytes", "sinks", "tensors", "arrays",
                  "resp", "resp_view", "slot", "scratch", "need")
 
     def __init__(self, rid, kind, scale, arrival):
         self.rid, self.kind, self.scale, self.arrival = rid, kind, scale, arrival
         self.admitted = self.done_at = None
         self.bytes = 0
-        self.final = -1
+        self.sinks = []
         self.tensors, self.arrays = [], []
         self.resp = None
         self.resp_view = None
@@ -138,7 +141,8 @@ class Request:
 class Server:
     """One gdag context shared by every request."""
 
-    def __init__(self, inputs, budget_bytes=40 << 30, max_streams=32, device="cuda", fuse_max=None, backend="cuda"):
+    def __init__(self, inputs, budget_bytes=40 << 30, max_streams=32, device="cuda", fuse_max=None, backend="cuda",
+                 record_log=False):
         """``fuse_max``: {kind: largest node size (elements) that is fused
         across requests}; None or {} turns fusion off.  ``backend="fake"``
         (with ``device="cpu"``) runs the dispatcher on the recording backend:
@@ -150,7 +154,7 @@ class Server:
         self.used = 0
         self.device = device
         self.ctx = G.Context(max_streams=max_streams, retire_by_query=True, backend=backend,
-                             fake_complete=backend == "fake")
+                             fake_complete=backend == "fake", record_log=record_log)
         self.shared = {}
         self._slots = []  # pinned response buffers, reused
         self._scratch_pool = {}
@@ -211,6 +215,7 @@ class Server:
         d = self.inp.data[(r.kind, b)]
         dev = self.device
         r.slot = self._slot()
+        tails = []  # nodes of r that are not ancestors of its response prefetch
         if r.kind == "VEC":
             n = d["n"]
             X = self._arr(r, torch.empty(n, dtype=F32, device=dev), host=d["hx"])
@@ -229,7 +234,9 @@ class Server:
             for i, St in enumerate(d["S"]):
                 Sa = self._shared(("bs", b, i), St)
                 Ca = self._arr(r, torch.empty(n, dtype=F32, device=dev), host=r.slot if i == 0 else None)
-                c.launch("bs_call", Sa, Ca, n, 60.0, 0.1, 0.2, 1.0)
+                k = c.launch("bs_call", Sa, Ca, n, 60.0, 0.1, 0.2, 1.0)
+                if i:
+                    tails.append(k)
                 outs.append(Ca)
             r.resp = (outs[0], min(4 * n, RESPONSE_BYTES))
         elif r.kind == "IMG+ML":
@@ -264,7 +271,7 @@ class Server:
             c.launch("dense_scores", XA, T2, B2, S2, rows, 1024, 10)
             c.launch("row_softmax", S1, rows, 10)
             c.launch("row_softmax", S2, rows, 10)
-            c.launch("argmax_combine", S1, S2, LAB, rows, 10)
+            tails.append(c.launch("argmax_combine", S1, S2, LAB, rows, 10))
             # the response: the head of the combined image (the labels stay
             # on the device)
             r.resp = (OUT, min(4 * n, RESPONSE_BYTES))
@@ -293,15 +300,12 @@ class Server:
                 c.launch("l2norm", a_out, NA, SA, n)
                 c.launch("l2norm", h_out, NH, SH, n)
                 c.launch("scale", a_out, NA, n)
-                c.launch("scale", h_out, NH, n)
+                k = c.launch("scale", h_out, NH, n)
                 cur = (a_out, h_out)
+            tails.append(k)  # the last hub update
             # 5 iterations end in the first buffer pair (a2, h2)
             r.resp = (v["a2"], min(4 * n, RESPONSE_BYTES))
-        arr, nb = r.resp
-        c.prefetch_host(arr, 0, nb)
-        r.final = self.ctx.nodes()[-1][0] if self.ctx.options.record_log else None
-        if r.final is None:
-            r.final = self._last_node()
+        self._finish_issue(r, tails)
 
     def _fusable(self, r):
         lim = self.fuse_max.get(r.kind)
@@ -364,10 +368,12 @@ class Server:
         for r in g:
             self._finish_issue(r)
 
-    def _finish_issue(self, r):
+    def _finish_issue(self, r, tails=()):
+        """Issue r's response prefetch and set its sinks (in a fused group
+        every member's nodes are ancestors of its prefetch)."""
         arr, nb = r.resp
         self.ctx.prefetch_host(arr, 0, nb)
-        r.final = self._last_node()
+        r.sinks = list(tails) + [self._last_node()]
 
     def _last_node(self):
         return G.gdag_stats_get(self.ctx.h).nodes - 1
@@ -454,7 +460,9 @@ class Server:
                 inflight.extend(batch)
             still = []
             for r in inflight:
-                if self.ctx.done(r.final):
+                while r.sinks and self.ctx.done(r.sinks[-1]):
+                    r.sinks.pop()
+                if not r.sinks:
                     self.finish(r, clock() - t0)
                     done += 1
                 else:

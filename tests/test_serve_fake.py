@@ -87,3 +87,49 @@ def test_fusion_threshold_excludes_large_nodes(inputs):
     srv.run([SV.Request(r.rid, r.kind, r.scale, 0.0) for r in burst])
     assert srv.ctx.stats()["fused_members"] == f0
     srv.close()
+
+
+def _ancestors(edges, sinks):
+    par = {}
+    for s, d, _a, _k in edges:
+        par.setdefault(d, set()).add(s)
+    seen, stack = set(), list(sinks)
+    while stack:
+        v = stack.pop()
+        if v not in seen:
+            seen.add(v)
+            stack.extend(par.get(v, ()))
+    return seen
+
+
+def test_sinks_cover_every_node_of_a_request(inputs):
+    """A request is complete when its sinks are: every node it issued is an
+    ancestor of (or is) one of them.  For every kind but VEC the response
+    prefetch alone does not cover the request (other outputs, the ML branch,
+    the last hub update), so the extra sinks are needed."""
+    srv = server(inputs, record_log=True)
+    for kind in SV.KINDS:
+        r = SV.Request(0, kind, SCALES[0], 0.0)
+        first = srv._last_node() + 1
+        srv.issue(r)
+        mine = set(range(first, srv._last_node() + 1))
+        edges = srv.ctx.edges()
+        assert mine <= _ancestors(edges, r.sinks), kind
+        covered_by_prefetch = mine <= _ancestors(edges, r.sinks[-1:])
+        assert covered_by_prefetch == (kind == "VEC"), kind
+        srv.ctx.sync()
+        srv.finish(r, 0.0)
+    # fused groups: each member's sink is its prefetch, after the fused nodes
+    for kind in ("VEC", "B&S"):
+        g = [SV.Request(i, kind, SCALES[i % 2], 0.0) for i in range(4)]
+        srv.fuse_max = {kind: 1 << 30}
+        first = srv._last_node() + 1
+        srv.issue_batch(g)
+        mine = set(range(first, srv._last_node() + 1))
+        edges = srv.ctx.edges()
+        assert all(len(r.sinks) == 1 for r in g)
+        assert mine <= set().union(*(_ancestors(edges, r.sinks) for r in g)), kind
+        srv.ctx.sync()
+        for r in g:
+            srv.finish(r, 0.0)
+    srv.close()
