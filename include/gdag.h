@@ -20,7 +20,13 @@
  *     gdag context is poisoned and every later call returns
  *     GDAG_ERR_POISONED; gdag_destroy() still releases host resources;
  *   - host waits poll for completion against options.timeout_ms and return
- *     GDAG_ERR_TIMEOUT instead of blocking forever.
+ *     GDAG_ERR_TIMEOUT instead of blocking forever;
+ *   - an element whose stream wait, launch, copy or event record fails with
+ *     a non-sticky error still gets its node id and its edges, but is
+ *     retired at once.  Before the call returns, the host waits for the
+ *     element's active parents (or, when its work was issued but its event
+ *     could not be recorded, for its stream), so that later elements stay
+ *     ordered after them.
  */
 #ifndef GDAG_H
 #define GDAG_H
