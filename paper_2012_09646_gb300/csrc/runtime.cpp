@@ -1145,7 +1145,16 @@ int gdag_array_read(gdag_ctx *c, gdag_array a, void *dst, size_t off, size_t byt
         if (r) return r;
         if (off == 0 && bytes == s->bytes) s->host_valid = true;
     } else {
-        // the view already holds the data: a host-only element
+        // The view already holds the data: a host-only element.  A later
+        // writer of the array takes its edges from the readers alone, so
+        // this element must not complete before its writer: when that is a
+        // host write whose copy to the device is still in flight, the host
+        // waits for the copy first (a writer that races it would otherwise
+        // be overwritten by it).
+        for (int64_t p : c->par) {
+            r = c->host_wait(p);
+            if (r) return r;
+        }
         c->log_op(GDAG_OP_HOST_NODE, -1, -1, id);
     }
     if (dst && dst != view) std::memcpy(dst, view, bytes);

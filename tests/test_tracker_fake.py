@@ -438,3 +438,74 @@ def test_failed_element_keeps_its_parents_ordered(fail_op, where):
     ctx.sync()
     assert ctx.stats()["active"] == 0
     ctx.close()
+
+
+BACKEND_OPS = (G.GDAG_OP_RECORD, G.GDAG_OP_WAIT, G.GDAG_OP_LAUNCH, G.GDAG_OP_COPY_H2D, G.GDAG_OP_COPY_D2H,
+               G.GDAG_OP_EXTERNAL)
+
+
+@pytest.mark.parametrize("seed", range(400))
+def test_random_programs_with_an_injected_failure_stay_ordered(seed):
+    """A random program whose k-th backend op fails (not sticky): the failing
+    call raises and the program goes on.  With the failed op taken out of the
+    recorded log, every two elements that conflict directly and did not fail
+    are still ordered by CUDA's stream/event rules plus host waits, even
+    where the nearest edges between them ran through the failed element.
+    Without a failure (k beyond the program's ops) this is the plain
+    serialisability check over every conflicting pair."""
+    rng = random.Random(1000 + seed)
+    n_arrays = rng.randint(1, 5)
+    opts = rng.choice([{}, {"max_streams": 2}, {"retire_by_query": True, "fake_complete": True},
+                       {"policy": G.GDAG_POLICY_SERIAL_ASYNC}, {"policy": G.GDAG_POLICY_SERIAL_SYNC}])
+    fail_at = rng.randrange(60)
+    p = Program(n_arrays, fake_fail_op=fail_at, **opts)
+    failed = []
+    for _ in range(rng.randint(1, 30)):
+        r = rng.random()
+        a = rng.randrange(n_arrays)
+        if r < 0.12:
+            acc, call = {a: D.W}, lambda: p.ctx.write(p.arrays[a], None)
+        elif r < 0.22:
+            acc, call = {a: D.R}, lambda: p.ctx.read(p.arrays[a])
+        else:
+            arrs = rng.sample(range(n_arrays), rng.randint(1, min(4, n_arrays)))
+            acc = {b: rng.choice([D.R, D.R, D.W, D.RW]) for b in arrs}
+            args = [G.array_arg(p.arrays[b].handle, MODE_OF[m]) for b, m in acc.items()]
+            call = lambda: G.gdag_launch(p.ctx.h, p.kern[len(args)], G.gdag_dim3(1, 1, 1),
+                                         G.gdag_dim3(32, 1, 1), 0, args)
+        try:
+            call()
+        except G.GdagError as e:
+            assert e.code == G.GDAG_ERR_CUDA and "injected failure at op %d" % fail_at in str(e)
+            failed.append(len(p.elems))
+        p.elems.append(acc)
+    assert len(failed) <= 1
+    assert [n[0] for n in p.ctx.nodes()] == list(range(len(p.elems)))
+    ops = p.ctx.ops()
+    backend = [q for q, o in enumerate(ops) if o[0] in BACKEND_OPS]
+    if failed:
+        del ops[backend[fail_at]]
+    pairs = [(i, j) for i, j in D.conflict_pairs(p.elems) if i not in failed and j not in failed]
+    assert D.check_hb(ops, pairs) == []
+    p.ctx.sync()
+    assert p.ctx.stats()["active"] == 0
+
+
+def test_read_from_the_view_waits_for_the_copy_that_filled_it():
+    """A full host write fills the view and starts its copy to the device; a
+    host read is then served from the view.  A kernel that next writes the
+    array takes its edge from the read alone (the dependency-set rule), so
+    the read may not complete before the copy: the host waits for it, and
+    the kernel cannot race the copy."""
+    p = Program(2)
+    p.kernel({1: D.W})          # keeps stream 0 busy
+    w = len(p.elems)
+    p.write(0)                  # copy on its own stream, still in flight
+    r = len(p.elems)
+    p.read(0)                   # served from the view
+    k = p.kernel({0: D.W})
+    edges = {(s, d) for s, d, _a, _k in p.ctx.edges()}
+    assert (w, r) in edges and (r, k) in edges and (w, k) not in edges
+    ops = p.ctx.ops()
+    assert (G.GDAG_OP_HOST_WAIT, ) == tuple(o[0] for o in ops if o[3] == w and o[0] == G.GDAG_OP_HOST_WAIT)
+    assert D.check_hb(ops, [(w, k)]) == []
