@@ -455,9 +455,10 @@ int gdag_capture_end(gdag_ctx *ctx, gdag_graph *out);
 
 /* Replay graph g as one DAG element whose accesses are the union of the
  * captured elements' accesses (edges, stream choice and waits as for a
- * kernel).  The arrays must still be registered, at the device and host
- * addresses and sizes they had at capture (the graph holds those addresses);
- * otherwise GDAG_ERR_INVALID. */
+ * kernel).  The arrays must still be registered, at the device address,
+ * size and (where the array had one at capture) host view they had at
+ * capture, since the graph holds those addresses; otherwise
+ * GDAG_ERR_INVALID. */
 int gdag_graph_launch(gdag_ctx *ctx, gdag_graph g, int64_t *node_out);
 
 /* Wait for all work, then free graph g. */

@@ -1408,7 +1408,9 @@ int gdag_graph_launch(gdag_ctx *c, gdag_graph g, int64_t *node_out)
         const int32_t a = gr.access[i].array;
         const ArrayState *st = c->arr(a);
         if (!st) return c->fail(GDAG_ERR_INVALID, "graph uses unregistered array %d", a);
-        if (st->dev != gr.dev[i] || st->host != gr.host[i] || st->bytes != gr.bytes[i])
+        // (an array without a host view at capture had no host copy in it;
+        // its view may have been allocated since)
+        if (st->dev != gr.dev[i] || (gr.host[i] && st->host != gr.host[i]) || st->bytes != gr.bytes[i])
             return c->fail(GDAG_ERR_INVALID, "array %d was registered again at another address since graph %d was captured",
                            a, g);
     }

@@ -509,3 +509,110 @@ def test_read_from_the_view_waits_for_the_copy_that_filled_it():
     ops = p.ctx.ops()
     assert (G.GDAG_OP_HOST_WAIT, ) == tuple(o[0] for o in ops if o[3] == w and o[0] == G.GDAG_OP_HOST_WAIT)
     assert D.check_hb(ops, [(w, k)]) == []
+
+
+@pytest.mark.parametrize("seed", range(300))
+def test_random_programs_of_every_element_kind_are_serialisable(seed):
+    """Random programs mixing every kind of element: kernels with mode
+    overrides, fused launches, external library calls, full and partial
+    host writes, reads and prefetches, replays of a captured graph, with
+    syncs and node queries in between and, sometimes, one injected backend
+    failure.  Every two elements that conflict directly, both of which did
+    their work, are ordered by CUDA's stream/event rules plus host waits;
+    the edge log equals the brute-force edges of the program as issued."""
+    rng = random.Random(7000 + seed)
+    n_arrays = rng.randint(2, 6)
+    opts = rng.choice([{}, {"max_streams": 2}, {"max_streams": 1}, {"prefetch": False},
+                       {"retire_by_query": True, "fake_complete": True},
+                       {"policy": G.GDAG_POLICY_SERIAL_ASYNC}, {"policy": G.GDAG_POLICY_SERIAL_SYNC}])
+    # a capture issues backend ops of its own that the op log leaves out
+    # (the fork and join of the capture stream), so a program with a capture
+    # gets no injected failure: the failed op could not be found in the log
+    use_capture = rng.random() < 0.5 and opts.get("policy") != G.GDAG_POLICY_SERIAL_SYNC
+    fail_at = rng.randrange(120) if not use_capture and rng.random() < 0.7 else -1
+    p = Program(n_arrays, fake_fail_op=fail_at, **opts)
+    arrs = p.arrays
+    skip = set()       # elements that did no work (failed, or only captured)
+    graph = None
+    graph_acc = None
+
+    def n_nodes():
+        return G.gdag_stats_get(p.ctx.h).nodes
+
+    def attempt(acc, call, work=True):
+        before = n_nodes()
+        try:
+            call()
+        except G.GdagError as e:
+            assert e.code == G.GDAG_ERR_CUDA and "injected failure at op %d" % fail_at in str(e)
+            work = False
+        if n_nodes() > before:  # the call made one element
+            assert n_nodes() == before + 1
+            if not work:
+                skip.add(len(p.elems))
+            p.elems.append(acc)
+
+    def random_kernel():
+        ks = rng.sample(range(n_arrays), rng.randint(1, min(4, n_arrays)))
+        acc = {b: rng.choice([D.R, D.R, D.W, D.RW]) for b in ks}
+        args = [G.array_arg(arrs[b].handle, MODE_OF[m]) for b, m in acc.items()]
+        return acc, lambda: G.gdag_launch(p.ctx.h, p.kern[len(args)], G.gdag_dim3(1, 1, 1),
+                                          G.gdag_dim3(32, 1, 1), 0, args)
+
+    for _ in range(rng.randint(1, 35)):
+        r = rng.random()
+        a = rng.randrange(n_arrays)
+        off = rng.choice([0, 0, 16])
+        nb = 64 - off if rng.random() < 0.7 else 16
+        if r < 0.10:
+            attempt({a: D.W}, lambda: p.ctx.write(arrs[a], None, off, nb))
+        elif r < 0.18:
+            attempt({a: D.R}, lambda: p.ctx.read(arrs[a], None, off, nb))
+        elif r < 0.24:
+            attempt({a: D.R}, lambda: p.ctx.prefetch_host(arrs[a], off, nb))
+        elif r < 0.30:
+            # fused bs_call: members read shared prices, each writes its own output
+            outs = rng.sample(range(n_arrays), rng.randint(1, n_arrays - 1))
+            ins = [b for b in range(n_arrays) if b not in outs]
+            members = [(arrs[rng.choice(ins)], arrs[o], 16, 60.0, 0.1, 0.2, 1.0) for o in outs]
+            acc = {}
+            for S, C, *_ in members:
+                acc[S.handle - arrs[0].handle] = D.R
+                acc[C.handle - arrs[0].handle] = D.W
+            attempt(acc, lambda: p.ctx.launch_fused("bs_call", members))
+        elif r < 0.35:
+            ks = rng.sample(range(n_arrays), rng.randint(1, min(3, n_arrays)))
+            acc = {b: rng.choice([D.R, D.W, D.RW]) for b in ks}
+            attempt(acc, lambda: p.ctx.external(lambda s, u: None, [(arrs[b], MODE_OF[m]) for b, m in acc.items()]))
+        elif r < 0.40 and graph is None and use_capture:
+            G.gdag_capture_begin(p.ctx.h)
+            graph_acc = {}
+            try:
+                for _ in range(rng.randint(1, 3)):
+                    acc, call = random_kernel()
+                    call()
+                    skip.add(len(p.elems))
+                    p.elems.append(acc)
+                    for b, m in acc.items():
+                        graph_acc[b] = graph_acc.get(b, 0) | m
+            finally:
+                graph = G.gdag_capture_end(p.ctx.h)
+        elif r < 0.48 and graph is not None:
+            attempt(dict(graph_acc), lambda: G.gdag_graph_launch(p.ctx.h, graph))
+        elif r < 0.52:
+            p.ctx.sync()
+        elif r < 0.56 and p.elems:
+            p.ctx.done(rng.randrange(len(p.elems)))
+        else:
+            attempt(*random_kernel())
+    assert [n[0] for n in p.ctx.nodes()] == list(range(len(p.elems)))
+    assert edges_of(p.ctx) == D.expected_edges(p.elems)
+    ops = p.ctx.ops()
+    if fail_at >= 0:
+        backend = [q for q, o in enumerate(ops) if o[0] in BACKEND_OPS]
+        if fail_at < len(backend):
+            del ops[backend[fail_at]]
+    pairs = [(i, j) for i, j in D.conflict_pairs(p.elems) if i not in skip and j not in skip]
+    assert D.check_hb(ops, pairs) == []
+    p.ctx.sync()
+    assert p.ctx.stats()["active"] == 0
