@@ -516,8 +516,8 @@ def test_random_programs_of_every_element_kind_are_serialisable(seed):
     """Random programs mixing every kind of element: kernels with mode
     overrides, fused launches, external library calls, full and partial
     host writes, reads and prefetches, replays of a captured graph, with
-    syncs and node queries in between and, sometimes, one injected backend
-    failure.  Every two elements that conflict directly, both of which did
+    syncs, node queries and array re-registrations in between and,
+    sometimes, one injected backend failure.  Every two elements that conflict directly, both of which did
     their work, are ordered by CUDA's stream/event rules plus host waits;
     the edge log equals the brute-force edges of the program as issued."""
     rng = random.Random(7000 + seed)
@@ -531,10 +531,13 @@ def test_random_programs_of_every_element_kind_are_serialisable(seed):
     use_capture = rng.random() < 0.5 and opts.get("policy") != G.GDAG_POLICY_SERIAL_SYNC
     fail_at = rng.randrange(120) if not use_capture and rng.random() < 0.7 else -1
     p = Program(n_arrays, fake_fail_op=fail_at, **opts)
-    arrs = p.arrays
+    arrs = p.arrays    # slot -> registered array (slots are re-registered)
+    logical = list(range(n_arrays))   # slot -> logical array id
+    handle_of = {i: arrs[i].handle for i in range(n_arrays)}  # logical -> handle
     skip = set()       # elements that did no work (failed, or only captured)
     graph = None
     graph_acc = None
+    graph_live = True  # no array of the graph unregistered since its capture
 
     def n_nodes():
         return G.gdag_stats_get(p.ctx.h).nodes
@@ -550,7 +553,7 @@ def test_random_programs_of_every_element_kind_are_serialisable(seed):
             assert n_nodes() == before + 1
             if not work:
                 skip.add(len(p.elems))
-            p.elems.append(acc)
+            p.elems.append({logical[b]: m for b, m in acc.items()})
 
     def random_kernel():
         ks = rng.sample(range(n_arrays), rng.randint(1, min(4, n_arrays)))
@@ -574,11 +577,12 @@ def test_random_programs_of_every_element_kind_are_serialisable(seed):
             # fused bs_call: members read shared prices, each writes its own output
             outs = rng.sample(range(n_arrays), rng.randint(1, n_arrays - 1))
             ins = [b for b in range(n_arrays) if b not in outs]
-            members = [(arrs[rng.choice(ins)], arrs[o], 16, 60.0, 0.1, 0.2, 1.0) for o in outs]
+            pick = [(rng.choice(ins), o) for o in outs]
+            members = [(arrs[i], arrs[o], 16, 60.0, 0.1, 0.2, 1.0) for i, o in pick]
             acc = {}
-            for S, C, *_ in members:
-                acc[S.handle - arrs[0].handle] = D.R
-                acc[C.handle - arrs[0].handle] = D.W
+            for i, o in pick:
+                acc[i] = D.R
+                acc[o] = D.W
             attempt(acc, lambda: p.ctx.launch_fused("bs_call", members))
         elif r < 0.35:
             ks = rng.sample(range(n_arrays), rng.randint(1, min(3, n_arrays)))
@@ -592,13 +596,24 @@ def test_random_programs_of_every_element_kind_are_serialisable(seed):
                     acc, call = random_kernel()
                     call()
                     skip.add(len(p.elems))
-                    p.elems.append(acc)
+                    p.elems.append({logical[b]: m for b, m in acc.items()})
                     for b, m in acc.items():
                         graph_acc[b] = graph_acc.get(b, 0) | m
             finally:
                 graph = G.gdag_capture_end(p.ctx.h)
-        elif r < 0.48 and graph is not None:
+        elif r < 0.48 and graph is not None and graph_live:
             attempt(dict(graph_acc), lambda: G.gdag_graph_launch(p.ctx.h, graph))
+        elif r < 0.50:
+            # unregister (waits for the array's users) and register a new
+            # array, which may take the freed handle: a new logical array
+            p.ctx.unregister(arrs[a])
+            if graph_acc and a in graph_acc:
+                graph_live = False
+                with pytest.raises(G.GdagError):
+                    G.gdag_graph_launch(p.ctx.h, graph)
+            arrs[a] = p.ctx.array(dev=0x1000000 + 0x10000 * len(handle_of), nbytes=64)
+            logical[a] = len(handle_of)
+            handle_of[logical[a]] = arrs[a].handle
         elif r < 0.52:
             p.ctx.sync()
         elif r < 0.56 and p.elems:
@@ -606,7 +621,7 @@ def test_random_programs_of_every_element_kind_are_serialisable(seed):
         else:
             attempt(*random_kernel())
     assert [n[0] for n in p.ctx.nodes()] == list(range(len(p.elems)))
-    assert edges_of(p.ctx) == D.expected_edges(p.elems)
+    assert edges_of(p.ctx) == {(i, j, handle_of[a], k) for i, j, a, k in D.expected_edges(p.elems)}
     ops = p.ctx.ops()
     if fail_at >= 0:
         backend = [q for q, o in enumerate(ops) if o[0] in BACKEND_OPS]
