@@ -9,6 +9,7 @@ accepts torch tensors (device memory) and Python scalars.
 from __future__ import annotations
 
 import ctypes
+import numbers
 import os
 import struct
 
@@ -372,12 +373,7 @@ def array_arg(a, mode=GDAG_MODE_SIGNATURE):
 
 
 def scalar_arg(value, size):
-    if isinstance(value, float):
-        bits = struct.unpack("<I", struct.pack("<f", value))[0] if size == 4 else \
-            struct.unpack("<Q", struct.pack("<d", value))[0]
-    else:
-        bits = int(value) & ((1 << (8 * size)) - 1)
-    return gdag_arg(GDAG_ARG_SCALAR, 0, 0, size, bits)
+    return gdag_arg(GDAG_ARG_SCALAR, 0, 0, size, _scalar_bits(value, size))
 
 
 _F32 = struct.Struct("<f")
@@ -389,10 +385,23 @@ assert _ARG.size == ctypes.sizeof(gdag_arg)
 
 
 def _scalar_bits(value, size):
-    """The value field of a scalar argument (as scalar_arg builds it)."""
-    if isinstance(value, float):
-        return _U32.unpack(_F32.pack(value))[0] if size == 4 else _U64.unpack(_F64.pack(value))[0]
-    return int(value) & ((1 << (8 * size)) - 1)
+    """The value field of a scalar argument (as scalar_arg builds it):
+    integers (Python or numpy, and bool) as two's complement, anything else
+    (Python or numpy floats) as an IEEE float of `size` bytes."""
+    if isinstance(value, numbers.Integral):
+        return int(value) & ((1 << (8 * size)) - 1)
+    value = float(value)
+    return _U32.unpack(_F32.pack(value))[0] if size == 4 else _U64.unpack(_F64.pack(value))[0]
+
+
+def _scalar_key(a):
+    """Cache key of a scalar argument that is not an int or a nonzero float:
+    equal keys give equal argument bits.  Value equality alone would not do
+    (-0.0 == 0.0), so these keys add the value's bits as a double.  (A
+    nonzero Python float is its own key: equal nonzero floats have equal
+    bits, and a NaN, never equal, only misses the cache.)"""
+    c = a.__class__
+    return (c, a) if c is int else (c, a, _F64.pack(a))
 
 
 class Array:
@@ -511,7 +520,9 @@ class Context:
         scalars) come from a cache."""
         key = (name,) + tuple(
             a.handle if a.__class__ is Array else
-            (Mode, a.array.handle, a.mode) if a.__class__ is Mode else (a.__class__, a) for a in args)
+            (Mode, a.array.handle, a.mode) if a.__class__ is Mode else
+            (int, a) if a.__class__ is int else
+            (float, a) if a.__class__ is float and a else _scalar_key(a) for a in args)
         hit = self._packed.get(key)
         if hit is not None:
             out += hit[1]
@@ -561,7 +572,9 @@ class Context:
         # choice and event waits still run on every launch, in the library.
         key = (name, tuple(grid) if grid else None, tuple(block) if block else None, smem) + tuple(
             a.handle if a.__class__ is Array else
-            (Mode, a.array.handle, a.mode) if a.__class__ is Mode else (a.__class__, a) for a in args)
+            (Mode, a.array.handle, a.mode) if a.__class__ is Mode else
+            (int, a) if a.__class__ is int else
+            (float, a) if a.__class__ is float and a else _scalar_key(a) for a in args)
         p = self._prepared.get(key)
         if p is None:
             buf = bytearray()

@@ -386,6 +386,40 @@ def test_launch_argument_cache_keys_types_and_handles():
     assert len(ctx.nodes()) == 3
 
 
+def test_launch_argument_cache_keeps_the_sign_of_zero_and_numpy_floats():
+    """-0.0 == 0.0 in Python, but the two are different arguments: the
+    cached marshalling must not hand the bits of one to the other.  numpy
+    float scalars are floats, not truncated integers."""
+    import numpy as np
+    ctx = G.Context(backend="fake")
+    a = ctx.array(dev=0x1000, nbytes=400)
+    c = ctx.array(dev=0x2000, nbytes=400)
+
+    def r_bits():  # the r argument (index 4) of the latest prepared launch
+        return list(ctx._prepared.values())[-1][4][4].value
+
+    ctx.launch("bs_call", a, c, 100, 60.0, 0.0, 0.2, 1.0)
+    assert r_bits() == 0
+    ctx.launch("bs_call", a, c, 100, 60.0, -0.0, 0.2, 1.0)
+    assert r_bits() == 0x80000000 and len(ctx._prepared) == 2
+    ctx.launch("bs_call", a, c, 100, 60.0, np.float32(-0.0), 0.2, 1.0)
+    assert r_bits() == 0x80000000
+    ctx.launch("bs_call", a, c, 100, 60.0, np.float32(0.5), 0.2, 1.0)
+    assert r_bits() == 0x3F000000
+    ctx.launch("bs_call", a, c, 100, 60.0, np.float32(0.0), 0.2, 1.0)
+    assert r_bits() == 0
+    assert G._scalar_bits(np.float64(-0.0), 8) == 1 << 63
+    assert G._scalar_bits(np.int32(-1), 4) == 0xFFFFFFFF
+    assert G._scalar_bits(True, 4) == 1
+    # fused members go through the same keys
+    buf = bytearray()
+    ctx._pack("bs_call", (a, c, 100, 60.0, 0.0, 0.2, 1.0), buf)
+    ctx._pack("bs_call", (a, c, 100, 60.0, -0.0, 0.2, 1.0), buf)
+    half = len(buf) // 2
+    assert bytes(buf[:half]) != bytes(buf[half:])
+    ctx.close()
+
+
 def test_chrome_trace_export(tmp_path):
     import json
     p = Program(3, trace=True, fake_complete=True)
