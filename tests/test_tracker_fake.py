@@ -556,15 +556,19 @@ def test_random_programs_of_every_element_kind_are_serialisable(seed):
     the edge log equals the brute-force edges of the program as issued."""
     rng = random.Random(7000 + seed)
     n_arrays = rng.randint(2, 6)
-    opts = rng.choice([{}, {"max_streams": 2}, {"max_streams": 1}, {"prefetch": False},
+    opts = rng.choice([{}, {"max_streams": 2}, {"max_streams": 1}, {"prefetch": False}, {"trace": True},
                        {"retire_by_query": True, "fake_complete": True},
                        {"policy": G.GDAG_POLICY_SERIAL_ASYNC}, {"policy": G.GDAG_POLICY_SERIAL_SYNC}])
-    # a capture issues backend ops of its own that the op log leaves out
-    # (the fork and join of the capture stream), so a program with a capture
-    # gets no injected failure: the failed op could not be found in the log
+    # a capture and tracing issue backend ops of their own that the op log
+    # leaves out (the fork and join of the capture stream, timing events),
+    # so such a program gets no injected failure: the failed op could not be
+    # found in the log
     use_capture = rng.random() < 0.5 and opts.get("policy") != G.GDAG_POLICY_SERIAL_SYNC
-    fail_at = rng.randrange(120) if not use_capture and rng.random() < 0.7 else -1
+    inject = not use_capture and not opts.get("trace")
+    fail_at = rng.randrange(120) if inject and rng.random() < 0.7 else -1
     p = Program(n_arrays, fake_fail_op=fail_at, **opts)
+    for k in range(min(rng.choice([0, 0, 1, 2]), opts.get("max_streams", 16))):  # caller-owned streams
+        G.gdag_add_stream(p.ctx.h, 0xC0000 + k)
     arrs = p.arrays    # slot -> registered array (slots are re-registered)
     logical = list(range(n_arrays))   # slot -> logical array id
     handle_of = {i: arrs[i].handle for i in range(n_arrays)}  # logical -> handle
