@@ -322,6 +322,11 @@ int gdag_array_prefetch_host(gdag_ctx *ctx, gdag_array a, size_t off,
  *        spmv_csr        (rowptr IN, col IN i32[nnz], val IN f32[nnz],
  *                         x IN f32[n], part IN, y OUT f32[n], carry INOUT,
  *                         n i32, nnz i32)                         y = A x
+ *                         The index data is not checked (only sizes are):
+ *                         rowptr must rise from 0 to nnz, every col entry
+ *                         must lie in [0, n), and part must come from
+ *                         spmv_partition of the same rowptr; a col entry
+ *                         outside x is an out-of-bounds device read
  *        l2norm          (x IN f32[n], norm OUT f32[1], scratch INOUT, n i64)
  *        scale           (x INOUT f32[n], norm IN f32[1], n i64)
  *                                                x := x/norm (norm 0: kept)
