@@ -401,7 +401,12 @@ def _scalar_key(a):
     nonzero Python float is its own key: equal nonzero floats have equal
     bits, and a NaN, never equal, only misses the cache.)"""
     c = a.__class__
-    return (c, a) if c is int else (c, a, _F64.pack(a))
+    if c is int:
+        return (c, a)
+    try:
+        return (c, a, _F64.pack(a))
+    except (struct.error, TypeError):  # not convertible to a double
+        return (c, a)
 
 
 class Array:
