@@ -109,11 +109,27 @@ typedef struct {
                                 wait; default 0 (the paper retires on host
                                 access only)                                  */
     int32_t record_log;      /* 1: keep element, edge and op logs for the
-                                export calls; default 0                      */
+                                export calls; 2: keep the op log only (for
+                                long programs: retired readers may then be
+                                dropped, see trim_nodes); default 0          */
     int32_t trace;           /* 1: timing events around every node for
                                 gdag_trace_export, and an NVTX range around
                                 each element's host-side issue; default 0    */
     int32_t timeout_ms;      /* host-wait deadline; default 60000            */
+    int32_t trim_nodes;      /* node-table size at which retired elements
+                                are dropped, so that a long-running program
+                                (a serving loop that never calls gdag_sync)
+                                holds memory for its active window only:
+                                once the table holds this many elements, the
+                                retired ones issued before the oldest active
+                                element are dropped, and unless record_log
+                                is 1 so are retired readers in each array's
+                                reader set.  A dropped element counts as
+                                retired everywhere (gdag_node_query reports
+                                it done).  Scheduling is unchanged: retired
+                                elements cause no waits and pick no
+                                streams.  0 = 65536; ignored when trace = 1
+                                (the trace keeps every element)              */
     int32_t fake_complete;   /* FAKE backend: 1 = an event reports complete
                                 when queried; 0 = only after a host wait;
                                 2 = never (host waits time out)              */
@@ -186,7 +202,8 @@ typedef struct {
 
 typedef struct {
     int64_t nodes;          /* elements issued                               */
-    int64_t edges;          /* logical edges inferred                        */
+    int64_t edges;          /* logical edges inferred (a reader dropped from
+                               its array's reader set gives none)           */
     int64_t waits;          /* cudaStreamWaitEvent calls issued              */
     int64_t launches;       /* kernel launches issued (all nodes)            */
     int64_t copies;         /* host<->device copies issued                   */
@@ -194,6 +211,8 @@ typedef struct {
     int32_t streams;        /* streams in the pool                           */
     int32_t active;         /* nodes currently active                        */
     int64_t fused_members;  /* launches folded into gdag_launch_fused calls  */
+    int64_t held_nodes;     /* elements held in the node table               */
+    int64_t held_readers;   /* reader-set entries held over all arrays       */
 } gdag_stats;
 
 /* ------------------------------------------------------------ lifetime */
@@ -471,8 +490,9 @@ int gdag_graph_destroy(gdag_ctx *ctx, gdag_graph g);
 
 /* ---------------------------------------------------------- inspection */
 
-/* Copy up to cap records; *n receives the total available.  These need
- * options.record_log = 1 (INVALID otherwise). */
+/* Copy up to cap records; *n receives the total available.  The edge and
+ * element logs need options.record_log = 1, the op log record_log = 1 or 2
+ * (INVALID otherwise). */
 int gdag_dag_export(gdag_ctx *ctx, gdag_edge *buf, size_t cap, size_t *n);
 int gdag_nodes_export(gdag_ctx *ctx, gdag_node_info *buf, size_t cap,
                       size_t *n);

@@ -61,6 +61,7 @@ struct Node {
     bool active = false;
     bool first_child_taken = false;
     uint32_t parent_off = 0, parent_cnt = 0;
+    int64_t parent_of = -1;   // last element that took this node as a parent
 };
 
 struct ArrayState {
@@ -109,6 +110,7 @@ struct Ctx {
     std::deque<Node> nodes;
     std::vector<int64_t> parent_arena;
     int64_t active_count = 0;
+    size_t trim_at = 0;  // node-table size of the next trim check
 
     std::vector<StreamState> streams;
     std::deque<int32_t> free_streams;  // empty streams, oldest first
@@ -355,11 +357,20 @@ struct Ctx {
     }
 
     // --------------------------------------------------------- tracking
+    // Every edge is logged; only an active source becomes a parent of dst.
+    // A retired one is complete and observed: it needs no wait, picks no
+    // stream and ends the retirement walk, so leaving it out of the parent
+    // list changes nothing but the list's length (which, for a writer after
+    // many readers, would otherwise grow with every read ever issued).
     void add_edge(int64_t src, int64_t dst, int32_t a, int32_t kind)
     {
         ++st.edges;
-        if (opt.record_log) edge_log.push_back(gdag_edge{src, dst, a, kind});
-        if (std::find(par.begin(), par.end(), src) == par.end()) par.push_back(src);
+        if (opt.record_log == 1) edge_log.push_back(gdag_edge{src, dst, a, kind});
+        Node *n = node(src);
+        if (n && n->active && n->parent_of != dst) {
+            n->parent_of = dst;
+            par.push_back(src);
+        }
     }
 
     // Section III-A dependency rule for element `id` with accesses acc.
@@ -388,6 +399,7 @@ struct Ctx {
     // Append the node for element `id` (after infer()).
     void push_node(int32_t kind)
     {
+        trim();
         Node nd;
         nd.kind = kind;
         nd.parent_off = (uint32_t)parent_arena.size();
@@ -395,7 +407,33 @@ struct Ctx {
         parent_arena.insert(parent_arena.end(), par.begin(), par.end());
         nodes.push_back(nd);
         ++st.nodes;
-        if (opt.record_log) node_log.push_back(gdag_node_info{next_id() - 1, kind, -1});
+        if (opt.record_log == 1) node_log.push_back(gdag_node_info{next_id() - 1, kind, -1});
+    }
+
+    // Drop the retired elements issued before the oldest active one, once
+    // the node table holds opt.trim_nodes elements.  Nothing needs them:
+    // node() of a dropped id is null, which every lookup reads as retired
+    // (complete), and the parent lists hold active nodes only.  Unless the
+    // edge log is kept, the dropped ids also leave the reader sets (each
+    // sorted by id), where they would only have produced edges to retired
+    // elements.  The next check comes when the table has grown to twice
+    // what is left, so the scans cost O(1) per element.
+    void trim(bool now = false)
+    {
+        if (opt.trace || (!now && nodes.size() < trim_at)) return;
+        size_t f = 0;
+        while (f < nodes.size() && !nodes[f].active) ++f;
+        if (f > 0) {
+            const size_t keep = f < nodes.size() ? nodes[f].parent_off : parent_arena.size();
+            parent_arena.erase(parent_arena.begin(), parent_arena.begin() + (std::ptrdiff_t)keep);
+            for (size_t i = f; i < nodes.size(); ++i) nodes[i].parent_off -= (uint32_t)keep;
+            nodes.erase(nodes.begin(), nodes.begin() + (std::ptrdiff_t)f);
+            base += (int64_t)f;
+            if (opt.record_log != 1)
+                for (auto &a : arrays)
+                    a.readers.erase(a.readers.begin(), std::lower_bound(a.readers.begin(), a.readers.end(), base));
+        }
+        trim_at = std::max((size_t)opt.trim_nodes, 2 * nodes.size());
     }
 
     // Make stream `to` wait for the work issued so far on `from`.
@@ -475,7 +513,7 @@ struct Ctx {
         ss.active++;
         ss.tail = id;
         ss.last_use = ++tick;
-        if (opt.record_log) node_log.back().stream = s;
+        if (opt.record_log == 1) node_log.back().stream = s;
         *stream_out = s;
         if (opt.trace) {
             void *e;
@@ -636,10 +674,12 @@ using gdag::LaunchArgs;
 struct gdag_ctx : Ctx {};
 
 template <class T>
-static int export_vec(gdag_ctx *c, const std::vector<T> &v, T *buf, size_t cap, size_t *n)
+static int export_vec(gdag_ctx *c, const std::vector<T> &v, T *buf, size_t cap, size_t *n, bool op_log = false)
 {
     if (!c || !n) return GDAG_ERR_INVALID;
-    if (!c->opt.record_log) return c->fail(GDAG_ERR_INVALID, "logs need options.record_log = 1");
+    if (!(c->opt.record_log == 1 || (op_log && c->opt.record_log == 2)))
+        return c->fail(GDAG_ERR_INVALID, op_log ? "the op log needs options.record_log = 1 or 2"
+                                                : "edge and element logs need options.record_log = 1");
     *n = v.size();
     if (buf)
         for (size_t i = 0; i < v.size() && i < cap; ++i) buf[i] = v[i];
@@ -660,6 +700,7 @@ void gdag_options_default(gdag_options *o)
     o->record_log = 0;
     o->trace = 0;
     o->timeout_ms = 60000;
+    o->trim_nodes = 0;
     o->fake_complete = 0;
     o->fake_fail_sticky = 0;
     o->fake_fail_op = -1;
@@ -671,7 +712,8 @@ void gdag_options_default(gdag_options *o)
     } env[] = {{"GDAG_POLICY", &o->policy},           {"GDAG_MAX_STREAMS", &o->max_streams},
                {"GDAG_PREFETCH", &o->prefetch},       {"GDAG_RETIRE_BY_QUERY", &o->retire_by_query},
                {"GDAG_RECORD_LOG", &o->record_log},   {"GDAG_TRACE", &o->trace},
-               {"GDAG_TIMEOUT_MS", &o->timeout_ms}, {"GDAG_DEVICE", &o->device}};
+               {"GDAG_TIMEOUT_MS", &o->timeout_ms}, {"GDAG_DEVICE", &o->device},
+               {"GDAG_TRIM_NODES", &o->trim_nodes}};
     for (const auto &e : env) {
         const char *v = std::getenv(e.name);
         if (!v || !*v) continue;
@@ -691,11 +733,14 @@ int gdag_create(gdag_ctx **out, const gdag_options *opts)
     else
         gdag_options_default(&o);
     if (o.policy < 0 || o.policy > 2 || o.max_streams < 1 || o.max_streams > 1024 || o.timeout_ms <= 0 ||
+        o.record_log < 0 || o.record_log > 2 || o.trim_nodes < 0 ||
         (o.backend != GDAG_BACKEND_CUDA && o.backend != GDAG_BACKEND_FAKE))
         return GDAG_ERR_INVALID;
     gdag_ctx *c = new (std::nothrow) gdag_ctx();
     if (!c) return GDAG_ERR_OOM;
     c->opt = o;
+    if (c->opt.trim_nodes == 0) c->opt.trim_nodes = 65536;
+    c->trim_at = (size_t)c->opt.trim_nodes;
     c->be.reset(o.backend == GDAG_BACKEND_FAKE
                     ? gdag::make_fake_backend(o.fake_complete, o.fake_fail_op, o.fake_fail_sticky)
                     : gdag::make_cuda_backend());
@@ -1211,22 +1256,7 @@ int gdag_sync(gdag_ctx *c)
         if (r) return r;
     }
     c->retire_all();
-    if (!c->opt.record_log && !c->opt.trace) {
-        // nothing can refer to retired nodes any more: drop them
-        c->base = c->next_id();
-        c->nodes.clear();
-        c->parent_arena.clear();
-        for (auto &a : c->arrays) {
-            // a completed whole-array prefetch leaves the view current
-            if (a.prefetch >= 0 && a.pf_writer == a.writer && a.pf_off == 0 && a.pf_bytes == a.bytes)
-                a.host_valid = true;
-            a.prefetch = -1;
-            a.writer = -1;
-            a.readers.clear();
-            a.view_copy = -1;
-        }
-        for (auto &s : c->streams) s.tail = -1;
-    }
+    c->trim(true);  // every element is retired now
     return GDAG_OK;
 }
 
@@ -1267,7 +1297,10 @@ int gdag_nodes_export(gdag_ctx *c, gdag_node_info *buf, size_t cap, size_t *n)
 {
     return export_vec(c, c->node_log, buf, cap, n);
 }
-int gdag_ops_export(gdag_ctx *c, gdag_op *buf, size_t cap, size_t *n) { return export_vec(c, c->op_log, buf, cap, n); }
+int gdag_ops_export(gdag_ctx *c, gdag_op *buf, size_t cap, size_t *n)
+{
+    return export_vec(c, c->op_log, buf, cap, n, true);
+}
 
 int gdag_trace_export(gdag_ctx *c, gdag_trace_rec *buf, size_t cap, size_t *n)
 {
@@ -1363,20 +1396,10 @@ int gdag_capture_end(gdag_ctx *c, gdag_graph *out)
     void *exec = nullptr;
     int rr = c->be->capture_end(c->cap_stream, &exec);
     c->capturing = false;
-    // nothing captured has run: the captured nodes leave the frontier
+    // nothing captured has run: the captured nodes leave the frontier (the
+    // capture began with a sync, so every element is retired now)
     c->retire_all();
-    if (!c->opt.record_log && !c->opt.trace) {
-        c->base = c->next_id();
-        c->nodes.clear();
-        c->parent_arena.clear();
-        for (auto &a : c->arrays) {
-            a.writer = -1;
-            a.readers.clear();
-            a.view_copy = -1;
-            a.prefetch = -1;
-        }
-        for (auto &st : c->streams) st.tail = -1;
-    }
+    c->trim(true);
     if (r) return r;
     if (rr) return c->be_fail(rr, "capture end");
     Ctx::Graph g;
@@ -1450,6 +1473,9 @@ int gdag_stats_get(gdag_ctx *c, gdag_stats *out)
     *out = c->st;
     out->streams = (int32_t)c->streams.size();
     out->active = (int32_t)c->active_count;
+    out->held_nodes = (int64_t)c->nodes.size();
+    out->held_readers = 0;
+    for (const auto &a : c->arrays) out->held_readers += (int64_t)a.readers.size();
     return GDAG_OK;
 }
 

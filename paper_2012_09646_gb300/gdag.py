@@ -70,7 +70,7 @@ class gdag_options(ctypes.Structure):
     _fields_ = [("policy", ctypes.c_int32), ("backend", ctypes.c_int32), ("device", ctypes.c_int32),
                 ("max_streams", ctypes.c_int32), ("prefetch", ctypes.c_int32),
                 ("retire_by_query", ctypes.c_int32), ("record_log", ctypes.c_int32),
-                ("trace", ctypes.c_int32), ("timeout_ms", ctypes.c_int32),
+                ("trace", ctypes.c_int32), ("timeout_ms", ctypes.c_int32), ("trim_nodes", ctypes.c_int32),
                 ("fake_complete", ctypes.c_int32), ("fake_fail_sticky", ctypes.c_int32),
                 ("fake_fail_op", ctypes.c_int64)]
 
@@ -107,7 +107,8 @@ class gdag_trace_rec(ctypes.Structure):
 class gdag_stats(ctypes.Structure):
     _fields_ = [("nodes", ctypes.c_int64), ("edges", ctypes.c_int64), ("waits", ctypes.c_int64),
                 ("launches", ctypes.c_int64), ("copies", ctypes.c_int64), ("host_waits", ctypes.c_int64),
-                ("streams", ctypes.c_int32), ("active", ctypes.c_int32), ("fused_members", ctypes.c_int64)]
+                ("streams", ctypes.c_int32), ("active", ctypes.c_int32), ("fused_members", ctypes.c_int64),
+                ("held_nodes", ctypes.c_int64), ("held_readers", ctypes.c_int64)]
 
 
 EXTERNAL_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
@@ -434,7 +435,7 @@ class Context:
     """One gdag context.  ``backend='fake'`` records operations only."""
 
     def __init__(self, policy=GDAG_POLICY_PARALLEL, backend="cuda", device=0, max_streams=16, prefetch=True,
-                 retire_by_query=False, record_log=False, trace=False, timeout_ms=60000,
+                 retire_by_query=False, record_log=False, trace=False, timeout_ms=60000, trim_nodes=0,
                  fake_complete=False, fake_fail_op=-1, fake_fail_sticky=False):
         o = gdag_options_default()
         o.policy = policy
@@ -446,6 +447,7 @@ class Context:
         o.record_log = int(record_log)
         o.trace = int(trace)
         o.timeout_ms = timeout_ms
+        o.trim_nodes = trim_nodes
         o.fake_complete = int(fake_complete)
         o.fake_fail_op = fake_fail_op
         o.fake_fail_sticky = int(fake_fail_sticky)
