@@ -431,8 +431,9 @@ int gdag_launch_raw(gdag_ctx *ctx, gdag_kernel k, gdag_dim3 grid,
 
 /* A library call as a DAG element (Section III-A: pre-registered library
  * functions are scheduled asynchronously when they take a stream).  fn is
- * called on the host with the chosen cudaStream_t and user; it must only
- * enqueue work on that stream.  arrays/modes give its accesses. */
+ * called once on the host with the chosen cudaStream_t and user, before this
+ * call returns (the library keeps neither afterwards); it must only enqueue
+ * work on that stream.  arrays/modes give its accesses. */
 int gdag_launch_external(gdag_ctx *ctx, void (*fn)(void *stream, void *user),
                          void *user, const gdag_array *arrays,
                          const int32_t *modes, int32_t n, int64_t *node_out);

@@ -454,7 +454,6 @@ class Context:
         self.options = o
         self.h = gdag_create(o)
         self._kernels = {}
-        self._keep = []
         self._prepared = {}  # marshalled argument arrays of repeated launches
         self._packed = {}    # packed argument bytes of repeated fused-launch members
 
@@ -623,8 +622,9 @@ class Context:
         gdag_launch_raw(self.h, kid, g, b, smem, a, stream)
 
     def external(self, fn, arrays_modes, user=None):
+        # the library calls fn before gdag_launch_external returns and keeps
+        # no reference to it, so the ctypes thunk only has to outlive the call
         cb = EXTERNAL_FN(fn)
-        self._keep.append(cb)
         return gdag_launch_external(self.h, cb, user, [a.handle for a, _ in arrays_modes],
                                     [m for _, m in arrays_modes])
 

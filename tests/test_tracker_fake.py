@@ -262,9 +262,14 @@ def test_external_call_gets_chosen_stream():
     a = ctx.array(dev=0x1000, nbytes=400)
     b = ctx.array(dev=0x2000, nbytes=400)
     ctx.launch("vec_square", a, 100)
-    node = ctx.external(lambda s, u: seen.append(s), [(a, G.GDAG_MODE_IN), (b, G.GDAG_MODE_OUT)])
-    # fake backend does not call the function; the edge is still inferred
+    node = ctx.external(lambda s, u: seen.append((s, u)), [(a, G.GDAG_MODE_IN), (b, G.GDAG_MODE_OUT)], user=7)
+    # called once, before the call returns, with a stream handle of the pool
+    assert len(seen) == 1 and seen[0][0] and seen[0][1] == 7
     assert (0, node, a.handle, G.GDAG_EDGE_RAW) in ctx.edges()
+    # the library keeps no reference to the function: many calls hold nothing
+    for _ in range(1000):
+        ctx.external(lambda s, u: seen.append(s), [(b, G.GDAG_MODE_INOUT)])
+    assert len(seen) == 1001
 
 
 def test_prefetch_then_read_copies_once():
