@@ -320,8 +320,11 @@ int gdag_array_prefetch_host(gdag_ctx *ctx, gdag_array a, size_t off,
  *                         blocks of at most 256 threads
  *  IMG   gauss_blur      (img IN f32[rows*cols], out OUT, w IN f32[2R+1],
  *                         rows i32, cols i32, R i32)    separable, clamped
+ *                         rows, cols >= 1; R 1..8
  *        sobel           (in IN, out OUT, rows i32, cols i32)    magnitude
+ *                         rows, cols >= 1
  *        minmax          (x IN f32[n], mm OUT f32[2], scratch INOUT, n i64)
+ *                         n >= 1
  *        extend          (x INOUT f32[n], mm IN f32[2], n i64)
  *                                               x := (x-min)/(max-min) or 0
  *        unsharp         (img IN, blur IN, out OUT, alpha f32, n i64)
@@ -329,14 +332,18 @@ int gdag_array_prefetch_host(gdag_ctx *ctx, gdag_array a, size_t off,
  *  ML    dense_scores    (X IN i32[rows*feats], table IN f32[feats*classes],
  *                         bias IN f32[classes], S OUT f32[rows*classes],
  *                         rows i32, feats i32, classes i32)  S = X table + b
- *                         classes 1..16, feats a multiple of 32, X 16-byte
+ *                         classes 1..16, feats a multiple of 32 with
+ *                         feats * ceil(classes/4) <= 12796 (the table is
+ *                         held in shared memory), X 16-byte
  *                         aligned; feats a multiple of 64 up to 1024 runs on
  *                         the tensor cores (exact products: X in bf16, the
  *                         table as three bf16 pieces; 128-row tiles holding
  *                         any |x| > 256 are recomputed on CUDA cores)
  *        row_softmax     (S INOUT f32[rows*classes], rows i32, classes i32)
+ *                         classes 1..32
  *        argmax_combine  (P1 IN, P2 IN, labels OUT i32[rows], rows i32,
  *                         classes i32)                 argmax(P1+P2), lowest
+ *                         classes >= 1
  *  HITS  spmv_partition  (rowptr IN i32[n+1], part OUT, n i32, nnz i32)
  *        spmv_csr        (rowptr IN, col IN i32[nnz], val IN f32[nnz],
  *                         x IN f32[n], part IN, y OUT f32[n], carry INOUT,
@@ -361,17 +368,20 @@ int gdag_array_prefetch_host(gdag_ctx *ctx, gdag_array a, size_t off,
  *                         bias IN f32[64], out OUT bf16[n*64*(h/2)*(w/2)],
  *                         status INOUT i32[1], n i32, h i32, w i32)
  *                         3x3 conv (zero pad 1) + bias + ReLU + 2x2 max-pool
- *                         on the tensor cores; h even, w a multiple of 8, x
+ *                         on the tensor cores; n >= 1, h >= 2 even, w >= 8
+ *                         a multiple of 8, x
  *                         and out 16-byte aligned; status := 1 if a tensor-core
  *                         or copy wait timed out (the output is then
  *                         incomplete), 2 if the kernel's shared-memory window
  *                         was not 128-byte aligned (nothing computed)
  *        avgpool_global  (p IN bf16[planes*hw], e OUT f32[planes],
  *                         planes i32, hw i32)               plane means
+ *                         planes, hw >= 1
  *        concat_dense    (e1 IN f32[n*c], e2 IN f32[n*c],
  *                         wd IN f32[2c*classes], bd IN f32[classes],
  *                         out OUT f32[n*classes], n i32, c i32, classes i32)
  *                                                  out = [e1 e2] wd + bd
+ *                         n, c, classes >= 1
  * Scratch and part/carry sizes come from gdag_scratch_bytes.
  * Errors: NOT_FOUND. */
 int gdag_kernel_lookup(gdag_ctx *ctx, const char *name, gdag_kernel *out);
