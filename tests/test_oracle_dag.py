@@ -104,3 +104,41 @@ def test_happens_before_rules():
     assert D.check_hb(ops, {(2, 4)}) == [(2, 4)]
     assert D.waits_off_edges(ops, {(0, 2), (1, 2)}) == []
     assert D.waits_off_edges(ops, {(1, 2)}) == [(0, 2, 5)]
+
+
+def test_hazard_labels_follow_the_textbook_classes():
+    """Between a writer and the next element that writes the same array, the
+    edge is a true (read-after-write) dependence when that element also
+    reads the array, and an output (write-after-write) dependence when it
+    only overwrites it; a reader after readers of a written value gives
+    anti (write-after-read) dependences."""
+    X = "X"
+    assert D.expected_edges([{X: D.W}, {X: D.RW}]) == {(0, 1, X, D.RAW)}
+    assert D.expected_edges([{X: D.RW}, {X: D.RW}]) == {(0, 1, X, D.RAW)}
+    assert D.expected_edges([{X: D.W}, {X: D.W}]) == {(0, 1, X, D.WAW)}
+    assert D.expected_edges([{X: D.RW}, {X: D.W}]) == {(0, 1, X, D.WAW)}
+    assert D.expected_edges([{X: D.W}, {X: D.R}, {X: D.RW}]) == {(0, 1, X, D.RAW), (1, 2, X, D.WAR)}
+
+
+def test_stream_sync_and_same_stream_waits():
+    """A STREAM_SYNC orders everything issued on its stream before what the
+    host issues next; a WAIT whose recorded parent runs on the waiting
+    stream is not a cross-stream wait along an edge."""
+    L, REC, WT, SS, H = D.OP_LAUNCH, D.OP_RECORD, D.OP_WAIT, D.OP_STREAM_SYNC, D.OP_HOST_NODE
+    ops = [
+        (L, 0, -1, 0),    # 0: node 0 on stream 0
+        (L, 1, -1, 1),    # 1: node 1 on stream 1
+        (SS, 0, -1, -1),  # 2: host syncs stream 0
+        (H, -1, -1, 2),   # 3: host node 2
+        (L, 2, -1, 3),    # 4: node 3 on stream 2
+    ]
+    anc = D.happens_before(ops)
+    hb = lambda p, q: bool((anc[q] >> p) & 1)
+    assert hb(0, 3) and hb(0, 4) and hb(2, 4)
+    assert not hb(1, 3) and not hb(1, 4)
+    assert D.check_hb(ops, {(0, 2), (0, 3)}) == []
+    assert D.check_hb(ops, {(1, 3)}) == [(1, 3)]
+    same = [(L, 0, -1, 0), (REC, 0, 5, 0), (WT, 0, 5, -1), (L, 0, -1, 1)]
+    assert D.waits_off_edges(same, {(0, 1)}) == [(0, 1, 5)]
+    cross = [(L, 0, -1, 0), (REC, 0, 5, 0), (WT, 1, 5, -1), (L, 1, -1, 1)]
+    assert D.waits_off_edges(cross, {(0, 1)}) == []

@@ -241,6 +241,11 @@ def test_spmv_matches_library_sparse():
     A = scipy.sparse.csr_matrix((val.astype(np.float64), col, rp), shape=(300, 300))
     np.testing.assert_allclose(N.spmv_csr(rp, col, val, x), A @ x, rtol=1e-14)
     np.testing.assert_allclose(N.spmv_csr_abs(rp, col, -val, x), A @ x, rtol=1e-14)
+    # the benchmark's weights are all 1: general weights, signed, as well
+    w = np.random.default_rng(1).normal(size=val.size)
+    Aw = scipy.sparse.csr_matrix((w, col, rp), shape=(300, 300))
+    np.testing.assert_allclose(N.spmv_csr(rp, col, w, x), Aw @ x, rtol=1e-12, atol=1e-12)
+    np.testing.assert_allclose(N.spmv_csr_abs(rp, col, w, x), abs(Aw) @ x, rtol=1e-12)
 
 
 def test_l2norm_and_scale():
@@ -309,3 +314,69 @@ def test_bf16_rounding_matches_torch():
     ours = datagen.to_bf16_bits(a)
     theirs = torch.from_numpy(a).to(torch.bfloat16).view(torch.int16).numpy().view(np.uint16)
     assert np.array_equal(ours, theirs)
+
+
+# ------------------------------------------------------- whole programs
+# Each benchmark program composed again from library primitives, so that the
+# wiring of the oracle's programs (which intermediate feeds which node) is
+# pinned, not only each node.  The inputs of the two branches differ, so a
+# crossed wire changes the result.
+
+def _library_conv_pool(x, wt, bias):
+    n, cin, h, w = x.shape
+    cout = wt.shape[0]
+    ref = np.zeros((n, cout, h, w))
+    for b in range(n):
+        for co in range(cout):
+            s = np.full((h, w), float(bias[co]))
+            for ci in range(cin):
+                s += scipy.signal.correlate2d(x[b, ci].astype(np.float64), wt[co, ci].astype(np.float64),
+                                              mode="same", boundary="fill", fillvalue=0.0)
+            ref[b, co] = np.maximum(s, 0.0)
+    return ref.reshape(n, cout, h // 2, 2, w // 2, 2).max(axis=(3, 5))
+
+
+def test_img_program_matches_library_composition():
+    image = datagen.image(23, 31, seed=21).astype(np.float64)
+    out = P.img(image)
+
+    def blur(R, sigma):
+        w = scipy.signal.windows.gaussian(2 * R + 1, sigma)
+        w /= w.sum()
+        return scipy.ndimage.correlate(image, np.outer(w, w), mode="nearest")
+
+    def magnitude(b):
+        return np.hypot(scipy.ndimage.sobel(b, axis=0, mode="nearest"), scipy.ndimage.sobel(b, axis=1, mode="nearest"))
+
+    b5, b9 = blur(P.IMG_R5, P.IMG_SIGMA5), blur(P.IMG_R9, P.IMG_SIGMA9)
+    e5r, e9r = magnitude(b5), magnitude(b9)
+    e5, e9 = (e5r - e5r.min()) / np.ptp(e5r), (e9r - e9r.min()) / np.ptp(e9r)
+    s = image + P.IMG_ALPHA * (image - b5)
+    final = e5 * s + (1 - e5) * (e9 * b5 + (1 - e9) * b9)
+    for key, want in (("b5", b5), ("b9", b9), ("e5_raw", e5r), ("e9_raw", e9r), ("e5", e5), ("e9", e9),
+                      ("s", s), ("out", final)):
+        np.testing.assert_allclose(np.asarray(out[key]).reshape(image.shape), want, rtol=1e-12, atol=1e-12,
+                                   err_msg=key)
+
+
+def test_ml_program_matches_library_composition():
+    X, T, p, W, b = datagen.ml_inputs(41, feats=64, classes=10, seed=22)
+    out = P.ml(X, T, p, W, b)
+    Xd = X.astype(np.float64)
+    s1, s2 = Xd @ T + p, Xd @ W + b
+    p1, p2 = scipy.special.softmax(s1, axis=1), scipy.special.softmax(s2, axis=1)
+    np.testing.assert_array_equal(out["s1"], s1)
+    np.testing.assert_array_equal(out["s2"], s2)
+    np.testing.assert_allclose(out["p1"], p1, rtol=1e-13)
+    np.testing.assert_allclose(out["p2"], p2, rtol=1e-13)
+    assert np.array_equal(out["labels"], np.argmax(p1 + p2, axis=1))
+
+
+def test_dl_program_matches_library_composition():
+    (x1, x2, w1, b1, w2, b2, wd, bd), _ = datagen.dl_inputs(n=2, h=6, w=10, cout=4, classes=3, seed=23)
+    out = P.dl(x1, x2, w1, b1, w2, b2, wd, bd)
+    p1, p2 = _library_conv_pool(x1, w1, b1), _library_conv_pool(x2, w2, b2)
+    e1, e2 = p1.mean(axis=(2, 3)), p2.mean(axis=(2, 3))
+    logits = np.concatenate([e1, e2], axis=1) @ wd.astype(np.float64) + bd
+    for key, want in (("p1", p1), ("p2", p2), ("e1", e1), ("e2", e2), ("logits", logits)):
+        np.testing.assert_allclose(out[key], want, rtol=1e-12, atol=1e-13, err_msg=key)
