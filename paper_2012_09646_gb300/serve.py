@@ -158,6 +158,7 @@ class Server:
         self.shared = {}
         self._slots = []  # pinned response buffers, reused
         self._scratch_pool = {}
+        self._need = {}  # (kind, bucket) -> working bytes
         self.partitions = {}
 
     # ---------------------------------------------------------- helpers
@@ -195,17 +196,28 @@ class Server:
         return torch.empty(RESPONSE_BYTES // 4, dtype=F32, pin_memory=self.device != "cpu")
 
     def working_bytes(self, r):
-        """Bytes of the private arrays a request will allocate."""
-        d = self.inp.data[(r.kind, self.inp.bucket(r.scale))]
-        if r.kind == "VEC":
-            return 8 * d["n"] + 4 + 16400
-        if r.kind == "B&S":
-            return 40 * d["n"]
-        if r.kind == "IMG+ML":
-            n = d["side"] ** 2
-            return 6 * 4 * n + 2 * 16400 + 80 * d["rows"] + 4 * d["rows"]
-        n, nnz = d["n"], d["nnz"]
-        return 16 * n + 8 + 2 * 8200 + 16 * (n + nnz) // 1792 + 64
+        """Bytes of the private arrays and scratch a request will allocate
+        (exactly what issue() adds up in r.bytes), per kind and bucket."""
+        key = (r.kind, self.inp.bucket(r.scale))
+        got = self._need.get(key)
+        if got is None:
+            d = self.inp.data[key]
+            S = G.gdag_scratch_bytes
+            if r.kind == "VEC":
+                n = d["n"]
+                got = 2 * 4 * n + 4 + S("vec_reduce_diff", n)           # x, y, z, scratch
+            elif r.kind == "B&S":
+                got = 10 * 4 * d["n"]                                  # ten price outputs
+            elif r.kind == "IMG+ML":
+                n, rows = d["side"] ** 2, d["rows"]
+                got = (6 * 4 * n + 2 * 8 + 2 * S("minmax", n)          # five images, output, min/max pairs
+                       + 2 * 4 * rows * 10 + 4 * rows)                 # two score tables, labels
+            else:
+                n, nnz = d["n"], d["nnz"]
+                got = (4 * 4 * n + 2 * 4 + 2 * S("l2norm", n)          # ping-pong vectors, norms
+                       + 2 * S("spmv_csr", n + nnz))                   # carries
+            self._need[key] = got
+        return got
 
     # ----------------------------------------------------------- issue
     def issue(self, r):

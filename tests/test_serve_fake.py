@@ -133,3 +133,27 @@ def test_sinks_cover_every_node_of_a_request(inputs):
         for r in g:
             srv.finish(r, 0.0)
     srv.close()
+
+
+def test_admission_charges_exactly_what_a_request_allocates(inputs):
+    """Admission adds working_bytes(r) to the budget and finish() releases
+    it: it must equal the bytes the request allocates, for every kind and
+    bucket, alone and in fused groups, so that the budget is never exceeded
+    and never held back."""
+    srv = server(inputs)
+    for s in SCALES:
+        for kind in SV.KINDS:
+            r = SV.Request(0, kind, s, 0.0)
+            srv.issue(r)
+            assert r.bytes == srv.working_bytes(r), (kind, s)
+            srv.ctx.sync()
+            srv.finish(r, 0.0)
+    for kind in ("VEC", "B&S"):
+        g = [SV.Request(i, kind, SCALES[i % 2], 0.0) for i in range(4)]
+        srv.fuse_max = {kind: 1 << 30}
+        srv.issue_batch(g)
+        assert all(r.bytes == srv.working_bytes(r) for r in g), kind
+        srv.ctx.sync()
+        for r in g:
+            srv.finish(r, 0.0)
+    srv.close()
