@@ -1174,6 +1174,9 @@ def main():
         return
     from paper_2012_09646_gb300 import replicas as RP
     rank, world, local_rank = RP.rank_env()
+    # timed numbers follow at least three untimed warm-up steps; the JSON
+    # line reports the count actually run
+    args.warmup = max(3, args.warmup)
     if args.impl == "reference":
         run_reference(args, rank)
         return
