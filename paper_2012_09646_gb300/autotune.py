@@ -33,17 +33,22 @@ _CACHE = {}
 
 
 class History:
-    """Durations (ms) per (kernel name, launch shape) from traced contexts."""
+    """Durations (ms) per (kernel name, launch shape) from traced contexts,
+    the most recent ``keep`` per key (a ring: a long-running process holds
+    a bounded history, and old samples age out as conditions change)."""
 
-    def __init__(self):
-        self.samples = collections.defaultdict(list)
+    def __init__(self, keep=256):
+        self.samples = collections.defaultdict(lambda: collections.deque(maxlen=keep))
+
+    def add(self, key, ms):
+        self.samples[key].append(ms)
 
     def add_trace(self, ctx, names):
         """``names``: node id -> (kernel name, shape key) for the nodes of
         interest; trace records of other nodes are ignored."""
         for node, _kind, _stream, t0, t1 in ctx.trace():
             if node in names:
-                self.samples[names[node]].append(t1 - t0)
+                self.add(names[node], t1 - t0)
 
     def median(self, key):
         s = self.samples.get(key)

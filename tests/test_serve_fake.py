@@ -157,3 +157,26 @@ def test_admission_charges_exactly_what_a_request_allocates(inputs):
         for r in g:
             srv.finish(r, 0.0)
     srv.close()
+
+
+def test_budget_is_exceeded_only_by_a_request_admitted_alone(inputs):
+    """Under a budget a few requests wide, the bytes admitted never exceed
+    it, except by a single request admitted while nothing else is in flight
+    (which must run for the queue to make progress)."""
+    reqs = SV.poisson_requests(rate=200_000.0, count=60, scales=SCALES, seed=6)
+    srv = server(inputs, budget_bytes=40_000_000)
+    seen = []
+    issue_batch = srv.issue_batch
+
+    def watched(batch):
+        inflight_before = srv.used - sum(r.need for r in batch)
+        seen.append((srv.used, inflight_before, len(batch)))
+        issue_batch(batch)
+    srv.issue_batch = watched
+    out = srv.run(fresh(reqs))
+    assert all(r.done_at is not None for r in out)
+    assert len(seen) > 1
+    for used, before, n in seen:
+        assert used <= srv.budget or (before == 0 and n == 1), (used, before, n)
+    assert srv.used == 0
+    srv.close()
