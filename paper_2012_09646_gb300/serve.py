@@ -122,8 +122,11 @@ class Inputs:
 
 
 class Request:
+    """One DAG submission.  ``done_at`` is set when it completes or fails;
+    ``error`` is then None or the GdagError that failed it."""
+
     __slots__ = ("rid", "kind", "scale", "arrival", "admitted", "done_at", "bytes", "sinks", "tensors", "arrays",
-                 "resp", "resp_view", "slot", "scratch", "need")
+                 "resp", "resp_view", "slot", "scratch", "need", "error")
 
     def __init__(self, rid, kind, scale, arrival):
         self.rid, self.kind, self.scale, self.arrival = rid, kind, scale, arrival
@@ -136,25 +139,28 @@ class Request:
         self.slot = None
         self.scratch = []
         self.need = 0
+        self.error = None
 
 
 class Server:
     """One gdag context shared by every request."""
 
     def __init__(self, inputs, budget_bytes=40 << 30, max_streams=32, device="cuda", fuse_max=None, backend="cuda",
-                 record_log=False):
+                 record_log=False, fake_fail_op=-1, fake_fail_sticky=False):
         """``fuse_max``: {kind: largest node size (elements) that is fused
         across requests}; None or {} turns fusion off.  ``backend="fake"``
         (with ``device="cpu"``) runs the dispatcher on the recording backend:
         admission, batching and bookkeeping without a GPU (every node
-        reports complete when queried; nothing is computed)."""
+        reports complete when queried; nothing is computed), and
+        ``fake_fail_op`` / ``fake_fail_sticky`` inject a failure there."""
         self.inp = inputs
         self.fuse_max = dict(fuse_max or {})
         self.budget = budget_bytes
         self.used = 0
         self.device = device
         self.ctx = G.Context(max_streams=max_streams, retire_by_query=True, backend=backend,
-                             fake_complete=backend == "fake", record_log=record_log)
+                             fake_complete=backend == "fake", record_log=record_log,
+                             fake_fail_op=fake_fail_op, fake_fail_sticky=fake_fail_sticky)
         self.shared = {}
         self._slots = []  # pinned response buffers, reused
         self._scratch_pool = {}
@@ -328,18 +334,33 @@ class Server:
     def issue_batch(self, rs):
         """Issue the requests admitted in one pass: fusable VEC and B&S
         requests as fused groups (when two or more share a kind), the rest
-        one by one."""
+        one by one.  A call that fails fails the requests it was issuing
+        (all members of a fused group) and no others."""
         groups = {"VEC": [], "B&S": []}
         for r in rs:
             if self._fusable(r):
                 groups[r.kind].append(r)
             else:
-                self.issue(r)
+                self._guarded([r], self.issue, r)
         for kind, g in groups.items():
             if len(g) == 1:
-                self.issue(g[0])
+                self._guarded(g, self.issue, g[0])
             elif g:
-                (self._issue_vec_group if kind == "VEC" else self._issue_bs_group)(g)
+                self._guarded(g, self._issue_vec_group if kind == "VEC" else self._issue_bs_group, g)
+
+    def _guarded(self, rs, fn, arg):
+        """fn(arg); on a library error the requests `rs` fail: they get no
+        sinks, so the dispatcher finishes them at once (finish() releases
+        what they hold).  An error that poisoned the context is raised:
+        nothing further can run on it."""
+        try:
+            fn(arg)
+        except G.GdagError as e:
+            if e.code == G.GDAG_ERR_POISONED:
+                raise
+            for r in rs:
+                r.error = e
+                r.sinks = []
 
     def _issue_vec_group(self, g):
         c = self.ctx
@@ -419,18 +440,25 @@ class Server:
 
     # ------------------------------------------------------------ finish
     def finish(self, r, now):
-        arr, nb = r.resp
-        self.ctx.read(arr, None, 0, nb)  # served from the completed prefetch
+        if r.error is None:
+            arr, nb = r.resp
+            self.ctx.read(arr, None, 0, nb)  # served from the completed prefetch
+            r.resp_view = r.slot[: nb // 4].clone() if nb >= 4 else None
         r.done_at = now
-        r.resp_view = r.slot[: nb // 4].clone() if nb >= 4 else None
+        # unregistering waits for the request's elements that use an array,
+        # also those a failed request had issued before its error
         for a in r.arrays:
             self.ctx.unregister(a)
         r.arrays.clear()
         r.tensors.clear()
         for nbytes, t, a in r.scratch:
-            self._scratch_pool[nbytes].append((t, a))
+            if r.error is None:
+                self._scratch_pool[nbytes].append((t, a))
+            else:  # a failed reduction may have left its counter nonzero
+                self.ctx.unregister(a)
         r.scratch.clear()
-        self._slots.append(r.slot)
+        if r.slot is not None:
+            self._slots.append(r.slot)
         r.slot = None
         self.used -= r.need
 
@@ -507,11 +535,14 @@ def poisson_requests(rate, count, scales, seed=0, kinds=KINDS):
 
 
 def latency_summary(reqs):
+    failed = sum(r.error is not None for r in reqs)
+    reqs = [r for r in reqs if r.error is None]
     lat = np.array([(r.done_at - r.arrival) * 1e3 for r in reqs])
     span = max(r.done_at for r in reqs) - min(r.arrival for r in reqs)
     by = {}
     for k in sorted({r.kind for r in reqs}):
         l = np.array([(r.done_at - r.arrival) * 1e3 for r in reqs if r.kind == k])
         by[k] = {"n": int(l.size), "p50_ms": float(np.percentile(l, 50)), "p99_ms": float(np.percentile(l, 99))}
-    return {"requests": len(reqs), "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+    return {"requests": len(reqs), "failed": failed,
+            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
             "mean_ms": float(lat.mean()), "throughput_req_s": len(reqs) / span, "by_kind": by}

@@ -180,3 +180,58 @@ def test_budget_is_exceeded_only_by_a_request_admitted_alone(inputs):
         assert used <= srv.budget or (before == 0 and n == 1), (used, before, n)
     assert srv.used == 0
     srv.close()
+
+
+def _warm_ops(inputs):
+    """Backend operations the server issues before serving (warm-up)."""
+    from tests.test_tracker_fake import BACKEND_OPS
+    ref = server(inputs, record_log=True)
+    n = sum(1 for o in ref.ctx.ops() if o[0] in BACKEND_OPS)
+    ref.close()
+    return n
+
+
+def test_a_failed_request_fails_alone(inputs):
+    """A backend operation that fails (not sticky) while a request is being
+    issued fails that request only: it finishes at once with the error, its
+    memory is released, and every other request is served."""
+    from paper_2012_09646_gb300 import gdag as G
+    w = _warm_ops(inputs)
+    reqs = SV.poisson_requests(rate=50_000.0, count=40, scales=SCALES, seed=7)
+    for k in (w, w + 37, w + 150, w + 400):
+        srv = server(inputs, fake_fail_op=k)
+        out = srv.run(fresh(reqs))
+        failed = [r for r in out if r.error is not None]
+        assert len(failed) == 1, k
+        assert failed[0].error.code == G.GDAG_ERR_CUDA
+        assert all(r.done_at is not None for r in out)
+        assert all(r.resp_view is not None for r in out if r.error is None and r.kind != "VEC")
+        assert srv.used == 0 and not srv.ctx.stats()["active"]
+        s = SV.latency_summary(out)
+        assert s["requests"] == len(out) - 1 and s["failed"] == 1
+        srv.close()
+
+
+def test_a_fused_group_fails_together(inputs):
+    from paper_2012_09646_gb300 import gdag as G
+    w = _warm_ops(inputs)
+    burst = [SV.Request(i, "B&S", SCALES[i % 2], 0.0) for i in range(5)]
+    srv = server(inputs, fuse_max={"B&S": 1 << 30}, fake_fail_op=w)  # the group's fused launch
+    out = srv.run(burst)
+    assert all(r.error is not None and r.error.code == G.GDAG_ERR_CUDA for r in out)
+    assert srv.used == 0
+    # the server goes on serving
+    more = srv.run([SV.Request(9, "VEC", SCALES[0], 0.0)])
+    assert more[0].error is None and more[0].done_at is not None
+    srv.close()
+
+
+def test_a_context_losing_failure_stops_the_server(inputs):
+    from paper_2012_09646_gb300 import gdag as G
+    w = _warm_ops(inputs)
+    reqs = SV.poisson_requests(rate=50_000.0, count=20, scales=SCALES, seed=8)
+    srv = server(inputs, fake_fail_op=w + 10, fake_fail_sticky=True)
+    with pytest.raises(G.GdagError) as e:
+        srv.run(fresh(reqs))
+    assert e.value.code == G.GDAG_ERR_POISONED
+    srv.ctx.close()
