@@ -146,21 +146,28 @@ class Server:
     """One gdag context shared by every request."""
 
     def __init__(self, inputs, budget_bytes=40 << 30, max_streams=32, device="cuda", fuse_max=None, backend="cuda",
-                 record_log=False, fake_fail_op=-1, fake_fail_sticky=False):
+                 record_log=False, fake_fail_op=-1, fake_fail_sticky=False, fake_complete=None,
+                 request_timeout_s=120.0):
         """``fuse_max``: {kind: largest node size (elements) that is fused
         across requests}; None or {} turns fusion off.  ``backend="fake"``
         (with ``device="cpu"``) runs the dispatcher on the recording backend:
         admission, batching and bookkeeping without a GPU (every node
         reports complete when queried; nothing is computed), and
-        ``fake_fail_op`` / ``fake_fail_sticky`` inject a failure there."""
+        ``fake_fail_op`` / ``fake_fail_sticky`` / ``fake_complete`` inject
+        a failure or a device that never completes there.
+        ``request_timeout_s``: a request still incomplete this long after
+        its admission means the device has stopped making progress; run()
+        then raises GDAG_ERR_TIMEOUT instead of polling forever (None: no
+        limit)."""
         self.inp = inputs
         self.fuse_max = dict(fuse_max or {})
         self.budget = budget_bytes
         self.used = 0
         self.device = device
         self.ctx = G.Context(max_streams=max_streams, retire_by_query=True, backend=backend,
-                             fake_complete=backend == "fake", record_log=record_log,
-                             fake_fail_op=fake_fail_op, fake_fail_sticky=fake_fail_sticky)
+                             fake_complete=(backend == "fake") if fake_complete is None else fake_complete,
+                             record_log=record_log, fake_fail_op=fake_fail_op, fake_fail_sticky=fake_fail_sticky)
+        self.request_timeout_s = request_timeout_s
         self.shared = {}
         self._slots = []  # pinned response buffers, reused
         self._scratch_pool = {}
@@ -508,6 +515,12 @@ class Server:
                 else:
                     still.append(r)
             inflight = still
+            if inflight and self.request_timeout_s is not None:
+                late = clock() - t0 - self.request_timeout_s
+                for r in inflight:
+                    if r.admitted < late:
+                        raise G.GdagError(G.GDAG_ERR_TIMEOUT, "request %d (%s) incomplete %.1f s after admission"
+                                          % (r.rid, r.kind, self.request_timeout_s))
             if not inflight and not pending and i < len(requests):
                 # idle until the next arrival
                 wait = requests[i].arrival - (clock() - t0)

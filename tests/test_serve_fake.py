@@ -235,3 +235,20 @@ def test_a_context_losing_failure_stops_the_server(inputs):
         srv.run(fresh(reqs))
     assert e.value.code == G.GDAG_ERR_POISONED
     srv.ctx.close()
+
+
+def test_a_device_that_stops_completing_times_out(inputs):
+    """Nodes that never report complete (the recording backend completes
+    them only on a host wait, which the dispatcher never issues): run()
+    raises GDAG_ERR_TIMEOUT after the request deadline instead of polling
+    forever."""
+    import time
+    from paper_2012_09646_gb300 import gdag as G
+    reqs = SV.poisson_requests(rate=50_000.0, count=5, scales=SCALES, seed=9)
+    srv = server(inputs, fake_complete=0, request_timeout_s=0.2)
+    t = time.perf_counter()
+    with pytest.raises(G.GdagError) as e:
+        srv.run(fresh(reqs))
+    assert e.value.code == G.GDAG_ERR_TIMEOUT
+    assert time.perf_counter() - t < 10
+    srv.close()
