@@ -220,7 +220,8 @@ typedef struct {
 /* Fill *o with the defaults listed in gdag_options, then apply environment
  * overrides where set to an integer: GDAG_POLICY, GDAG_MAX_STREAMS,
  * GDAG_PREFETCH, GDAG_RETIRE_BY_QUERY, GDAG_RECORD_LOG, GDAG_TRACE,
- * GDAG_TIMEOUT_MS, GDAG_DEVICE (a caller may still change any field before
+ * GDAG_TIMEOUT_MS, GDAG_DEVICE, GDAG_TRIM_NODES (a caller may still change
+ * any field before
  * gdag_create, which validates them). */
 void gdag_options_default(gdag_options *o);
 
