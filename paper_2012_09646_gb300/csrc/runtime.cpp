@@ -111,6 +111,7 @@ struct Ctx {
     std::vector<int64_t> parent_arena;
     int64_t active_count = 0;
     size_t trim_at = 0;  // node-table size of the next trim check
+    int64_t reader_entries = 0;  // sum of the arrays' reader-set sizes
 
     std::vector<StreamState> streams;
     std::deque<int32_t> free_streams;  // empty streams, oldest first
@@ -383,6 +384,7 @@ struct Ctx {
             if (!(bits & W_BIT)) {
                 if (s.writer >= 0) add_edge(s.writer, id, acc[i].array, GDAG_EDGE_RAW);
                 s.readers.push_back(id);
+                ++reader_entries;
             } else {
                 if (!s.readers.empty()) {
                     for (int64_t r : s.readers) add_edge(r, id, acc[i].array, GDAG_EDGE_WAR);
@@ -390,6 +392,7 @@ struct Ctx {
                     add_edge(s.writer, id, acc[i].array, (bits & R_BIT) ? GDAG_EDGE_RAW : GDAG_EDGE_WAW);
                 }
                 s.writer = id;
+                reader_entries -= (int64_t)s.readers.size();
                 s.readers.clear();
             }
         }
@@ -430,8 +433,11 @@ struct Ctx {
             nodes.erase(nodes.begin(), nodes.begin() + (std::ptrdiff_t)f);
             base += (int64_t)f;
             if (opt.record_log != 1)
-                for (auto &a : arrays)
-                    a.readers.erase(a.readers.begin(), std::lower_bound(a.readers.begin(), a.readers.end(), base));
+                for (auto &a : arrays) {
+                    auto keep = std::lower_bound(a.readers.begin(), a.readers.end(), base);
+                    reader_entries -= (int64_t)(keep - a.readers.begin());
+                    a.readers.erase(a.readers.begin(), keep);
+                }
         }
         trim_at = std::max((size_t)opt.trim_nodes, 2 * nodes.size());
     }
@@ -836,6 +842,7 @@ int gdag_array_unregister(gdag_ctx *c, gdag_array a)
         if (r) return r;
     }
     if (s->host_owned) c->be->host_free(s->host);
+    c->reader_entries -= (int64_t)s->readers.size();
     *s = ArrayState();
     c->free_arrays.push_back(a);
     return GDAG_OK;
@@ -1474,8 +1481,7 @@ int gdag_stats_get(gdag_ctx *c, gdag_stats *out)
     out->streams = (int32_t)c->streams.size();
     out->active = (int32_t)c->active_count;
     out->held_nodes = (int64_t)c->nodes.size();
-    out->held_readers = 0;
-    for (const auto &a : c->arrays) out->held_readers += (int64_t)a.readers.size();
+    out->held_readers = c->reader_entries;
     return GDAG_OK;
 }
 

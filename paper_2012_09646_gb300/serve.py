@@ -147,7 +147,7 @@ class Server:
 
     def __init__(self, inputs, budget_bytes=40 << 30, max_streams=32, device="cuda", fuse_max=None, backend="cuda",
                  record_log=False, fake_fail_op=-1, fake_fail_sticky=False, fake_complete=None,
-                 request_timeout_s=120.0):
+                 request_timeout_s=120.0, trim_nodes=0):
         """``fuse_max``: {kind: largest node size (elements) that is fused
         across requests}; None or {} turns fusion off.  ``backend="fake"``
         (with ``device="cpu"``) runs the dispatcher on the recording backend:
@@ -158,7 +158,8 @@ class Server:
         ``request_timeout_s``: a request still incomplete this long after
         its admission means the device has stopped making progress; run()
         then raises GDAG_ERR_TIMEOUT instead of polling forever (None: no
-        limit)."""
+        limit).  ``trim_nodes``: the context's node-table threshold for
+        dropping retired elements (0: the library default)."""
         self.inp = inputs
         self.fuse_max = dict(fuse_max or {})
         self.budget = budget_bytes
@@ -166,7 +167,8 @@ class Server:
         self.device = device
         self.ctx = G.Context(max_streams=max_streams, retire_by_query=True, backend=backend,
                              fake_complete=(backend == "fake") if fake_complete is None else fake_complete,
-                             record_log=record_log, fake_fail_op=fake_fail_op, fake_fail_sticky=fake_fail_sticky)
+                             record_log=record_log, fake_fail_op=fake_fail_op, fake_fail_sticky=fake_fail_sticky,
+                             trim_nodes=trim_nodes)
         self.request_timeout_s = request_timeout_s
         self.shared = {}
         self._slots = []  # pinned response buffers, reused

@@ -252,3 +252,30 @@ def test_a_device_that_stops_completing_times_out(inputs):
     assert e.value.code == G.GDAG_ERR_TIMEOUT
     assert time.perf_counter() - t < 10
     srv.close()
+
+
+def test_a_long_serving_run_holds_a_bounded_node_table(inputs):
+    """The dispatcher never calls gdag_sync while serving, yet the context
+    holds only its active window, not every element of every request
+    served: a budget ten requests wide keeps at most ten in flight, and the
+    node table and the shared inputs' reader sets stay within twice the
+    trim threshold over 4000 requests."""
+    n, trim = 4000, 1024
+    reqs = [SV.Request(i, "VEC", SCALES[0], 0.0) for i in range(n)]
+    srv = server(inputs, trim_nodes=trim)
+    srv.budget = 10 * srv.working_bytes(reqs[0])
+    peak = [0, 0]
+    issue_batch = srv.issue_batch
+
+    def watched(batch):
+        issue_batch(batch)
+        st = srv.ctx.stats()
+        peak[0] = max(peak[0], st["held_nodes"])
+        peak[1] = max(peak[1], st["held_readers"])
+    srv.issue_batch = watched
+    srv.run(reqs)
+    st = srv.ctx.stats()
+    assert st["nodes"] > 10 * trim  # far more elements than the table keeps
+    assert peak[0] <= 2 * trim and peak[1] <= 2 * trim, peak
+    assert all(r.error is None for r in reqs)
+    srv.close()

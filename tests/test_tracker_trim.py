@@ -145,8 +145,16 @@ def test_trimming_changes_no_backend_operation(seed):
     s_ref, s_full, s_lean = ref.stats(), full.stats(), lean.stats()
     assert all(s_full[k] == s_ref[k] and s_lean[k] == s_ref[k] for k in keys)
     assert s_full["edges"] == s_ref["edges"]
+    # reader sets: kept whole with the full logs, pruned with the op log only
+    assert s_full["held_readers"] == s_ref["held_readers"]
+    assert s_lean["held_readers"] <= s_ref["held_readers"]
     for c in (ref, full, lean):
         c.sync()
+    # after a sync every element is retired: the op-log-only context drops
+    # them all, and its running reader count returns to exactly zero
+    assert lean.stats()["held_nodes"] == 0 and lean.stats()["held_readers"] == 0
+    assert full.stats()["held_nodes"] == 0
+    for c in (ref, full, lean):
         c.close()
 
 
