@@ -451,7 +451,10 @@ int gdag_launch_external(gdag_ctx *ctx, void (*fn)(void *stream, void *user),
 
 /* ----------------------------------------------------------------- sync */
 
-/* Wait for every stream (bounded) and retire every node. */
+/* Wait for every stream (bounded) and retire every node; the retired nodes
+ * then leave the node table (unless options.trace = 1) as under trim_nodes,
+ * which changes no later dependency or wait.  Errors: TIMEOUT (a stream did
+ * not finish within timeout_ms), POISONED, INVALID while capturing. */
 int gdag_sync(gdag_ctx *ctx);
 
 /* Non-blocking: *done = 1 if node's work has completed (it and its
