@@ -82,10 +82,12 @@ int main(int argc, char **argv)
             const uint32_t r = rnd(100);
             int64_t node = -1;
             ++calls;
+            unsigned char hostbuf[NB];  /* a caller buffer of exactly `bytes` bytes is enough */
+            for (size_t k = 0; k < bytes; ++k) hostbuf[k] = (unsigned char)(s + k);
             if (r < 10) {
-                gdag_array_write(c, arr[a], NULL, off, bytes);
+                gdag_array_write(c, arr[a], rnd(2) ? hostbuf : NULL, off, bytes);
             } else if (r < 18) {
-                gdag_array_read(c, arr[a], NULL, off, bytes);
+                gdag_array_read(c, arr[a], rnd(2) ? hostbuf : NULL, off, bytes);
             } else if (r < 23) {
                 gdag_array_prefetch_host(c, arr[a], off, bytes);
             } else if (r < 28 && na > 1) {
