@@ -68,6 +68,13 @@ def contracts():
     }
 
 
+# the built-in kernels, listed here so that collecting these tests loads no
+# library (the table itself asks the library for scratch sizes)
+NAMES = ["argmax_combine", "avgpool_global", "bs_call", "combine", "concat_dense", "conv3x3_relu_pool",
+         "dense_scores", "extend", "gauss_blur", "l2norm", "minmax", "row_softmax", "scale", "seg_l2norm",
+         "seg_scale", "sobel", "spmv_csr", "spmv_partition", "unsharp", "vec_reduce_diff", "vec_square"]
+
+
 def issue(ctx, name, args, shrink=None):
     """Register each array at its documented size (for argument `shrink`,
     one byte less, or half for a gdag_scratch_bytes size) at a 256-byte
@@ -82,7 +89,7 @@ def issue(ctx, name, args, shrink=None):
     return ctx.launch(name, *vals)
 
 
-@pytest.mark.parametrize("name", sorted(contracts()))
+@pytest.mark.parametrize("name", NAMES)
 def test_documented_modes(name):
     ctx = G.Context(backend="fake")
     _, spec = ctx.kernel(name)
@@ -96,7 +103,7 @@ def test_documented_modes(name):
     ctx.close()
 
 
-@pytest.mark.parametrize("name", sorted(contracts()))
+@pytest.mark.parametrize("name", NAMES)
 def test_documented_sizes_are_exactly_enough(name):
     args = contracts()[name]
     ctx = G.Context(backend="fake", record_log=True)
@@ -116,6 +123,7 @@ def test_documented_sizes_are_exactly_enough(name):
 
 def test_every_builtin_kernel_has_a_contract():
     """The table above covers the whole built-in kernel table."""
+    assert sorted(contracts()) == NAMES
     ctx = G.Context(backend="fake")
     for name in contracts():
         ctx.kernel(name)
