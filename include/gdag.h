@@ -542,16 +542,23 @@ size_t gdag_scratch_bytes(const char *kernel, int64_t n);
  * the process exits.  No cudaMalloc, cudaFree or allocating library routine
  * is called.
  *   - The first call on a device (with that device current) looks up the
- *     array's device address and zeroes it; make that first call before any
- *     stream capture on the device.
+ *     array's device address and keeps it for the life of the process; make
+ *     that first call before any stream capture on the device.  It issues no
+ *     GPU work: every call enqueues only on the caller's stream (a clear of
+ *     the arrival counter, then the kernel), so the first call is ordered
+ *     like any other, on blocking and non-blocking streams alike.
+ *   - The cached address is not refreshed: do not call this entry point on a
+ *     device after cudaDeviceReset() on it in the same process.
  *   - Every call shares the one array per device and leaves the last call's
  *     partial sums in it; each call clears the counter it needs on its own
- *     stream first.  Calls whose kernels overlap on the GPU (different
- *     streams, or different host threads, without ordering) race on the
- *     array: order them on one stream or with events.
- *   - The array holds 1024 partial sums, the most any launch of this
- *     reduction uses (its grid is capped at 1024 blocks); a request that
- *     would need more, a negative n, or a NULL pointer is rejected with
+ *     stream first, and every partial sum is written before it is read.
+ *     Calls whose kernels overlap on the GPU (different streams, or
+ *     different host threads, without ordering) race on the array: order
+ *     them on one stream or with events.
+ *   - The array holds 1024 partial sums and the counter, the most any launch
+ *     of this reduction uses: its grid is capped at 1024 blocks whatever n
+ *     is, and a compile-time check ties the array's size to that cap, so no
+ *     size is too large.  A negative n, or a NULL pointer, is rejected with
  *     GDAG_ERR_INVALID before anything is enqueued.
  *   - Returns GDAG_ERR_CUDA if the set-up or the launch fails. */
 #define GDAG_NOALLOC_SCRATCH_BYTES 16384

@@ -37,7 +37,11 @@ std::mutex g_mu;
 void *g_addr[kMaxDevices];  // device address of g_noalloc_scratch, per device
 
 // Set-up, once per device, with that device current: look up the array's
-// device address and zero it.
+// device address.  Nothing is written to the array here: the partial sums are
+// written by every launch before they are read, and the arrival counter is
+// cleared on the caller's stream by every call, so no work is issued outside
+// the caller's stream (a memset on the legacy default stream would not be
+// ordered before a non-blocking caller stream).
 int scratch_for_current_device(double **out)
 {
     int dev = 0;
@@ -46,10 +50,6 @@ int scratch_for_current_device(double **out)
     if (!g_addr[dev]) {
         void *p = nullptr;
         if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
-            (void)cudaGetLastError();
-            return GDAG_ERR_CUDA;
-        }
-        if (cudaMemset(p, 0, kNoallocBytes) != cudaSuccess) {
             (void)cudaGetLastError();
             return GDAG_ERR_CUDA;
         }
@@ -67,9 +67,10 @@ extern "C" int gdag_vec_reduce_diff_noalloc(const void *dev_x, const void *dev_y
 {
     using namespace gdag;
     if (n < 0 || (n > 0 && (!dev_x || !dev_y)) || !dev_z) return GDAG_ERR_INVALID;
+    // reduce_grid() caps the grid at kReduceMaxBlocks, and the static_assert
+    // above makes the array hold that many partial sums plus the counter, so
+    // no n can need more scratch than the array has.
     const unsigned grid = reduce_grid(n >> 2);
-    // the array holds kReduceMaxBlocks partial sums and the counter
-    if (grid > (unsigned)kReduceMaxBlocks || reduce_scratch_bytes<1>() > kNoallocBytes) return GDAG_ERR_INVALID;
     double *scratch = nullptr;
     int r = scratch_for_current_device(&scratch);
     if (r) return r;
