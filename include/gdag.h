@@ -449,6 +449,53 @@ int gdag_launch_external(gdag_ctx *ctx, void (*fn)(void *stream, void *user),
                          void *user, const gdag_array *arrays,
                          const int32_t *modes, int32_t n, int64_t *node_out);
 
+/* ------------------------------------------------------ batched issue
+ * Section III-B: the runtime sees a program as a stream of element
+ * requests, and the host-side cost of each sits on the critical path of
+ * short DAGs (the comparison with CUDA Graphs, Section IV-D, finds the
+ * runtime's overhead negligible only for computations longer than a few
+ * milliseconds).  gdag_issue takes several consecutive
+ * non-blocking elements of a program in one call; element i is inferred,
+ * placed and issued exactly as its own call would be (gdag_launch,
+ * gdag_launch_fused, gdag_array_write with src NULL, or
+ * gdag_array_prefetch_host), in order, so the DAG, the streams, the waits
+ * and the results are those of the single calls.                         */
+#define GDAG_ELEM_LAUNCH        0  /* gdag_launch                            */
+#define GDAG_ELEM_LAUNCH_FUSED  1  /* gdag_launch_fused                      */
+#define GDAG_ELEM_WRITE         2  /* gdag_array_write(a, NULL, off, bytes):
+                                      the host view already holds the data  */
+#define GDAG_ELEM_PREFETCH_HOST 3  /* gdag_array_prefetch_host(a, off, bytes) */
+typedef struct {
+    int32_t type;     /* GDAG_ELEM_*                                         */
+    int32_t kernel;   /* LAUNCH, LAUNCH_FUSED: kernel handle                 */
+    int32_t array;    /* WRITE, PREFETCH_HOST: array handle                  */
+    int32_t nargs;    /* LAUNCH: arguments; LAUNCH_FUSED: arguments per member */
+    int32_t count;    /* LAUNCH_FUSED: members (args holds count * nargs)    */
+    uint32_t smem;    /* LAUNCH: dynamic shared memory, bytes                */
+    int64_t arg0;     /* LAUNCH, LAUNCH_FUSED: index in args of the first one */
+    uint64_t off;     /* WRITE, PREFETCH_HOST: byte offset                   */
+    uint64_t bytes;   /* WRITE, PREFETCH_HOST: byte count                    */
+    gdag_dim3 grid;   /* LAUNCH: {0,0,0} = the kernel's automatic shape      */
+    gdag_dim3 block;  /* LAUNCH                                              */
+} gdag_elem;
+
+/* Issue elems[0..n) in order.  args holds nargs_total gdag_arg entries that
+ * the launch elements index (arg0 .. arg0 + nargs*count - 1 must lie inside
+ * it).  nodes_out (may be NULL) receives each element's node id, or -1 for
+ * an element that made no node (a prefetch of a view that is already
+ * current, or an element not issued).  *issued (may be NULL) receives the
+ * number of elements handled before the first failure (n on success).  On
+ * a failure the call returns that element's error at once: the elements
+ * before it stay issued, the failing one behaves as its single call does
+ * on that error, and the ones after it are not issued.  Never blocks the
+ * host except where a single call would (policy SERIAL_SYNC, prefetch = 0,
+ * both staging uses of a view in flight).  Errors: INVALID (an element
+ * type, index range, or anything its single call rejects), CUDA, TIMEOUT,
+ * POISONED. */
+int gdag_issue(gdag_ctx *ctx, const gdag_elem *elems, int32_t n,
+               const gdag_arg *args, int64_t nargs_total, int64_t *nodes_out,
+               int32_t *issued);
+
 /* ----------------------------------------------------------------- sync */
 
 /* Wait for every stream (bounded) and retire every node; the retired nodes
@@ -463,6 +510,13 @@ int gdag_sync(gdag_ctx *ctx);
  * any (Section III-B: results become available when the host asks).
  * Errors: INVALID (unknown node, or while capturing), CUDA. */
 int gdag_node_query(gdag_ctx *ctx, int64_t node, int32_t *done);
+
+/* gdag_node_query for nodes[0..n): done[i] receives node i's completion
+ * flag.  One call lets a dispatcher poll every in-flight DAG without a host
+ * round trip per node.  Errors: as gdag_node_query, for the first failing
+ * node (later flags are then unset). */
+int gdag_nodes_query(gdag_ctx *ctx, const int64_t *nodes, int32_t n,
+                     int32_t *done);
 
 /* Make the caller's CUDA stream wait for all work issued so far, without
  * blocking the host (a join for timing events or stream capture). */

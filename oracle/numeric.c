@@ -144,6 +144,29 @@ void orc_sobel(const double *in, double *out, int64_t rows, int64_t cols)
         }
 }
 
+/* Condition scale of the Sobel magnitude at each pixel: the sum of the
+ * absolute values of the terms of both gradients, sum |Kx v| + sum |Ky v|
+ * over the clamped 3x3 window.  A rounding error of a few units in the last
+ * place of each term bounds the error of gx and gy, and so of
+ * sqrt(gx^2 + gy^2), by a small multiple of this scale (the reading used for
+ * every sum of terms of mixed sign).                                      */
+void orc_sobel_scale(const double *in, double *out, int64_t rows, int64_t cols)
+{
+    static const double Kx[3][3] = {{-1, 0, 1}, {-2, 0, 2}, {-1, 0, 1}};
+    for (int64_t r = 0; r < rows; ++r)
+        for (int64_t c = 0; c < cols; ++c) {
+            double sx = 0.0, sy = 0.0;
+            for (int i = -1; i <= 1; ++i)
+                for (int j = -1; j <= 1; ++j) {
+                    double v = in[clampi(r + i, 0, rows - 1) * cols
+                                  + clampi(c + j, 0, cols - 1)];
+                    sx += fabs(Kx[i + 1][j + 1] * v);
+                    sy += fabs(Kx[j + 1][i + 1] * v);
+                }
+            out[r * cols + c] = sx + sy;
+        }
+}
+
 void orc_minmax(const double *x, int64_t n, double *mn, double *mx)
 {
     double lo = x[0], hi = x[0];

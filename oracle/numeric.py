@@ -51,6 +51,7 @@ _SIGS = {
     "orc_gauss_weights": (None, [ctypes.c_int, _dbl, _D]),
     "orc_blur": (None, [_D, _D, _i64, _i64, _D, ctypes.c_int]),
     "orc_sobel": (None, [_D, _D, _i64, _i64]),
+    "orc_sobel_scale": (None, [_D, _D, _i64, _i64]),
     "orc_minmax": (None, [_D, _i64, _D, _D]),
     "orc_extend": (None, [_D, _dbl, _dbl, _D, _i64]),
     "orc_unsharp": (None, [_D, _D, _dbl, _D, _i64]),
@@ -155,6 +156,15 @@ def sobel(img):
     img = _f64(img)
     out = np.empty_like(img)
     lib().orc_sobel(_p(img), _p(out), img.shape[0], img.shape[1])
+    return out
+
+
+def sobel_scale(img):
+    """Per pixel: sum of |terms| of both Sobel gradients (the condition scale
+    of the magnitude)."""
+    img = _f64(img)
+    out = np.empty_like(img)
+    lib().orc_sobel_scale(_p(img), _p(out), img.shape[0], img.shape[1])
     return out
 
 

@@ -1249,6 +1249,56 @@ int gdag_array_prefetch_host(gdag_ctx *c, gdag_array a, size_t off, size_t bytes
     return c->finish(id, st);
 }
 
+int gdag_issue(gdag_ctx *c, const gdag_elem *elems, int32_t n, const gdag_arg *args, int64_t nargs_total,
+               int64_t *nodes_out, int32_t *issued)
+{
+    if (issued) *issued = 0;
+    if (!c) return GDAG_ERR_INVALID;
+    if (n < 0 || (n && !elems) || nargs_total < 0 || (nargs_total && !args))
+        return c->fail(GDAG_ERR_INVALID, "bad element or argument list");
+    if (nodes_out)
+        for (int32_t i = 0; i < n; ++i) nodes_out[i] = -1;
+    for (int32_t i = 0; i < n; ++i) {
+        const gdag_elem &e = elems[i];
+        const int64_t before = c->next_id();
+        int64_t node = -1;
+        int r;
+        switch (e.type) {
+        case GDAG_ELEM_LAUNCH:
+        case GDAG_ELEM_LAUNCH_FUSED: {
+            const int64_t count = e.type == GDAG_ELEM_LAUNCH ? 1 : (int64_t)e.count;
+            if (e.nargs < 0 || count < 1 || e.arg0 < 0 || e.arg0 > nargs_total ||
+                (int64_t)e.nargs * count > nargs_total - e.arg0) {
+                r = c->fail(GDAG_ERR_INVALID, "element %d: arguments [%lld, +%lld) outside the %lld given", i,
+                            (long long)e.arg0, (long long)e.nargs * count, (long long)nargs_total);
+                break;
+            }
+            const gdag_arg *a = e.nargs ? args + e.arg0 : nullptr;
+            if (e.type == GDAG_ELEM_LAUNCH)
+                r = gdag_launch(c, e.kernel, e.grid, e.block, (size_t)e.smem, a, e.nargs, &node);
+            else
+                r = gdag_launch_fused(c, e.kernel, a, e.nargs, e.count, &node);
+            break;
+        }
+        case GDAG_ELEM_WRITE:
+            r = gdag_array_write(c, e.array, nullptr, (size_t)e.off, (size_t)e.bytes);
+            break;
+        case GDAG_ELEM_PREFETCH_HOST:
+            r = gdag_array_prefetch_host(c, e.array, (size_t)e.off, (size_t)e.bytes);
+            break;
+        default:
+            r = c->fail(GDAG_ERR_INVALID, "element %d: unknown type %d", i, e.type);
+        }
+        // the element's node, when it made one (a write or prefetch made the
+        // last node; a failed element may still have one)
+        if (c->next_id() > before) node = c->next_id() - 1;
+        if (nodes_out) nodes_out[i] = node;
+        if (r) return r;
+        if (issued) *issued = i + 1;
+    }
+    return GDAG_OK;
+}
+
 int gdag_sync(gdag_ctx *c)
 {
     if (!c) return GDAG_ERR_INVALID;
@@ -1363,6 +1413,16 @@ int gdag_node_query(gdag_ctx *c, int64_t node, int32_t *done)
     c->log_op(GDAG_OP_QUERY_DONE, n->stream, n->event, node);
     c->retire(node);
     *done = 1;
+    return GDAG_OK;
+}
+
+int gdag_nodes_query(gdag_ctx *c, const int64_t *nodes, int32_t n, int32_t *done)
+{
+    if (!c || n < 0 || (n && (!nodes || !done))) return GDAG_ERR_INVALID;
+    for (int32_t i = 0; i < n; ++i) {
+        int r = gdag_node_query(c, nodes[i], &done[i]);
+        if (r) return r;
+    }
     return GDAG_OK;
 }
 

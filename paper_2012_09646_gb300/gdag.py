@@ -55,6 +55,7 @@ GDAG_EDGE_RAW, GDAG_EDGE_WAR, GDAG_EDGE_WAW = 0, 1, 2
 GDAG_NODE_KERNEL, GDAG_NODE_HOST_WRITE, GDAG_NODE_HOST_READ, GDAG_NODE_EXTERNAL, GDAG_NODE_HOST_PREFETCH = 0, 1, 2, 3, 4
 GDAG_NODE_GRAPH = 5
 GDAG_ARG_ARRAY, GDAG_ARG_SCALAR = 0, 1
+GDAG_ELEM_LAUNCH, GDAG_ELEM_LAUNCH_FUSED, GDAG_ELEM_WRITE, GDAG_ELEM_PREFETCH_HOST = 0, 1, 2, 3
 GDAG_FUSED_MAX = 4096     # members per gdag_launch_fused call
 GDAG_FUSED_TABLE = 128    # members per persistent launch of a fused element
 (GDAG_OP_LAUNCH, GDAG_OP_COPY_H2D, GDAG_OP_COPY_D2H, GDAG_OP_EXTERNAL, GDAG_OP_RECORD, GDAG_OP_WAIT,
@@ -111,6 +112,13 @@ class gdag_stats(ctypes.Structure):
                 ("held_nodes", ctypes.c_int64), ("held_readers", ctypes.c_int64)]
 
 
+class gdag_elem(ctypes.Structure):
+    _fields_ = [("type", ctypes.c_int32), ("kernel", ctypes.c_int32), ("array", ctypes.c_int32),
+                ("nargs", ctypes.c_int32), ("count", ctypes.c_int32), ("smem", ctypes.c_uint32),
+                ("arg0", ctypes.c_int64), ("off", ctypes.c_uint64), ("bytes", ctypes.c_uint64),
+                ("grid", gdag_dim3), ("block", gdag_dim3)]
+
+
 EXTERNAL_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
 
 _P = ctypes.POINTER
@@ -149,6 +157,8 @@ SIGNATURES = {
     "gdag_trace_export": (ctypes.c_int, [_ctx, _P(gdag_trace_rec), _sz, _P(_sz)]),
     "gdag_stats_get": (ctypes.c_int, [_ctx, _P(gdag_stats)]),
     "gdag_node_query": (ctypes.c_int, [_ctx, _i64, _P(_i32)]),
+    "gdag_nodes_query": (ctypes.c_int, [_ctx, _vp, _i32, _vp]),
+    "gdag_issue": (ctypes.c_int, [_ctx, _vp, _i32, _vp, _i64, _vp, _P(_i32)]),
     "gdag_capture_begin": (ctypes.c_int, [_ctx]),
     "gdag_capture_end": (ctypes.c_int, [_ctx, _P(_i32)]),
     "gdag_graph_launch": (ctypes.c_int, [_ctx, _i32, _P(_i64)]),
@@ -337,6 +347,32 @@ def gdag_node_query(ctx, node):
     d = _i32()
     _check(ctx, lib().gdag_node_query(ctx, node, ctypes.byref(d)))
     return bool(d.value)
+
+
+def gdag_nodes_query(ctx, nodes):
+    """Completion flags of a sequence of node ids (one C call)."""
+    import numpy as np
+    nd = np.ascontiguousarray(nodes, dtype=np.int64)
+    done = np.zeros(nd.size, dtype=np.int32)
+    _check(ctx, lib().gdag_nodes_query(ctx, nd.ctypes.data, nd.size, done.ctypes.data))
+    return done
+
+
+def gdag_issue(ctx, elems, args):
+    """Issue a ctypes array of gdag_elem against a ctypes array of gdag_arg;
+    returns the node ids (-1 where an element made none)."""
+    n = len(elems)
+    nodes = (_i64 * max(1, n))()
+    issued = _i32()
+    r = lib().gdag_issue(ctx, ctypes.addressof(elems) if n else None, n,
+                         ctypes.addressof(args) if len(args) else None, len(args), ctypes.addressof(nodes),
+                         ctypes.byref(issued))
+    if r < 0:
+        e = GdagError(r, (lib().gdag_last_error(ctx) or b"").decode(errors="replace"))
+        e.issued = issued.value
+        e.nodes = [nodes[i] for i in range(n)]
+        raise e
+    return [nodes[i] for i in range(n)]
 
 
 def gdag_capture_begin(ctx):
@@ -615,6 +651,14 @@ class Context:
         _check(self.h, lib().gdag_launch_fused(self.h, kid, arr, nargs, len(members), ctypes.byref(node)))
         return node.value
 
+    def program(self):
+        """A new :class:`Program` recording elements for this context."""
+        return Program(self)
+
+    def done_many(self, nodes):
+        """Non-blocking: completion flags of several nodes (one C call)."""
+        return gdag_nodes_query(self.h, nodes)
+
     def launch_raw(self, name, *args, stream, grid=None, block=None, smem=0):
         kid, a = self._args(name, args)
         g = gdag_dim3(*grid) if grid else gdag_dim3(0, 0, 0)
@@ -696,6 +740,161 @@ class Context:
     def stats(self):
         s = gdag_stats_get(self.h)
         return {f: getattr(s, f) for f, _ in gdag_stats._fields_}
+
+
+class Param:
+    """A scalar of a :class:`Program` (a kernel's scalar argument, or the
+    offset or byte count of a write or prefetch) whose value is given at each
+    issue."""
+
+    __slots__ = ("name",)
+
+    def __init__(self, name):
+        self.name = name
+
+    def __repr__(self):
+        return "Param(%r)" % self.name
+
+
+_ELEM_WORDS = ctypes.sizeof(gdag_elem) // 8   # gdag_elem as 64-bit words
+_ELEM_OFF_WORD = gdag_elem.off.offset // 8
+_ELEM_BYTES_WORD = gdag_elem.bytes.offset // 8
+_ARG_WORDS = ctypes.sizeof(gdag_arg) // 8
+_ARG_VALUE_WORD = gdag_arg.value.offset // 8
+
+
+class Program:
+    """A recorded sequence of non-blocking elements of a program -- kernel
+    launches, fused launches, host writes from the array's host view, and
+    prefetches to the host -- issued by ONE gdag_issue call.  This is
+    argument marshalling only: the library infers, places and issues each
+    element exactly as its single call would.  Scalars may be :class:`Param`
+    objects whose values are bound at each :meth:`issue`, so one recording
+    serves every size of a request shape; the arrays are fixed at recording.
+    """
+
+    def __init__(self, ctx):
+        self.ctx = ctx
+        self._elems = []           # gdag_elem field tuples
+        self._args = bytearray()   # packed gdag_arg entries
+        self._nargs = 0
+        self._arg_params = []      # (name, arg index, scalar size)
+        self._elem_params = []     # (name, element index, word of the element)
+        self._ready = None
+
+    def __len__(self):
+        return len(self._elems)
+
+    def _pack_args(self, name, args):
+        kid, spec = self.ctx.kernel(name)
+        if len(args) != len(spec):
+            raise GdagError(GDAG_ERR_INVALID, "%s takes %d arguments, got %d" % (name, len(spec), len(args)))
+        first = self._nargs
+        for i, (sp, v) in enumerate(zip(spec, args)):
+            if sp.kind == GDAG_ARG_ARRAY:
+                if v.__class__ is Mode:
+                    self._args += _ARG.pack(GDAG_ARG_ARRAY, v.mode, v.array.handle, 0, 0)
+                else:
+                    self._args += _ARG.pack(GDAG_ARG_ARRAY, GDAG_MODE_SIGNATURE, v.handle, 0, 0)
+            elif v.__class__ is Param:
+                self._arg_params.append((v.name, first + i, sp.size))
+                self._args += _ARG.pack(GDAG_ARG_SCALAR, 0, 0, sp.size, 0)
+            else:
+                self._args += _ARG.pack(GDAG_ARG_SCALAR, 0, 0, sp.size, _scalar_bits(v, sp.size))
+        self._nargs += len(args)
+        return kid, first
+
+    def _sized(self, value, word):
+        if value.__class__ is Param:
+            self._elem_params.append((value.name, len(self._elems), word))
+            return 0
+        return int(value)
+
+    def launch(self, name, *args, grid=None, block=None, smem=0):
+        self._ready = None
+        kid, first = self._pack_args(name, args)
+        g = tuple(grid) if grid else (0, 0, 0)
+        b = tuple(block) if block else (0, 0, 0)
+        self._elems.append((GDAG_ELEM_LAUNCH, kid, 0, len(args), 1, smem, first, 0, 0, g, b))
+        return len(self._elems) - 1
+
+    def launch_fused(self, name, members):
+        """One fused element (gdag_launch_fused) of the member argument lists."""
+        self._ready = None
+        if not members:
+            raise GdagError(GDAG_ERR_INVALID, "fused launch of no members")
+        first = None
+        for m in members:
+            kid, f = self._pack_args(name, m)
+            first = f if first is None else first
+        self._elems.append((GDAG_ELEM_LAUNCH_FUSED, kid, 0, len(members[0]), len(members), 0, first, 0, 0,
+                            (0, 0, 0), (0, 0, 0)))
+        return len(self._elems) - 1
+
+    def _copy(self, kind, a, off, nbytes):
+        self._ready = None
+        nbytes = a.nbytes - off if nbytes is None else nbytes
+        o = self._sized(off, _ELEM_OFF_WORD)
+        nb = self._sized(nbytes, _ELEM_BYTES_WORD)
+        self._elems.append((kind, 0, a.handle, 0, 0, 0, 0, o, nb, (0, 0, 0), (0, 0, 0)))
+        return len(self._elems) - 1
+
+    def write(self, a, off=0, nbytes=None):
+        """Host write of [off, off + nbytes) from the array's host view."""
+        return self._copy(GDAG_ELEM_WRITE, a, off, nbytes)
+
+    def prefetch_host(self, a, off=0, nbytes=None):
+        return self._copy(GDAG_ELEM_PREFETCH_HOST, a, off, nbytes)
+
+    def _prepare(self):
+        import numpy as np
+        n = len(self._elems)
+        elems = (gdag_elem * max(1, n))()
+        for i, (t, k, a, na, cnt, sm, a0, off, nb, g, b) in enumerate(self._elems):
+            e = elems[i]
+            e.type, e.kernel, e.array, e.nargs, e.count, e.smem, e.arg0 = t, k, a, na, cnt, sm, a0
+            e.off, e.bytes = off, nb
+            e.grid = gdag_dim3(*g)
+            e.block = gdag_dim3(*b)
+        args = (gdag_arg * max(1, self._nargs)).from_buffer_copy(bytes(self._args) or bytes(_ARG.size))
+        ew = np.frombuffer(elems, dtype=np.uint64)
+        aw = np.frombuffer(args, dtype=np.uint64)
+        groups = {}
+        for name, idx, size in self._arg_params:
+            groups.setdefault(name, {}).setdefault(("a", size), []).append(idx * _ARG_WORDS + _ARG_VALUE_WORD)
+        for name, idx, word in self._elem_params:
+            groups.setdefault(name, {}).setdefault(("e", 8), []).append(idx * _ELEM_WORDS + word)
+        plan = {name: [(ew if w == "e" else aw, size, np.asarray(ix, dtype=np.intp))
+                       for (w, size), ix in g.items()] for name, g in groups.items()}
+        nodes = (_i64 * max(1, n))()
+        self._ready = (elems, args, plan, nodes, _i32(), n, self._nargs)
+
+    def params(self):
+        return sorted({p[0] for p in self._arg_params} | {p[0] for p in self._elem_params})
+
+    def issue(self, **values):
+        """Bind every Param and issue all elements in one call; returns the
+        node id of each element (-1 where it made none).  A failure raises
+        GdagError with ``issued`` (elements issued before the failing one)
+        and ``nodes``."""
+        if self._ready is None:
+            self._prepare()
+        elems, args, plan, nodes, issued, n, nargs = self._ready
+        if len(values) != len(plan) or any(k not in values for k in plan):
+            raise GdagError(GDAG_ERR_INVALID, "program parameters %s, given %s"
+                            % (sorted(plan), sorted(values)))
+        for name, targets in plan.items():
+            v = values[name]
+            for words, size, ix in targets:
+                words[ix] = _scalar_bits(v, size)
+        r = lib().gdag_issue(self.ctx.h, ctypes.addressof(elems), n, ctypes.addressof(args), nargs,
+                             ctypes.addressof(nodes), ctypes.byref(issued))
+        out = nodes[:n]
+        if r < 0:
+            e = GdagError(r, self.ctx.last_error)
+            e.issued, e.nodes = issued.value, out
+            raise e
+        return out
 
 
 def _host_ptr(x):

@@ -137,20 +137,18 @@ def test_bs_other_parameters(K, r, sigma, T):
 
 
 @pytest.mark.parametrize("policy", [G.GDAG_POLICY_PARALLEL, G.GDAG_POLICY_SERIAL_SYNC])
-def test_bs_full_config_sampled(policy):
+def test_bs_full_config(policy):
     """B&S at the benchmark size (10 x 1e7), in the launch shape the bench
-    times; 200k sampled outputs per vector against the oracle."""
+    times; every output of every vector against the oracle."""
     n = 10_000_000
     prices = datagen.bs_inputs(n, count=10, seed=1)
-    rng = np.random.default_rng(0)
     with G.Context(policy=policy) as ctx:
         b = BsDag(ctx, n, count=10)
         b.load_host(prices)
         b.step_e2e()
         for i, p in enumerate(prices):
-            idx = np.concatenate([rng.integers(0, n, 200_000), [0, n - 1]])
-            got = b.hC[i].numpy()[idx]
-            ok, worst = close(got, N.bs_call(p[idx]))
+            got = b.hC[i].numpy()[:n]
+            ok, worst = close(got, N.bs_call(p))
             assert ok, (i, worst)
         # resident form (no copies) gives the same bits
         before = [c.clone() for c in b.C]

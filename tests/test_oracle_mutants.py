@@ -42,6 +42,8 @@ MUTANTS = [
     ("numeric.c", "s += w[i + R] * w[j + R] * img[rr * cols + cc];", "s += w[i + R] * img[rr * cols + cc];"),
     ("numeric.c", "gy += Kx[j + 1][i + 1] * v;", "gy += Kx[i + 1][j + 1] * v;"),
     ("numeric.c", "out[r * cols + c] = sqrt(gx * gx + gy * gy);", "out[r * cols + c] = gx * gx + gy * gy;"),
+    ("numeric.c", "sy += fabs(Kx[j + 1][i + 1] * v);", "sy += fabs(Kx[i + 1][j + 1] * v);"),
+    ("numeric.c", "out[r * cols + c] = sx + sy;", "out[r * cols + c] = sx;"),
     ("numeric.c", "if (x[i] > hi) hi = x[i];", "if (x[i] < hi) hi = x[i];"),
     ("numeric.c", "(in[i] - mn) / (mx - mn)", "(in[i] - mn) / mx"),
     ("numeric.c", "(in[i] - mn) / (mx - mn) : 0.0;", "(in[i] - mn) / (mx - mn) : in[i];"),

@@ -173,6 +173,34 @@ def test_sobel_constant_and_ramp():
     np.testing.assert_allclose(got[1:-1, 0], 4 * s, rtol=1e-14)
 
 
+@pytest.mark.parametrize("shape", [(1, 1), (6, 11), (31, 40)])
+def test_sobel_scale_against_correlation_with_absolute_kernels(shape):
+    """The Sobel condition scale is sum |Kx v| + sum |Ky v|: for a signed
+    image that is the correlation of |img| with |Kx| plus with |Ky| (clamped
+    edges); scipy's correlate gives it independently."""
+    img = datagen.image(*shape, seed=18).astype(np.float64) - 0.5
+    kx = np.array([[-1.0, 0.0, 1.0], [-2.0, 0.0, 2.0], [-1.0, 0.0, 1.0]])
+    a = np.abs(img)
+    want = (scipy.ndimage.correlate(a, np.abs(kx), mode="nearest")
+            + scipy.ndimage.correlate(a, np.abs(kx.T), mode="nearest"))
+    np.testing.assert_allclose(N.sobel_scale(img), want, rtol=1e-14, atol=1e-15)
+
+
+def test_sobel_scale_closed_forms():
+    # constant c: each gradient has terms of total weight 8, so 16 |c|
+    np.testing.assert_allclose(N.sobel_scale(np.full((5, 7), -0.75)), 12.0, rtol=1e-15)
+    # a single impulse v at an interior pixel: every 3x3 window that holds
+    # it sees it once with |Kx| + |Ky| weight (0..4 each); the total over
+    # all pixels is sum(|Kx|) + sum(|Ky|) = 16 |v|
+    img = np.zeros((9, 9))
+    img[4, 4] = 2.5
+    sc = N.sobel_scale(img)
+    assert sc.sum() == pytest.approx(16 * 2.5, rel=1e-15)
+    assert sc[4, 4] == 0.0  # the centre weight of both kernels is 0
+    assert sc[4, 3] == pytest.approx(2.5 * (2 + 0), rel=1e-15)
+    assert sc[3, 3] == pytest.approx(2.5 * (1 + 1), rel=1e-15)
+
+
 def test_minmax_extend_unsharp_combine():
     x = datagen.image(13, 17, seed=9).astype(np.float64)
     mn, mx = N.minmax(x)
