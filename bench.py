@@ -820,6 +820,76 @@ def measure_dag(torch, G, spec, steps, peak_gbs, link):
     }
 
 
+def run_serving(args, torch, datagen, data):
+    """The serving loop (Section III-B's non-blocking completion, run as a
+    request server): Poisson arrivals of the five request kinds at their
+    drawn scales, on one context.  Fusion thresholds come from the
+    autotuner, the per-kind GPU-time model from a calibration pass; the
+    admission window is picked by p99 at the configured rate."""
+    from paper_2012_09646_gb300 import autotune as AT
+    from paper_2012_09646_gb300 import serve as SV
+    rate0 = 2000.0
+    t0 = time.perf_counter()
+    inputs = SV.Inputs(datagen, full_data=data, workers=max(1, min(15, (os.cpu_count() or 2) - 1)))
+    out = {"kinds": list(SV.KINDS), "scale": "U[1/64, 1] per request (DL: batch 16, unscaled)",
+           "hits_graph_scales": inputs.hits_buckets, "budget_gb": 40, "response_bytes_max": SV.RESPONSE_BYTES,
+           "inputs_s": time.perf_counter() - t0, "runs": []}
+    keep = []
+
+    def bs_member(ctx_, n, i):
+        St, Ct = torch.rand(n, device="cuda") * 90 + 10, torch.empty(n, device="cuda")
+        keep.append((St, Ct))
+        return (ctx_.array(St), ctx_.array(Ct), n, 60.0, 0.1, 0.2, 1.0)
+
+    def sq_member(ctx_, n, i):
+        Xt = torch.rand(n, device="cuda")
+        keep.append(Xt)
+        return (ctx_.array(Xt), n)
+    fr = (1 / 64, 1 / 8, 1 / 4, 1 / 2, 1.0)
+    thr_bs, t_bs = AT.tune_fusion("bs_call", bs_member, [int(1e7 * s) for s in fr], group=10, reps=5)
+    thr_sq, t_sq = AT.tune_fusion("vec_square", sq_member, [int(1e6 * s) for s in fr], group=8, reps=5)
+    del keep
+    fuse_max = {"B&S": thr_bs, "VEC": thr_sq}
+    out["fusion"] = {"fuse_max_elems": fuse_max,
+                     "bs_call_group10_ms": {str(n): {"separate": a, "fused": b} for n, (a, b) in t_bs.items()},
+                     "vec_square_group8_ms": {str(n): {"separate": a, "fused": b} for n, (a, b) in t_sq.items()}}
+    cost = None
+
+    def one(rate, window, fm, seed=7):
+        nonlocal cost
+        srv = SV.Server(inputs, fuse_max=fm, max_streams=32, window_ms=window)
+        srv.warm(calibrate=cost is None)
+        if cost is None:
+            cost = dict(srv.cost)
+        srv.cost = dict(cost)
+        f0 = srv.ctx.stats()["fused_members"]
+        reqs = SV.poisson_requests(rate, int(rate * args.serve_seconds), seed=seed)
+        srv.run(reqs)
+        fused = srv.ctx.stats()["fused_members"] - f0
+        srv.close()
+        return dict(SV.latency_summary(reqs), offered_req_s=rate, window_ms=window, fusion=bool(fm),
+                    fused_members=fused)
+    # the admission window (estimated GPU ms in flight): picked by p99 at
+    # the configured rate among the windows that keep up with it
+    sweep = {}
+    for w in (1.0, 2.0, 3.0, 4.0):
+        q = one(rate0, w, fuse_max, seed=8)
+        sweep[w] = {k: q[k] for k in ("p50_ms", "p99_ms", "throughput_req_s")}
+    keeps_up = [w for w in sweep if sweep[w]["throughput_req_s"] >= 0.97 * rate0] or list(sweep)
+    best = min(keeps_up, key=lambda w: sweep[w]["p99_ms"])
+    out["cost_model_ms"] = {k: {"a": a, "b": b} for k, (a, b) in cost.items()}
+    out["window_sweep_2000_req_s"] = {str(k): v for k, v in sweep.items()}
+    out["window_ms"] = best
+    out["max_streams"] = 32
+    # the configured rate (the headline), without fusion, at half the rate,
+    # and without a window (admission by memory alone)
+    for rate, w, fm in ((rate0, best, fuse_max), (rate0, best, None), (1000.0, best, fuse_max),
+                        (rate0, None, fuse_max)):
+        out["runs"].append(one(rate, w, fm))
+    del inputs
+    return out
+
+
 def run_ours(args, rank, world, local_rank):
     import numpy as np
     import torch
@@ -960,62 +1030,7 @@ def run_ours(args, rank, world, local_rank):
         # ---- serving: Poisson streams of DAG requests on one context
         serve_out = None
         if args.dags == "all" and args.serve:
-            from paper_2012_09646_gb300 import serve as SV
-            scales = [0.125, 0.25, 0.5, 1.0]
-            inputs = SV.Inputs(datagen, scales, full=data)
-            serve_out = {"kinds": list(SV.KINDS), "scale_buckets": scales,
-                         "budget_gb": 40, "response_bytes_max": SV.RESPONSE_BYTES, "runs": []}
-            # fusion thresholds from the autotuner: the largest node size at
-            # which one fused element beats the same nodes issued one by one
-            from paper_2012_09646_gb300 import autotune as AT
-            keep = []
-
-            def bs_member(ctx_, n, i):
-                St, Ct = torch.rand(n, device="cuda") * 90 + 10, torch.empty(n, device="cuda")
-                keep.append((St, Ct))
-                return (ctx_.array(St), ctx_.array(Ct), n, 60.0, 0.1, 0.2, 1.0)
-
-            def sq_member(ctx_, n, i):
-                Xt = torch.rand(n, device="cuda")
-                keep.append(Xt)
-                return (ctx_.array(Xt), n)
-            thr_bs, t_bs = AT.tune_fusion("bs_call", bs_member, [int(1e7 * s) for s in scales], group=10, reps=5)
-            thr_sq, t_sq = AT.tune_fusion("vec_square", sq_member, [int(1e6 * s) for s in scales], group=8, reps=5)
-            del keep
-            fuse_max = {"B&S": thr_bs, "VEC": thr_sq}
-            serve_out["fusion"] = {"fuse_max_elems": fuse_max,
-                                   "bs_call_group10_ms": {str(n): {"separate": a, "fused": b}
-                                                          for n, (a, b) in t_bs.items()},
-                                   "vec_square_group8_ms": {str(n): {"separate": a, "fused": b}
-                                                            for n, (a, b) in t_sq.items()}}
-            # the stream pool of the serving context: more streams interleave
-            # more requests (throughput), fewer keep them closer to arrival
-            # order (latency); pick the pool with the lowest p99 at 1000 req/s
-            sweep = {}
-            for ms in (4, 8, 16, 32):
-                srv = SV.Server(inputs, fuse_max=fuse_max, max_streams=ms)
-                srv.warm()
-                reqs = SV.poisson_requests(1000.0, int(1000 * args.serve_seconds), scales, seed=8)
-                srv.run(reqs)
-                srv.close()
-                q = SV.latency_summary(reqs)
-                sweep[ms] = {"p50_ms": q["p50_ms"], "p99_ms": q["p99_ms"], "throughput_req_s": q["throughput_req_s"]}
-            best_ms = min(sweep, key=lambda k: sweep[k]["p99_ms"])
-            serve_out["max_streams_sweep_1000_req_s"] = {str(k): v for k, v in sweep.items()}
-            serve_out["max_streams"] = best_ms
-            # the configured rate, two lower ones to locate the knee, and the
-            # lowest again without fusion for comparison
-            for rate, fm in ((2000.0, fuse_max), (1400.0, fuse_max), (1000.0, fuse_max), (1000.0, None)):
-                srv = SV.Server(inputs, fuse_max=fm, max_streams=best_ms)
-                srv.warm()
-                f0 = srv.ctx.stats()["fused_members"]
-                reqs = SV.poisson_requests(rate, int(rate * args.serve_seconds), scales, seed=7)
-                srv.run(reqs)
-                fused_members = srv.ctx.stats()["fused_members"] - f0
-                srv.close()
-                serve_out["runs"].append(dict(SV.latency_summary(reqs), offered_req_s=rate,
-                                              fusion=bool(fm), fused_members=fused_members))
-            del inputs
+            serve_out = run_serving(args, torch, datagen, data)
 
         # ---- e2e through the public API with host buffers
         ctx2 = G.Context(device=local_rank, policy=G.GDAG_POLICY_PARALLEL)

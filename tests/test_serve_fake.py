@@ -1,7 +1,8 @@
 """The serving dispatcher on the recording backend (CPU only): requests of
 every kind arrive as a Poisson stream or a burst and are all served;
 admission follows arrival order and, under a tiny memory budget, admits one
-request at a time; a burst of small VEC and B&S requests is issued as fused
+request at a time; a window on the estimated GPU time in flight bounds the
+requests in flight; a burst of small VEC and B&S requests is issued as fused
 groups (3 members per VEC request, 10 per B&S request).  The fake backend
 computes nothing, so this checks the dispatcher's logic, not results (the GPU
 tests check those)."""
@@ -11,12 +12,14 @@ import pytest
 from paper_2012_09646_gb300 import serve as SV
 
 SCALES = [1 / 64, 1 / 16]
-HITS_SMALL = (20_000, 100_000)
+SMALL = SV.Full(vec_n=4096, bs_n=8192, img_side=64, ml_rows=256, hits_n=20_000, hits_nnz=100_000, dl_n=2, dl_h=8,
+                dl_w=64)
+BUCKETS = 4
 
 
 @pytest.fixture(scope="module")
 def inputs():
-    return SV.Inputs(datagen, SCALES, device="cpu", hits_full=HITS_SMALL)
+    return SV.Inputs(datagen, full=SMALL, device="cpu", hits_buckets=BUCKETS)
 
 
 def server(inputs, **kw):
@@ -25,12 +28,23 @@ def server(inputs, **kw):
     return srv
 
 
+def poisson(rate, count, seed):
+    return SV.poisson_requests(rate, count, seed=seed)
+
+
+def request(srv, rid, kind, s):
+    """A request with its sizes and a slot, as admission gives it."""
+    r = srv._make(kind, s, rid)
+    r.slot = srv._take_slot(kind, True)
+    return r
+
+
 def fresh(reqs):
     return [SV.Request(r.rid, r.kind, r.scale, r.arrival) for r in reqs]
 
 
 def test_stream_all_served_in_arrival_order(inputs):
-    reqs = SV.poisson_requests(rate=50_000.0, count=40, scales=SCALES, seed=3)
+    reqs = poisson(50_000.0, 60, 3)
     srv = server(inputs)
     out = srv.run(fresh(reqs))
     assert all(r.done_at is not None and r.done_at >= r.arrival for r in out)
@@ -44,7 +58,7 @@ def test_stream_all_served_in_arrival_order(inputs):
 
 
 def test_tiny_budget_admits_one_at_a_time(inputs):
-    reqs = SV.poisson_requests(rate=1e6, count=12, scales=SCALES, seed=4)
+    reqs = poisson(1e6, 12, 4)
     srv = server(inputs, budget_bytes=1)
     out = srv.run(fresh(reqs))
     for a, b in zip(out, out[1:]):
@@ -53,8 +67,7 @@ def test_tiny_budget_admits_one_at_a_time(inputs):
 
 
 def test_burst_issues_fused_groups(inputs):
-    burst = [SV.Request(r.rid, r.kind, r.scale, 0.0)
-             for r in SV.poisson_requests(rate=1.0, count=30, scales=SCALES, seed=5)]
+    burst = [SV.Request(r.rid, r.kind, r.scale, 0.0) for r in poisson(1.0, 30, 5)]
     nv = sum(r.kind == "VEC" for r in burst)
     nb = sum(r.kind == "B&S" for r in burst)
     assert nv >= 2 and nb >= 2
@@ -74,9 +87,9 @@ def test_burst_issues_fused_groups(inputs):
 
 def test_fusion_threshold_excludes_large_nodes(inputs):
     """Only nodes at most fuse_max elements are fused: a threshold below the
-    smallest bucket fuses nothing."""
+    smallest request fuses nothing."""
     burst = [SV.Request(i, "B&S", SCALES[i % 2], 0.0) for i in range(6)]
-    small = inputs.data[("B&S", SCALES[0])]["n"]
+    small = SV.sizes(SMALL, "B&S", SCALES[0])["n"]
     srv = server(inputs, fuse_max={"B&S": small})
     f0 = srv.ctx.stats()["fused_members"]
     srv.run(burst)
@@ -86,6 +99,47 @@ def test_fusion_threshold_excludes_large_nodes(inputs):
     f0 = srv.ctx.stats()["fused_members"]
     srv.run([SV.Request(r.rid, r.kind, r.scale, 0.0) for r in burst])
     assert srv.ctx.stats()["fused_members"] == f0
+    srv.close()
+
+
+def test_sizes_follow_the_scale():
+    """Each request runs its own size: n = round(full * s) for VEC and B&S,
+    the image side ~ full * sqrt(s) (a multiple of 8) and the ML rows ~
+    full * s for IMG+ML, the smallest HITS graph at least s; DL is fixed."""
+    f = SV.Full()
+    assert SV.sizes(f, "VEC", 0.5) == {"n": 500_000, "nbytes": 2_000_000}
+    assert SV.sizes(f, "B&S", 1 / 64)["n"] == 156_250
+    z = SV.sizes(f, "IMG+ML", 0.25)
+    assert z["side"] == 2048 and z["rows"] == 25_000 and z["resp"] == SV.RESPONSE_BYTES
+    assert SV.sizes(f, "IMG+ML", 1.0)["side"] == 4096
+    assert [SV.hits_bucket(s, 16) for s in (1 / 64, 1 / 16, 1 / 16 + 1e-6, 0.5, 1.0)] == [1, 1, 2, 8, 16]
+    assert SV.sizes(f, "DL", 0.3) == {}
+    # the mean work of U[1/64, 1] requests: about 0.51 for the continuously
+    # scaled kinds, about 0.54 for HITS (16 graph scales)
+    s = [r.scale for r in SV.poisson_requests(1.0, 20000, seed=1)]
+    for kind, want in (("VEC", 0.508), ("B&S", 0.508), ("IMG+ML", 0.508), ("HITS", 0.539)):
+        m = sum(SV.work_scale(f, kind, x) for x in s) / len(s)
+        assert abs(m - want) < 0.01, (kind, m)
+
+
+def test_window_bounds_the_requests_in_flight(inputs):
+    """With every request estimated at 1 ms, a 3 ms window admits at most
+    three at a time (a request is always admitted when nothing is in
+    flight)."""
+    reqs = fresh(poisson(1e6, 40, 11))
+    srv = server(inputs, window_ms=3.0)
+    srv.cost = {k: (1.0, 0.0) for k in SV.KINDS}
+    peak = [0]
+    issue_batch = srv.issue_batch
+
+    def watched(batch):
+        issue_batch(batch)
+        live = [x for x in reqs if x.admitted is not None and x.done_at is None]
+        peak[0] = max(peak[0], len(live))
+    srv.issue_batch = watched
+    out = srv.run(reqs)
+    assert all(r.done_at is not None for r in out)
+    assert 1 <= peak[0] <= 3
     srv.close()
 
 
@@ -106,10 +160,11 @@ def test_sinks_cover_every_node_of_a_request(inputs):
     """A request is complete when its sinks are: every node it issued is an
     ancestor of (or is) one of them.  For every kind but VEC the response
     prefetch alone does not cover the request (other outputs, the ML branch,
-    the last hub update), so the extra sinks are needed."""
+    the last hub update, the DL status copies), so the extra sinks are
+    needed."""
     srv = server(inputs, record_log=True)
     for kind in SV.KINDS:
-        r = SV.Request(0, kind, SCALES[0], 0.0)
+        r = request(srv, 0, kind, SCALES[0])
         first = srv._last_node() + 1
         srv.issue(r)
         mine = set(range(first, srv._last_node() + 1))
@@ -121,7 +176,7 @@ def test_sinks_cover_every_node_of_a_request(inputs):
         srv.finish(r, 0.0)
     # fused groups: each member's sink is its prefetch, after the fused nodes
     for kind in ("VEC", "B&S"):
-        g = [SV.Request(i, kind, SCALES[i % 2], 0.0) for i in range(4)]
+        g = [request(srv, i, kind, SCALES[i % 2]) for i in range(4)]
         srv.fuse_max = {kind: 1 << 30}
         first = srv._last_node() + 1
         srv.issue_batch(g)
@@ -135,49 +190,48 @@ def test_sinks_cover_every_node_of_a_request(inputs):
     srv.close()
 
 
-def test_admission_charges_exactly_what_a_request_allocates(inputs):
-    """Admission adds working_bytes(r) to the budget and finish() releases
-    it: it must equal the bytes the request allocates, for every kind and
-    bucket, alone and in fused groups, so that the budget is never exceeded
-    and never held back."""
+def test_admission_charges_exactly_what_a_slot_holds(inputs):
+    """Admission charges slot_bytes(kind) against the budget: it must equal
+    the device bytes a slot allocates, for every kind, and every request,
+    at any scale, fits its kind's slot."""
     srv = server(inputs)
-    for s in SCALES:
-        for kind in SV.KINDS:
-            r = SV.Request(0, kind, s, 0.0)
-            srv.issue(r)
-            assert r.bytes == srv.working_bytes(r), (kind, s)
+    for kind in SV.KINDS:
+        sl = srv._take_slot(kind, True)
+        got = sum(t.numel() * t.element_size() for t in sl.tensors.values())
+        assert got == srv.slot_bytes(kind) == sl.nbytes, kind
+        srv._return_slot(sl)
+    for s in (SV.SCALE_MIN, 0.37, 1.0):
+        for kind in SV.SCALED:
+            r = request(srv, 0, kind, s)
+            srv.issue(r)  # a size beyond the slot would be rejected by the kernels' checks
             srv.ctx.sync()
             srv.finish(r, 0.0)
-    for kind in ("VEC", "B&S"):
-        g = [SV.Request(i, kind, SCALES[i % 2], 0.0) for i in range(4)]
-        srv.fuse_max = {kind: 1 << 30}
-        srv.issue_batch(g)
-        assert all(r.bytes == srv.working_bytes(r) for r in g), kind
-        srv.ctx.sync()
-        for r in g:
-            srv.finish(r, 0.0)
+            assert r.error is None
+    assert srv.used == 0
     srv.close()
 
 
 def test_budget_is_exceeded_only_by_a_request_admitted_alone(inputs):
-    """Under a budget a few requests wide, the bytes admitted never exceed
-    it, except by a single request admitted while nothing else is in flight
-    (which must run for the queue to make progress)."""
-    reqs = SV.poisson_requests(rate=200_000.0, count=60, scales=SCALES, seed=6)
-    srv = server(inputs, budget_bytes=40_000_000)
+    """Under a budget a few slots wide, the bytes held (slots in flight plus
+    idle slots kept for reuse) never exceed it, except by a single request
+    admitted while nothing else is in flight (which must run for the queue
+    to make progress); idle slots of other kinds are released for room."""
+    reqs = poisson(200_000.0, 80, 6)
+    srv = server(inputs)
+    srv.budget = 3 * max(srv.slot_bytes(k) for k in SV.KINDS)
     seen = []
     issue_batch = srv.issue_batch
 
     def watched(batch):
         inflight_before = srv.used - sum(r.need for r in batch)
-        seen.append((srv.used, inflight_before, len(batch)))
+        seen.append((srv.used + srv.cached, inflight_before, len(batch)))
         issue_batch(batch)
     srv.issue_batch = watched
     out = srv.run(fresh(reqs))
     assert all(r.done_at is not None for r in out)
     assert len(seen) > 1
-    for used, before, n in seen:
-        assert used <= srv.budget or (before == 0 and n == 1), (used, before, n)
+    for held, before, n in seen:
+        assert held <= srv.budget or (before == 0 and n == 1), (held, before, n)
     assert srv.used == 0
     srv.close()
 
@@ -197,7 +251,7 @@ def test_a_failed_request_fails_alone(inputs):
     memory is released, and every other request is served."""
     from paper_2012_09646_gb300 import gdag as G
     w = _warm_ops(inputs)
-    reqs = SV.poisson_requests(rate=50_000.0, count=40, scales=SCALES, seed=7)
+    reqs = poisson(50_000.0, 40, 7)
     for k in (w, w + 37, w + 150, w + 400):
         srv = server(inputs, fake_fail_op=k)
         out = srv.run(fresh(reqs))
@@ -205,7 +259,7 @@ def test_a_failed_request_fails_alone(inputs):
         assert len(failed) == 1, k
         assert failed[0].error.code == G.GDAG_ERR_CUDA
         assert all(r.done_at is not None for r in out)
-        assert all(r.resp_view is not None for r in out if r.error is None and r.kind != "VEC")
+        assert all(r.resp_view is not None for r in out if r.error is None)
         assert srv.used == 0 and not srv.ctx.stats()["active"]
         s = SV.latency_summary(out)
         assert s["requests"] == len(out) - 1 and s["failed"] == 1
@@ -229,7 +283,7 @@ def test_a_fused_group_fails_together(inputs):
 def test_a_context_losing_failure_stops_the_server(inputs):
     from paper_2012_09646_gb300 import gdag as G
     w = _warm_ops(inputs)
-    reqs = SV.poisson_requests(rate=50_000.0, count=20, scales=SCALES, seed=8)
+    reqs = poisson(50_000.0, 20, 8)
     srv = server(inputs, fake_fail_op=w + 10, fake_fail_sticky=True)
     with pytest.raises(G.GdagError) as e:
         srv.run(fresh(reqs))
@@ -244,7 +298,7 @@ def test_a_device_that_stops_completing_times_out(inputs):
     forever."""
     import time
     from paper_2012_09646_gb300 import gdag as G
-    reqs = SV.poisson_requests(rate=50_000.0, count=5, scales=SCALES, seed=9)
+    reqs = poisson(50_000.0, 5, 9)
     srv = server(inputs, fake_complete=0, request_timeout_s=0.2)
     t = time.perf_counter()
     with pytest.raises(G.GdagError) as e:
@@ -263,7 +317,7 @@ def test_a_long_serving_run_holds_a_bounded_node_table(inputs):
     n, trim = 4000, 1024
     reqs = [SV.Request(i, "VEC", SCALES[0], 0.0) for i in range(n)]
     srv = server(inputs, trim_nodes=trim)
-    srv.budget = 10 * srv.working_bytes(reqs[0])
+    srv.budget = 10 * srv.slot_bytes("VEC")
     peak = [0, 0]
     issue_batch = srv.issue_batch
 
