@@ -176,6 +176,35 @@ def time_launches(torch, issue, reps):
     return ms
 
 
+_FLUSH = []
+
+
+def time_cold(torch, issue, reps):
+    """Device ms of one call of ``issue(stream_handle)`` with a cold L2: each
+    of `reps` launches follows a read of a 512 MB buffer (four times the
+    L2), which leaves L2 holding clean lines of that buffer, and is timed
+    alone with CUDA events on its stream (the host enqueues the launch
+    while the flush runs); the median is returned."""
+    if not _FLUSH:
+        _FLUSH.append((torch.empty(128 << 20, dtype=torch.float32, device="cuda").fill_(1.0),
+                       torch.empty((), dtype=torch.float32, device="cuda")))
+    buf, acc = _FLUSH[0]
+    s = torch.cuda.Stream()
+    issue(s.cuda_stream)
+    torch.cuda.synchronize()
+    ev = []
+    with torch.cuda.stream(s):
+        for _ in range(reps):
+            torch.sum(buf, dim=0, out=acc)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(s)
+            issue(s.cuda_stream)
+            e1.record(s)
+            ev.append((e0, e1))
+    torch.cuda.synchronize()
+    return statistics.median(a.elapsed_time(b) for a, b in ev)
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -235,34 +264,56 @@ def cpu_oracle_rate_all_cores(seconds, n_per_vec=250_000):
     return options / (N_OPTS * N_VEC) / wall, cores, wall
 
 
+_REF_SHARDS = {}
+
+
+def _ref_price_shard(i, n_shard):
+    """Reference-arm worker: price shard i of a whole DAG (the ten vectors'
+    options i*n_shard .. (i+1)*n_shard, drawn like the workload's) with the
+    fp64 C oracle as it stands.  The shard's prices are generated on first
+    use and kept, so a timed step is pricing only."""
+    from oracle import numeric as N
+    if i not in _REF_SHARDS:
+        import datagen
+        _REF_SHARDS[i] = datagen.bs_inputs(n_shard, count=N_VEC, seed=1000 + i)
+    K, r, s, T = BS_PARAMS
+    for p in _REF_SHARDS[i]:
+        N.bs_call(p, K, r, s, T)
+    return len(_REF_SHARDS[i]) * n_shard
+
+
 def run_reference(args, rank):
+    """The base contract's reference arm: the CPU oracle, as it stands, on
+    the host cores.  Each step prices one whole B&S DAG (10 x 1e7 options),
+    its options split into one shard per core and priced by one spawned
+    process per core (the options are independent, so the oracle runs
+    unchanged, in parallel)."""
     from paper_2012_09646_gb300 import replicas as RP
     if not RP.reports(rank):
         return
-    n_per_vec = 1_000_000
-    import datagen
-    from oracle import numeric as N
-    prices = datagen.bs_inputs(n_per_vec, count=N_VEC, seed=1)
-    K, r, s, T = BS_PARAMS
-    for _ in range(args.warmup):
-        for p in prices:
-            N.bs_call(p, K, r, s, T)
-    times = []
-    for _ in range(args.steps):
-        t0 = time.perf_counter()
-        for p in prices:
-            N.bs_call(p, K, r, s, T)
-        times.append(time.perf_counter() - t0)
-    frac = n_per_vec / N_OPTS
+    import multiprocessing as mp
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
+    shards = cores
+    n_shard = -(-N_OPTS // shards)
+    with mp.get_context("spawn").Pool(cores) as pool:
+        jobs = [(i, n_shard) for i in range(shards)]
+        for _ in range(max(1, args.warmup)):
+            pool.starmap(_ref_price_shard, jobs)
+        times = []
+        for _ in range(args.steps):
+            t0 = time.perf_counter()
+            done = sum(pool.starmap(_ref_price_shard, jobs))
+            times.append(time.perf_counter() - t0)
+    frac = done / (N_OPTS * N_VEC)  # >= 1: shards round up
     ms_dag = statistics.mean(times) / frac * 1e3
     value = 1e3 / ms_dag
-    sample = "each step prices 10 x %d options (1/%d of one DAG) with the fp64 C oracle; makespan scaled" % (
-        n_per_vec, int(1 / frac))
+    sample = ("each step prices one whole DAG (10 x %d options, in %d shards of %d options per vector) with "
+              "the fp64 C oracle, one spawned process per host core" % (N_OPTS, shards, n_shard))
     out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_dag, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": WORKLOAD, "parallelism": "single host thread"},
-           "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+           "config": {"workload": WORKLOAD, "parallelism": "%d host processes" % cores},
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
 
@@ -293,8 +344,37 @@ class Recorder:
         self.log.append(("d2h", a, a.nbytes - off if nbytes is None else nbytes))
         return self.ctx.prefetch_host(a, off, nbytes)
 
+    def program(self):
+        return _RecordedProgram(self)
+
     def __getattr__(self, k):
         return getattr(self.ctx, k)
+
+
+class _RecordedProgram:
+    """A Program whose elements the Recorder logs at every issue."""
+
+    def __init__(self, rec):
+        self.rec, self.p, self.elems = rec, rec.ctx.program(), []
+
+    def __len__(self):
+        return len(self.p)
+
+    def launch(self, name, *args, **kw):
+        self.elems.append(("k", name, args))
+        return self.p.launch(name, *args, **kw)
+
+    def write(self, a, off=0, nbytes=None):
+        self.elems.append(("h2d", a, a.nbytes - off if nbytes is None else nbytes))
+        return self.p.write(a, off, nbytes)
+
+    def prefetch_host(self, a, off=0, nbytes=None):
+        self.elems.append(("d2h", a, a.nbytes - off if nbytes is None else nbytes))
+        return self.p.prefetch_host(a, off, nbytes)
+
+    def issue(self, **values):
+        self.rec.log.extend(self.elems)
+        return self.p.issue(**values)
 
 
 def alg_bytes(name, a):
@@ -363,8 +443,8 @@ class Spec:
 class BsSpec(Spec):
     name = "B&S"
 
-    def build(self, ctx):
-        d = self.W.BsDag(ctx, N_OPTS, count=N_VEC, host=False)
+    def build(self, ctx, batched=True):
+        d = self.W.BsDag(ctx, N_OPTS, count=N_VEC, host=False, batched=batched)
         d.load_device(self.data["bs"])
         return d
 
@@ -381,8 +461,8 @@ class VecSpec(Spec):
     name = "VEC"
     host_sync = True
 
-    def build(self, ctx):
-        d = self.W.VecDag(ctx, 1_000_000)
+    def build(self, ctx, batched=True):
+        d = self.W.VecDag(ctx, 1_000_000, batched=batched)
         d.load(*self.data["vec"])
         return d
 
@@ -409,8 +489,8 @@ class VecSpec(Spec):
 class ImgSpec(Spec):
     name = "IMG"
 
-    def build(self, ctx):
-        d = self.W.ImgDag(ctx, 4096, 4096)
+    def build(self, ctx, batched=True):
+        d = self.W.ImgDag(ctx, 4096, 4096, batched=batched)
         d.img.copy_(self.data["img"])
         return d
 
@@ -437,8 +517,8 @@ class ImgSpec(Spec):
 class MlSpec(Spec):
     name = "ML"
 
-    def build(self, ctx):
-        d = self.W.MlDag(ctx, 100_000)
+    def build(self, ctx, batched=True):
+        d = self.W.MlDag(ctx, 100_000, batched=batched)
         d.load(*self.data["ml"])
         return d
 
@@ -459,9 +539,9 @@ class HitsSpec(Spec):
     name = "HITS"
     ITERS = 5
 
-    def build(self, ctx):
+    def build(self, ctx, batched=True):
         csr, csc = self.data["hits"]
-        d = self.W.HitsDag(ctx, csr, csc)
+        d = self.W.HitsDag(ctx, csr, csc, batched=batched)
         d.run(iters=0, read=False)  # a = h = 1
         return d
 
@@ -494,8 +574,8 @@ class HitsBatchSpec(HitsSpec):
     iteration for the whole batch."""
     name = "HITS-batch"
 
-    def build(self, ctx):
-        d = self.W.HitsBatchDag(ctx, self.data["hits_batch"])
+    def build(self, ctx, batched=True):
+        d = self.W.HitsBatchDag(ctx, self.data["hits_batch"], batched=batched)
         d.run(iters=0, read=False)
         return d
 
@@ -557,8 +637,8 @@ def measure_hits_separate(torch, G, W, graphs, steps, iters=5):
 class DlSpec(Spec):
     name = "DL"
 
-    def build(self, ctx):
-        d = self.W.DlDag(ctx)
+    def build(self, ctx, batched=True):
+        d = self.W.DlDag(ctx, batched=batched)
         d.load(*self.data["dl"])
         return d
 
@@ -567,8 +647,8 @@ class DlSpec(Spec):
 
     def hand(self, d, ctx, H):
         n, h, w = d.n, d.h, d.w
-        H.k(0, "conv3x3_relu_pool", d.X1, d.W1, d.B1, d.P1, d.ST, n, h, w)
-        H.k(1, "conv3x3_relu_pool", d.X2, d.W2, d.B2, d.P2, d.ST, n, h, w)
+        H.k(0, "conv3x3_relu_pool", d.X1, d.W1, d.B1, d.P1, d.ST1, n, h, w)
+        H.k(1, "conv3x3_relu_pool", d.X2, d.W2, d.B2, d.P2, d.ST2, n, h, w)
         H.k(0, "avgpool_global", d.P1, d.E1, n * 64, (h // 2) * (w // 2))
         H.k(1, "avgpool_global", d.P2, d.E2, n * 64, (h // 2) * (w // 2))
         H.dep(0, 1)
@@ -634,9 +714,9 @@ def measure_dag(torch, G, spec, steps, peak_gbs, link):
     s0 = torch.cuda.Stream()
     out = {}
 
-    def timed_ctx(policy):
+    def timed_ctx(policy, batched=True):
         ctx = G.Context(policy=policy)
-        obj = spec.build(ctx)
+        obj = spec.build(ctx, batched=batched)
         for _ in range(3):
             spec.step(obj)
         ctx.sync()
@@ -660,6 +740,12 @@ def measure_dag(torch, G, spec, steps, peak_gbs, link):
         ctx.sync()
         return ctx, obj, ms
 
+    # the dynamic path as a program issues it one call per element (the
+    # paper's form), then batched: each step's non-blocking elements in one
+    # gdag_issue call (same DAG, streams and waits)
+    c1, o1, out["parallel_single_calls"] = timed_ctx(G.GDAG_POLICY_PARALLEL, batched=False)
+    c1.close()
+    del o1
     ctx, obj, out["parallel"] = timed_ctx(G.GDAG_POLICY_PARALLEL)
     streams_used = ctx.stats()["streams"]
 
@@ -752,7 +838,6 @@ def measure_dag(torch, G, spec, steps, peak_gbs, link):
     spec.step(lobj)
     lctx.sync()
     elems = rec.log
-    st = torch.cuda.Stream()
     solo_cache = {}
 
     def solo(e):
@@ -760,8 +845,7 @@ def measure_dag(torch, G, spec, steps, peak_gbs, link):
         if kind == "k":
             key = (e[1],) + tuple(getattr(x, "handle", x) for x in e[2])
             if key not in solo_cache:
-                solo_cache[key] = time_launches(
-                    torch, lambda sh: lctx.launch_raw(e[1], *e[2], stream=sh), 5)
+                solo_cache[key] = time_cold(torch, lambda sh: lctx.launch_raw(e[1], *e[2], stream=sh), 5)
             return solo_cache[key]
         nb = e[2]
         return nb / (link[kind] * 1e9) * 1e3
@@ -814,6 +898,7 @@ def measure_dag(torch, G, spec, steps, peak_gbs, link):
         "speedup_vs_serial_sync": out["serial_sync"] / out["parallel"],
         "vs_hand_cuda_graph": out["hand_cuda_graph"] / out["parallel"],
         "library_graph_vs_hand_cuda_graph": out["hand_cuda_graph"] / out["library_graph"],
+        "single_calls_vs_hand_cuda_graph": out["hand_cuda_graph"] / out["parallel_single_calls"],
         "frac_of_cp_bound": cp / out["parallel"], "frac_of_resource_bound": res / out["parallel"],
         "launches_per_step": kern, "per_kernel_solo": per_kernel,
         "makespan_single_run_ms": single, "overlap": overlap,
@@ -1119,6 +1204,29 @@ def run_ours(args, rank, world, local_rank):
         dist.destroy_process_group()
     if out is not None:
         print(json.dumps(out), flush=True)
+        print_summary(out)
+
+
+def print_summary(out):
+    """A short human-readable digest of the bench line on stderr."""
+    w = sys.stderr.write
+    w("summary: %s %.0f %s resident (%.3f ms/step), e2e %.1f %s; %s %.3f of HBM peak\n" % (
+        out["config"]["workload"].split(":")[0], out["value"], out["unit"], out["ms_per_step"], out["e2e"]["value"],
+        out["unit"], out["roofline"]["kernel"], out["roofline"]["frac"]))
+    w("%-11s %8s %8s %8s %8s %8s %8s\n" % ("DAG", "par_ms", "vsSYNC", "vsGraph", "1call/G", "ofCP", "ofRes"))
+    for name, d in (out.get("dags") or {}).items():
+        m = d["makespan_ms"]
+        w("%-11s %8.3f %8.2f %8.2f %8.2f %8.2f %8.2f\n" % (
+            name, m["parallel"], d["speedup_vs_serial_sync"], d["vs_hand_cuda_graph"],
+            d["single_calls_vs_hand_cuda_graph"], d["frac_of_cp_bound"], d["frac_of_resource_bound"]))
+    sv = out.get("serve")
+    if sv:
+        for r in sv["runs"]:
+            w("serve %5.0f req/s window %s fusion %d: served %.0f req/s p50 %.2f ms p99 %.2f ms "
+              "(queue p99 %.2f, device p99 %.2f)\n" % (
+                  r["offered_req_s"], r["window_ms"], r["fusion"], r["throughput_req_s"], r["p50_ms"], r["p99_ms"],
+                  r["queue_p99_ms"], r["device_p99_ms"]))
+    sys.stderr.flush()
 
 
 def run_profile(args):

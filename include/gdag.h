@@ -571,6 +571,14 @@ int gdag_ops_export(gdag_ctx *ctx, gdag_op *buf, size_t cap, size_t *n);
 int gdag_trace_export(gdag_ctx *ctx, gdag_trace_rec *buf, size_t cap,
                       size_t *n);
 
+/* Write the timing records (options.trace = 1; waits for completion first)
+ * to the file at path as a Chrome trace (JSON, for chrome://tracing or
+ * Perfetto): one complete event per node, named after its kernel or its
+ * kind, on one track per pool stream, in microseconds from context
+ * creation.  The trace of Section IV-F's overlap analysis.  Errors: INVALID
+ * (tracing off, or the file cannot be written), CUDA. */
+int gdag_trace_write(gdag_ctx *ctx, const char *path);
+
 int gdag_stats_get(gdag_ctx *ctx, gdag_stats *out);
 
 /* Bytes of scratch the built-in reductions (vec_reduce_diff, minmax, l2norm)

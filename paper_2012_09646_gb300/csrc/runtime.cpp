@@ -58,6 +58,7 @@ struct Node {
     int32_t stream = -1;
     int32_t event = -1;       // pooled event slot (active nodes only)
     int32_t tev0 = -1, tev1 = -1;  // timing events (trace)
+    int32_t label = -1;       // kernel handle of a kernel node (trace names)
     bool active = false;
     bool first_child_taken = false;
     uint32_t parent_off = 0, parent_cnt = 0;
@@ -964,6 +965,7 @@ int gdag_launch(gdag_ctx *c, gdag_kernel k, gdag_dim3 grid, gdag_dim3 block, siz
     for (int i = 0; i < nacc; ++i)
         if (acc[i].bits & gdag::W_BIT) c->arrays[(size_t)acc[i].array].host_valid = false;
     c->push_node(GDAG_NODE_KERNEL);
+    c->node(id)->label = k;
     if (node_out) *node_out = id;
     int32_t s;
     r = c->place(id, &s);
@@ -1027,6 +1029,7 @@ int gdag_launch_fused(gdag_ctx *c, gdag_kernel k, const gdag_arg *args, int32_t 
     for (const Access &x : acc)
         if (x.bits & gdag::W_BIT) c->arrays[(size_t)x.array].host_valid = false;
     c->push_node(GDAG_NODE_KERNEL);
+    c->node(id)->label = k;
     if (node_out) *node_out = id;
     int32_t s;
     r = c->place(id, &s);
@@ -1387,6 +1390,51 @@ int gdag_trace_export(gdag_ctx *c, gdag_trace_rec *buf, size_t cap, size_t *n)
 }
 
 
+
+static void json_string(FILE *f, const char *s)
+{
+    std::fputc('"', f);
+    for (; *s; ++s) {
+        const unsigned char ch = (unsigned char)*s;
+        if (ch == '"' || ch == '\\') std::fprintf(f, "\\%c", ch);
+        else if (ch < 0x20) std::fprintf(f, "\\u%04x", ch);
+        else std::fputc(ch, f);
+    }
+    std::fputc('"', f);
+}
+
+int gdag_trace_write(gdag_ctx *c, const char *path)
+{
+    if (!c || !path) return GDAG_ERR_INVALID;
+    size_t n = 0;
+    int r = gdag_trace_export(c, nullptr, 0, &n);
+    if (r) return r;
+    std::vector<gdag_trace_rec> recs(n);
+    r = gdag_trace_export(c, recs.data(), n, &n);
+    if (r) return r;
+    FILE *f = std::fopen(path, "w");
+    if (!f) return c->fail(GDAG_ERR_INVALID, "cannot open %s for writing", path);
+    static const char *kinds[] = {"kernel", "h2d", "read", "external", "d2h", "graph"};
+    std::fprintf(f, "{\"displayTimeUnit\": \"ms\", \"traceEvents\": [");
+    for (size_t i = 0; i < recs.size(); ++i) {
+        const gdag_trace_rec &t = recs[i];
+        const char *cat = (t.kind >= 0 && t.kind <= 5) ? kinds[t.kind] : "node";
+        const gdag::Node *nd = c->node(t.node);
+        const int32_t lab = nd ? nd->label : -1;
+        const char *name = (lab >= 0 && (size_t)lab < c->kernels.size()) ? c->kernels[(size_t)lab].name.c_str() : cat;
+        std::fprintf(f, "%s\n{\"name\": ", i ? "," : "");
+        json_string(f, name);
+        std::fprintf(f, ", \"cat\": \"%s\", \"ph\": \"X\", \"ts\": %.3f, \"dur\": %.3f, \"pid\": 0, ", cat,
+                     t.start_ms * 1e3, (t.end_ms > t.start_ms ? t.end_ms - t.start_ms : 0.0) * 1e3);
+        if (t.stream >= 0) std::fprintf(f, "\"tid\": \"stream %d\", ", t.stream);
+        else std::fprintf(f, "\"tid\": \"host\", ");
+        std::fprintf(f, "\"args\": {\"node\": %lld}}", (long long)t.node);
+    }
+    std::fprintf(f, "\n]}\n");
+    const bool bad = std::ferror(f) != 0;
+    if (std::fclose(f) != 0 || bad) return c->fail(GDAG_ERR_INVALID, "writing %s failed", path);
+    return GDAG_OK;
+}
 
 int gdag_node_query(gdag_ctx *c, int64_t node, int32_t *done)
 {

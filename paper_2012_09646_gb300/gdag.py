@@ -156,6 +156,7 @@ SIGNATURES = {
     "gdag_ops_export": (ctypes.c_int, [_ctx, _P(gdag_op), _sz, _P(_sz)]),
     "gdag_trace_export": (ctypes.c_int, [_ctx, _P(gdag_trace_rec), _sz, _P(_sz)]),
     "gdag_stats_get": (ctypes.c_int, [_ctx, _P(gdag_stats)]),
+    "gdag_trace_write": (ctypes.c_int, [_ctx, ctypes.c_char_p]),
     "gdag_node_query": (ctypes.c_int, [_ctx, _i64, _P(_i32)]),
     "gdag_nodes_query": (ctypes.c_int, [_ctx, _vp, _i32, _vp]),
     "gdag_issue": (ctypes.c_int, [_ctx, _vp, _i32, _vp, _i64, _vp, _P(_i32)]),
@@ -335,6 +336,10 @@ def gdag_ops_export(ctx):
 
 def gdag_trace_export(ctx):
     return _export(ctx, lib().gdag_trace_export, gdag_trace_rec)
+
+
+def gdag_trace_write(ctx, path):
+    return _check(ctx, lib().gdag_trace_write(ctx, os.fsencode(path)))
 
 
 def gdag_stats_get(ctx):
@@ -736,6 +741,10 @@ class Context:
         with open(path, "w") as f:
             json.dump({"traceEvents": ev, "displayTimeUnit": "ms"}, f)
         return len(ev)
+
+    def trace_write(self, path):
+        """The library's Chrome trace of a traced context (gdag_trace_write)."""
+        gdag_trace_write(self.h, path)
 
     def stats(self):
         s = gdag_stats_get(self.h)

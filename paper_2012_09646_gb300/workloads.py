@@ -6,6 +6,12 @@ device memory) and pinned host views, registers them with a
 per ``step`` call exactly as a user program would: host writes, kernel
 launches with per-argument access modes, host reads.  The dependency DAG,
 streams, events and copies are entirely the library's.
+
+With ``batched=True`` (the default) the non-blocking elements of a step are
+recorded once as a :class:`~paper_2012_09646_gb300.gdag.Program` and issued
+with one ``gdag_issue`` call per step; the library infers, places and
+issues each element exactly as one call per element would (``batched=False``),
+but the host's per-element cost leaves the critical path of short DAGs.
 """
 from __future__ import annotations
 
@@ -20,18 +26,57 @@ def _pinned(shape, dtype):
     return torch.empty(shape, dtype=dtype, pin_memory=True)
 
 
+class _Calls:
+    """The Program recording interface, one library call per element."""
+
+    def __init__(self, ctx):
+        self.ctx = ctx
+
+    def launch(self, name, *args, **kw):
+        return self.ctx.launch(name, *args, **kw)
+
+    def write(self, a, off=0, nbytes=None):
+        return self.ctx.write(a, None, off, nbytes)
+
+    def prefetch_host(self, a, off=0, nbytes=None):
+        return self.ctx.prefetch_host(a, off, nbytes)
+
+
+class _Issuer:
+    """Issues a DAG's recorded element sequences: one Program per sequence
+    (recorded on first use) when batched, else one call per element."""
+
+    def _init_issuer(self, ctx, batched):
+        self._batched = batched
+        self._progs = {}
+
+    def _run(self, key, record):
+        """record(c) issues the sequence on c, which has the Program
+        recording interface (launch, write from the view, prefetch_host)."""
+        if not self._batched:
+            record(_Calls(self.ctx))
+            return
+        p = self._progs.get(key)
+        if p is None:
+            p = self.ctx.program()
+            record(p)
+            self._progs[key] = p
+        p.issue()
+
+
 def _scratch(ctx, kernel, n, device):
     nbytes = G.gdag_scratch_bytes(kernel, n)
     t = torch.zeros(nbytes, dtype=torch.uint8, device=device)
     return t, ctx.array(t, name=kernel + "_scratch")
 
 
-class VecDag:
+class VecDag(_Issuer):
     """VEC: host writes x and y; K1 x := x*x; K2 y := y*y; K3 z = sum(x - y);
     host reads z."""
 
-    def __init__(self, ctx, n, device="cuda"):
+    def __init__(self, ctx, n, device="cuda", batched=True):
         self.ctx, self.n = ctx, n
+        self._init_issuer(ctx, batched)
         self.x = torch.zeros(max(n, 1), dtype=F32, device=device)
         self.y = torch.zeros(max(n, 1), dtype=F32, device=device)
         self.z = torch.zeros(1, dtype=F32, device=device)
@@ -46,26 +91,31 @@ class VecDag:
         self.hx[: self.n].copy_(torch.as_tensor(x))
         self.hy[: self.n].copy_(torch.as_tensor(y))
 
-    def step(self, read=True):
-        c, n = self.ctx, self.n
-        c.write(self.X, None, 0, 4 * n)
-        c.write(self.Y, None, 0, 4 * n)
+    def _elements(self, c):
+        n = self.n
+        c.write(self.X, 0, 4 * n)
+        c.write(self.Y, 0, 4 * n)
         c.launch("vec_square", self.X, n)
         c.launch("vec_square", self.Y, n)
         c.launch("vec_reduce_diff", self.X, self.Y, self.Z, self.S, n)
+
+    def step(self, read=True):
+        self._run("step", self._elements)
         if read:
-            c.read(self.Z)
+            self.ctx.read(self.Z)
             return float(self.hz[0])
         return None
 
 
-class BsDag:
+class BsDag(_Issuer):
     """B&S: `count` independent call-price nodes.  With ``host_inputs`` each
     step rewrites every price vector from the host (copy nodes overlapping
     the other chains' kernels) and reads every result back."""
 
-    def __init__(self, ctx, n, count=10, K=60.0, r=0.1, sigma=0.2, T=1.0, device="cuda", host=True):
+    def __init__(self, ctx, n, count=10, K=60.0, r=0.1, sigma=0.2, T=1.0, device="cuda", host=True,
+                 batched=True):
         self.ctx, self.n, self.count = ctx, n, count
+        self._init_issuer(ctx, batched)
         self.params = (float(K), float(r), float(sigma), float(T))
         self.S = [torch.zeros(max(n, 1), dtype=F32, device=device) for _ in range(count)]
         self.C = [torch.zeros(max(n, 1), dtype=F32, device=device) for _ in range(count)]
@@ -83,29 +133,35 @@ class BsDag:
             d[: self.n].copy_(torch.as_tensor(p).to(d.device))
         torch.cuda.synchronize()
 
-    def launch_all(self):
+    def _kernels(self, c):
         K, r, s, T = self.params
         for Sa, Ca in zip(self.SA, self.CA):
-            self.ctx.launch("bs_call", Sa, Ca, self.n, K, r, s, T)
+            c.launch("bs_call", Sa, Ca, self.n, K, r, s, T)
+
+    def launch_all(self):
+        self._run("kernels", self._kernels)
 
     def step_resident(self):
         """Kernels only (inputs already in HBM); no host access."""
         self.launch_all()
+
+    def _chains(self, c, prefetch):
+        nb = 4 * self.n
+        K, r, s, T = self.params
+        for Sa, Ca in zip(self.SA, self.CA):
+            c.write(Sa, 0, nb)
+            c.launch("bs_call", Sa, Ca, self.n, K, r, s, T)
+            if prefetch:
+                c.prefetch_host(Ca, 0, nb)
 
     def step_e2e(self, prefetch=True):
         """Host write of every price vector, all kernels, host read of every
         result (the paper's streaming form of the benchmark).  With
         ``prefetch`` each result's copy to the host is started right after its
         kernel, so it overlaps the other chains' input copies."""
-        c, nb = self.ctx, 4 * self.n
-        K, r, s, T = self.params
-        for Sa, Ca in zip(self.SA, self.CA):
-            c.write(Sa, None, 0, nb)
-            c.launch("bs_call", Sa, Ca, self.n, K, r, s, T)
-            if prefetch:
-                c.prefetch_host(Ca, 0, nb)
+        self._run(("e2e", prefetch), lambda c: self._chains(c, prefetch))
         for Ca in self.CA:
-            c.read(Ca, None, 0, nb)
+            self.ctx.read(Ca, None, 0, 4 * self.n)
 
 
 def gaussian_weights(radius, sigma):
@@ -117,7 +173,7 @@ def gaussian_weights(radius, sigma):
     return torch.tensor([v / s for v in w], dtype=F32)
 
 
-class ImgDag:
+class ImgDag(_Issuer):
     """IMG: blur5 and blur9 of the image, Sobel of each, min/max of each,
     contrast stretch of each edge map, unsharp mask of the image with blur5,
     and the final combination (10 kernels).  The host writes the image and
@@ -125,8 +181,9 @@ class ImgDag:
 
     R5, SIGMA5, R9, SIGMA9, ALPHA = 2, 1.0, 4, 2.0, 0.5
 
-    def __init__(self, ctx, rows, cols, device="cuda"):
+    def __init__(self, ctx, rows, cols, device="cuda", batched=True):
         self.ctx, self.rows, self.cols = ctx, rows, cols
+        self._init_issuer(ctx, batched)
         n = rows * cols
         self.n = n
         t = lambda: torch.zeros(n, dtype=F32, device=device)
@@ -149,8 +206,8 @@ class ImgDag:
     def load(self, image):
         self.h_img.copy_(torch.as_tensor(image).reshape(-1))
 
-    def launch_all(self):
-        c, n, rows, cols = self.ctx, self.n, self.rows, self.cols
+    def _kernels(self, c):
+        n, rows, cols = self.n, self.rows, self.cols
         c.launch("gauss_blur", self.IMG, self.B5, self.W5, rows, cols, self.R5)
         c.launch("gauss_blur", self.IMG, self.B9, self.W9, rows, cols, self.R9)
         c.launch("sobel", self.B5, self.E5, rows, cols)
@@ -162,21 +219,27 @@ class ImgDag:
         c.launch("unsharp", self.IMG, self.B5, self.S, self.ALPHA, n)
         c.launch("combine", self.S, self.B5, self.B9, self.E5, self.E9, self.OUT, n)
 
+    def launch_all(self):
+        self._run("kernels", self._kernels)
+
     def step(self, read=True):
-        self.ctx.write(self.IMG, None)
-        self.launch_all()
+        def elements(c):
+            c.write(self.IMG, 0, self.IMG.nbytes)
+            self._kernels(c)
+        self._run("step", elements)
         if read:
             self.ctx.read(self.OUT)
 
 
-class MlDag:
+class MlDag(_Issuer):
     """ML: naive-Bayes scores and ridge scores of the same X (both read-only
     users of X, so they run concurrently), a softmax of each, and the argmax
     of their sum as int32 labels.  X and the tables are resident; the host
     reads the labels each step."""
 
-    def __init__(self, ctx, rows, feats=1024, classes=10, device="cuda"):
+    def __init__(self, ctx, rows, feats=1024, classes=10, device="cuda", batched=True):
         self.ctx, self.rows, self.feats, self.classes = ctx, rows, feats, classes
+        self._init_issuer(ctx, batched)
         self.X = torch.zeros((max(rows, 1), feats), dtype=torch.int32, device=device)
         self.T1 = torch.zeros((feats, classes), dtype=F32, device=device)
         self.b1 = torch.zeros(classes, dtype=F32, device=device)
@@ -201,13 +264,16 @@ class MlDag:
         self.b2.copy_(torch.as_tensor(ridge_b))
         torch.cuda.synchronize()
 
-    def launch_all(self):
-        c, r, f, k = self.ctx, self.rows, self.feats, self.classes
+    def _kernels(self, c):
+        r, f, k = self.rows, self.feats, self.classes
         c.launch("dense_scores", self.XA, self.T1A, self.b1A, self.S1A, r, f, k)
         c.launch("dense_scores", self.XA, self.T2A, self.b2A, self.S2A, r, f, k)
         c.launch("row_softmax", self.S1A, r, k)
         c.launch("row_softmax", self.S2A, r, k)
         c.launch("argmax_combine", self.S1A, self.S2A, self.LA, r, k)
+
+    def launch_all(self):
+        self._run("kernels", self._kernels)
 
     def step(self, read=True):
         self.launch_all()
@@ -215,7 +281,7 @@ class MlDag:
             self.ctx.read(self.LA, None, 0, 4 * self.rows)
 
 
-class HitsDag:
+class HitsDag(_Issuer):
     """HITS: per iteration a' = A^T h and h' = A a (two SpMVs that read the
     previous iterate, so they run concurrently), the L2 norm of each and the
     scaling by it; ping-pong buffers.  The graph (CSR of A and of A^T, int32
@@ -223,8 +289,9 @@ class HitsDag:
     matrix is computed once by a spmv_partition node.  The host writes
     a = h = 1 and reads both final vectors."""
 
-    def __init__(self, ctx, csr, csc, device="cuda"):
+    def __init__(self, ctx, csr, csc, device="cuda", batched=True):
         self.ctx = ctx
+        self._init_issuer(ctx, batched)
         rp, col, val = csr
         trp, tcol, tval = csc
         self.n = n = len(rp) - 1
@@ -257,14 +324,17 @@ class HitsDag:
         ctx.launch("spmv_partition", self.AA[0], self.PA, n, nnz)
         ctx.launch("spmv_partition", self.ATA[0], self.PAT, n, nnz)
 
-    def iterate(self, a, h, a_next, h_next):
-        c, n, nnz = self.ctx, self.n, self.nnz
+    def _iteration(self, c, a, h, a_next, h_next):
+        n, nnz = self.n, self.nnz
         c.launch("spmv_csr", *self.ATA, self.V[h], self.PAT, self.V[a_next], self.CAT, n, nnz)
         c.launch("spmv_csr", *self.AA, self.V[a], self.PA, self.V[h_next], self.CA, n, nnz)
         c.launch("l2norm", self.V[a_next], self.NA, self.SA, n)
         c.launch("l2norm", self.V[h_next], self.NH, self.SH, n)
         c.launch("scale", self.V[a_next], self.NA, n)
         c.launch("scale", self.V[h_next], self.NH, n)
+
+    def iterate(self, a, h, a_next, h_next):
+        self._run(("it", a, h, a_next, h_next), lambda c: self._iteration(c, a, h, a_next, h_next))
 
     def run(self, iters=5, read=True):
         """Host writes a = h = 1, then `iters` iterations; returns the names
@@ -311,11 +381,11 @@ class HitsBatchDag(HitsDag):
     and scaling are per-graph segment kernels -- six launches per iteration
     for the whole batch (the fused form of one HITS program per graph)."""
 
-    def __init__(self, ctx, graphs, device="cuda"):
+    def __init__(self, ctx, graphs, device="cuda", batched=True):
         csr, seg = block_diag_csr([g[0] for g in graphs])
         csc, seg_t = block_diag_csr([g[1] for g in graphs])
         assert (seg == seg_t).all()
-        super().__init__(ctx, csr, csc, device=device)
+        super().__init__(ctx, csr, csc, device=device, batched=batched)
         self.G = G_ = len(graphs)
         self.seg_host = seg
         self.seg = torch.as_tensor(seg).to(dtype=torch.int32).to(device)
@@ -327,8 +397,8 @@ class HitsBatchDag(HitsDag):
         self._shs, self.SHS = _scratch(ctx, "seg_l2norm", G_, device)
         torch.cuda.synchronize()
 
-    def iterate(self, a, h, a_next, h_next):
-        c, n, nnz, G_ = self.ctx, self.n, self.nnz, self.G
+    def _iteration(self, c, a, h, a_next, h_next):
+        n, nnz, G_ = self.n, self.nnz, self.G
         c.launch("spmv_csr", *self.ATA, self.V[h], self.PAT, self.V[a_next], self.CAT, n, nnz)
         c.launch("spmv_csr", *self.AA, self.V[a], self.PA, self.V[h_next], self.CA, n, nnz)
         c.launch("seg_l2norm", self.V[a_next], self.SEG, self.NAS, self.SAS, G_, n)
@@ -340,14 +410,15 @@ class HitsBatchDag(HitsDag):
         return vec[int(self.seg_host[g]):int(self.seg_host[g + 1])]
 
 
-class DlDag:
+class DlDag(_Issuer):
     """DL: two convolution branches (conv3x3 + bias + ReLU + 2x2 max-pool on
     the tensor cores), a global average pool of each, and a dense layer over
     the concatenated embeddings.  bf16 NCHW activations, fp32 embeddings and
     logits; inputs resident, the host reads the logits."""
 
-    def __init__(self, ctx, n=16, h=256, w=256, classes=10, device="cuda"):
+    def __init__(self, ctx, n=16, h=256, w=256, classes=10, device="cuda", batched=True):
         self.ctx, self.n, self.h, self.w, self.classes = ctx, n, h, w, classes
+        self._init_issuer(ctx, batched)
         bf = torch.bfloat16
         self.x1 = torch.zeros((n, 3, h, w), dtype=bf, device=device)
         self.x2 = torch.zeros((n, 3, h, w), dtype=bf, device=device)
@@ -362,14 +433,16 @@ class DlDag:
         self.wd = torch.zeros((128, classes), dtype=F32, device=device)
         self.bd = torch.zeros(classes, dtype=F32, device=device)
         self.logits = torch.zeros((n, classes), dtype=F32, device=device)
-        self.status = torch.zeros(1, dtype=torch.int32, device=device)
+        # one status word per branch: a shared one would order the two
+        # branches (both write it)
+        self.status = torch.zeros(2, dtype=torch.int32, device=device)
         self.h_logits = _pinned((n, classes), F32)
         A = ctx.array
         self.X1, self.X2, self.W1, self.W2 = A(self.x1), A(self.x2), A(self.w1), A(self.w2)
         self.B1, self.B2, self.P1, self.P2 = A(self.b1), A(self.b2), A(self.p1), A(self.p2)
         self.E1, self.E2, self.WD, self.BD = A(self.e1), A(self.e2), A(self.wd), A(self.bd)
         self.LOG = A(self.logits, host=self.h_logits)
-        self.ST = A(self.status)
+        self.ST1, self.ST2 = A(self.status[0:1]), A(self.status[1:2])
         torch.cuda.synchronize()
 
     def load(self, x1, x2, w1, b1, w2, b2, wd, bd):
@@ -380,13 +453,16 @@ class DlDag:
             dst.copy_(torch.as_tensor(src))
         torch.cuda.synchronize()
 
-    def launch_all(self):
-        c, n, h, w = self.ctx, self.n, self.h, self.w
-        c.launch("conv3x3_relu_pool", self.X1, self.W1, self.B1, self.P1, self.ST, n, h, w)
-        c.launch("conv3x3_relu_pool", self.X2, self.W2, self.B2, self.P2, self.ST, n, h, w)
+    def _kernels(self, c):
+        n, h, w = self.n, self.h, self.w
+        c.launch("conv3x3_relu_pool", self.X1, self.W1, self.B1, self.P1, self.ST1, n, h, w)
+        c.launch("conv3x3_relu_pool", self.X2, self.W2, self.B2, self.P2, self.ST2, n, h, w)
         c.launch("avgpool_global", self.P1, self.E1, n * 64, (h // 2) * (w // 2))
         c.launch("avgpool_global", self.P2, self.E2, n * 64, (h // 2) * (w // 2))
         c.launch("concat_dense", self.E1, self.E2, self.WD, self.BD, self.LOG, n, 64, self.classes)
+
+    def launch_all(self):
+        self._run("kernels", self._kernels)
 
     def step(self, read=True):
         self.launch_all()
