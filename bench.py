@@ -940,37 +940,41 @@ def run_serving(args, torch, datagen, data):
                      "vec_square_group8_ms": {str(n): {"separate": a, "fused": b} for n, (a, b) in t_sq.items()}}
     cost = None
 
-    def one(rate, window, fm, seed=7):
+    def one(rate, window, fm, split=None, seed=7):
         nonlocal cost
-        srv = SV.Server(inputs, fuse_max=fm, max_streams=32, window_ms=window)
+        srv = SV.Server(inputs, fuse_max=fm, max_streams=32, window_ms=window, split_ms=split)
         srv.warm(calibrate=cost is None)
         if cost is None:
             cost = dict(srv.cost)
         srv.cost = dict(cost)
-        f0 = srv.ctx.stats()["fused_members"]
+        f0 = sum(c.stats()["fused_members"] for c in srv.ctxs.values())
         reqs = SV.poisson_requests(rate, int(rate * args.serve_seconds), seed=seed)
         srv.run(reqs)
-        fused = srv.ctx.stats()["fused_members"] - f0
+        fused = sum(c.stats()["fused_members"] for c in srv.ctxs.values()) - f0
         srv.close()
-        return dict(SV.latency_summary(reqs), offered_req_s=rate, window_ms=window, fusion=bool(fm),
-                    fused_members=fused)
-    # the admission window (estimated GPU ms in flight): picked by p99 at
-    # the configured rate among the windows that keep up with it
+        return dict(SV.latency_summary(reqs), offered_req_s=rate, window_ms=window, split_ms=split,
+                    fusion=bool(fm), fused_members=fused)
+    # the admission window (estimated GPU ms in flight) and the class split
+    # (requests estimated above split_ms form the long class, short ones run
+    # on high-priority streams): picked by p99 at the configured rate among
+    # the settings that keep up with it
     sweep = {}
-    for w in (1.0, 2.0, 3.0, 4.0):
-        q = one(rate0, w, fuse_max, seed=8)
-        sweep[w] = {k: q[k] for k in ("p50_ms", "p99_ms", "throughput_req_s")}
-    keeps_up = [w for w in sweep if sweep[w]["throughput_req_s"] >= 0.97 * rate0] or list(sweep)
-    best = min(keeps_up, key=lambda w: sweep[w]["p99_ms"])
+    for w in (1.0, 2.0, 4.0):
+        for split in (None, 0.5):
+            q = one(rate0, w, fuse_max, split, seed=8)
+            sweep[(w, split)] = {k: q[k] for k in ("p50_ms", "p99_ms", "throughput_req_s")}
+    keeps_up = [k for k in sweep if sweep[k]["throughput_req_s"] >= 0.97 * rate0] or list(sweep)
+    best_w, best_split = min(keeps_up, key=lambda k: sweep[k]["p99_ms"])
     out["cost_model_ms"] = {k: {"a": a, "b": b} for k, (a, b) in cost.items()}
-    out["window_sweep_2000_req_s"] = {str(k): v for k, v in sweep.items()}
-    out["window_ms"] = best
+    out["sweep_2000_req_s"] = {"window %s split %s" % k: v for k, v in sweep.items()}
+    out["window_ms"] = best_w
+    out["split_ms"] = best_split
     out["max_streams"] = 32
     # the configured rate (the headline), without fusion, at half the rate,
-    # and without a window (admission by memory alone)
-    for rate, w, fm in ((rate0, best, fuse_max), (rate0, best, None), (1000.0, best, fuse_max),
-                        (rate0, None, fuse_max)):
-        out["runs"].append(one(rate, w, fm))
+    # and without a window or classes (admission by memory alone)
+    for rate, w, fm, split in ((rate0, best_w, fuse_max, best_split), (rate0, best_w, None, best_split),
+                               (1000.0, best_w, fuse_max, best_split), (rate0, None, fuse_max, None)):
+        out["runs"].append(one(rate, w, fm, split))
     del inputs
     return out
 
@@ -1222,10 +1226,10 @@ def print_summary(out):
     sv = out.get("serve")
     if sv:
         for r in sv["runs"]:
-            w("serve %5.0f req/s window %s fusion %d: served %.0f req/s p50 %.2f ms p99 %.2f ms "
+            w("serve %5.0f req/s window %s split %s fusion %d: served %.0f req/s p50 %.2f ms p99 %.2f ms "
               "(queue p99 %.2f, device p99 %.2f)\n" % (
-                  r["offered_req_s"], r["window_ms"], r["fusion"], r["throughput_req_s"], r["p50_ms"], r["p99_ms"],
-                  r["queue_p99_ms"], r["device_p99_ms"]))
+                  r["offered_req_s"], r["window_ms"], r["split_ms"], r["fusion"], r["throughput_req_s"], r["p50_ms"],
+                  r["p99_ms"], r["queue_p99_ms"], r["device_p99_ms"]))
     sys.stderr.flush()
 
 

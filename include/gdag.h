@@ -138,6 +138,13 @@ typedef struct {
     int64_t fake_fail_op;    /* FAKE backend: index of the backend operation
                                 (launch, copy, record, wait, external) that
                                 fails, -1 = none                              */
+    int32_t stream_priority; /* CUDA priority of the streams the library
+                                creates (lower is more urgent; CUDA clamps it
+                                into the device's range): the block scheduler
+                                then prefers this context's pending work, e.g.
+                                a context serving short requests beside one
+                                serving long ones; default 0                  */
+    int32_t reserved0;       /* must be 0                                     */
 } gdag_options;
 
 /* Array argument or scalar argument of a launch. */
@@ -220,7 +227,8 @@ typedef struct {
 /* Fill *o with the defaults listed in gdag_options, then apply environment
  * overrides where set to an integer: GDAG_POLICY, GDAG_MAX_STREAMS,
  * GDAG_PREFETCH, GDAG_RETIRE_BY_QUERY, GDAG_RECORD_LOG, GDAG_TRACE,
- * GDAG_TIMEOUT_MS, GDAG_DEVICE, GDAG_TRIM_NODES (a caller may still change
+ * GDAG_TIMEOUT_MS, GDAG_DEVICE, GDAG_TRIM_NODES, GDAG_STREAM_PRIORITY (a
+ * caller may still change
  * any field before
  * gdag_create, which validates them). */
 void gdag_options_default(gdag_options *o);

@@ -23,7 +23,7 @@ class Backend {
   public:
     virtual ~Backend() {}
     virtual int init(int device) = 0;
-    virtual int stream_create(void **s) = 0;
+    virtual int stream_create(void **s, int priority) = 0;
     virtual int stream_destroy(void *s) = 0;
     virtual int event_create(void **e, bool timing) = 0;
     virtual int event_destroy(void *e) = 0;

@@ -53,13 +53,13 @@ class CudaBackend final : public Backend {
         }
         return chk(cudaSetDevice(device), "cudaSetDevice");
     }
-    int stream_create(void **s) override
+    int stream_create(void **s, int priority) override
     {
         // blocking streams: device work the caller put on the legacy default
         // stream (allocation fills, copies by the framework that owns the
         // memory) is ordered before anything issued here afterwards
         cudaStream_t st;
-        int r = chk(cudaStreamCreateWithFlags(&st, cudaStreamDefault), "cudaStreamCreate");
+        int r = chk(cudaStreamCreateWithPriority(&st, cudaStreamDefault, priority), "cudaStreamCreate");
         if (!r) *s = st;
         return r;
     }
@@ -177,7 +177,7 @@ class FakeBackend final : public Backend {
         return BE_OK;
     }
     int init(int) override { return BE_OK; }
-    int stream_create(void **s) override
+    int stream_create(void **s, int) override
     {
         *s = (void *)(uintptr_t)(0x1000 + next_++);
         return BE_OK;

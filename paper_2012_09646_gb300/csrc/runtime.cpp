@@ -298,7 +298,7 @@ struct Ctx {
     int new_stream(int32_t *out)
     {
         void *h;
-        int r = be->stream_create(&h);
+        int r = be->stream_create(&h, opt.stream_priority);
         if (r) return be_fail(r, "stream create");
         StreamState s;
         s.handle = h;
@@ -720,7 +720,7 @@ void gdag_options_default(gdag_options *o)
                {"GDAG_PREFETCH", &o->prefetch},       {"GDAG_RETIRE_BY_QUERY", &o->retire_by_query},
                {"GDAG_RECORD_LOG", &o->record_log},   {"GDAG_TRACE", &o->trace},
                {"GDAG_TIMEOUT_MS", &o->timeout_ms}, {"GDAG_DEVICE", &o->device},
-               {"GDAG_TRIM_NODES", &o->trim_nodes}};
+               {"GDAG_TRIM_NODES", &o->trim_nodes}, {"GDAG_STREAM_PRIORITY", &o->stream_priority}};
     for (const auto &e : env) {
         const char *v = std::getenv(e.name);
         if (!v || !*v) continue;
@@ -740,7 +740,7 @@ int gdag_create(gdag_ctx **out, const gdag_options *opts)
     else
         gdag_options_default(&o);
     if (o.policy < 0 || o.policy > 2 || o.max_streams < 1 || o.max_streams > 1024 || o.timeout_ms <= 0 ||
-        o.record_log < 0 || o.record_log > 2 || o.trim_nodes < 0 ||
+        o.record_log < 0 || o.record_log > 2 || o.trim_nodes < 0 || o.reserved0 != 0 ||
         (o.backend != GDAG_BACKEND_CUDA && o.backend != GDAG_BACKEND_FAKE))
         return GDAG_ERR_INVALID;
     gdag_ctx *c = new (std::nothrow) gdag_ctx();
@@ -1485,7 +1485,7 @@ int gdag_capture_begin(gdag_ctx *c)
     r = gdag_sync(c);  // no parent from before the capture can remain active
     if (r) return r;
     if (!c->cap_stream) {
-        r = c->be->stream_create(&c->cap_stream);
+        r = c->be->stream_create(&c->cap_stream, c->opt.stream_priority);
         if (r) return c->be_fail(r, "stream create");
     }
     r = c->be->capture_begin(c->cap_stream);

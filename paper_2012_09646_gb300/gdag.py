@@ -73,7 +73,7 @@ class gdag_options(ctypes.Structure):
                 ("retire_by_query", ctypes.c_int32), ("record_log", ctypes.c_int32),
                 ("trace", ctypes.c_int32), ("timeout_ms", ctypes.c_int32), ("trim_nodes", ctypes.c_int32),
                 ("fake_complete", ctypes.c_int32), ("fake_fail_sticky", ctypes.c_int32),
-                ("fake_fail_op", ctypes.c_int64)]
+                ("fake_fail_op", ctypes.c_int64), ("stream_priority", ctypes.c_int32), ("reserved0", ctypes.c_int32)]
 
 
 class gdag_arg(ctypes.Structure):
@@ -477,7 +477,7 @@ class Context:
 
     def __init__(self, policy=GDAG_POLICY_PARALLEL, backend="cuda", device=0, max_streams=16, prefetch=True,
                  retire_by_query=False, record_log=False, trace=False, timeout_ms=60000, trim_nodes=0,
-                 fake_complete=False, fake_fail_op=-1, fake_fail_sticky=False):
+                 fake_complete=False, fake_fail_op=-1, fake_fail_sticky=False, stream_priority=0):
         o = gdag_options_default()
         o.policy = policy
         o.backend = GDAG_BACKEND_FAKE if backend == "fake" else GDAG_BACKEND_CUDA
@@ -492,6 +492,7 @@ class Context:
         o.fake_complete = int(fake_complete)
         o.fake_fail_op = fake_fail_op
         o.fake_fail_sticky = int(fake_fail_sticky)
+        o.stream_priority = stream_priority
         self.options = o
         self.h = gdag_create(o)
         self._kernels = {}

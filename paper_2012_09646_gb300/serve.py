@@ -9,11 +9,15 @@ dispatcher thread does four things:
   kind is free, or a new one fits the HBM budget (idle slots of other kinds
   are released to make room), and (2) the estimated GPU time of the
   admitted, unfinished requests stays within ``window_ms``.  This is
-  continuous batching: an admitted request adds its elements to the one
-  shared context, and requests share no written array, so the scheduler
-  puts them on separate streams and they overlap on the GPU.  The window
-  keeps the device queue short, so that a request is not queued behind
-  every request admitted before it;
+  continuous batching: an admitted request adds its elements to a shared
+  context, and requests share no written array, so the scheduler puts them
+  on separate streams and they overlap on the GPU.  The window keeps the
+  device queue short, so that a request is not queued behind every request
+  admitted before it.  With ``split_ms`` the requests form two classes by
+  their estimated GPU time, each with its own queue (arrival order within
+  the class), its own window and its own context; the short class's
+  context runs on high-priority CUDA streams, so short requests neither
+  wait behind a long one on the host nor behind its kernels on the GPU;
 * issues each admitted request's whole program with one ``gdag_issue`` call
   (a recorded :class:`~.gdag.Program` whose sizes are bound per request),
   ending with a device-to-host prefetch of the response.  Requests admitted
@@ -211,7 +215,7 @@ class Request:
     seconds from the start of the run."""
 
     __slots__ = ("rid", "kind", "scale", "arrival", "admitted", "issued", "done_at", "sinks", "slot", "need",
-                 "est", "size", "resp", "resp_view", "result", "error")
+                 "est", "size", "resp", "resp_view", "result", "error", "cls")
 
     def __init__(self, rid, kind, scale, arrival):
         self.rid, self.kind, self.scale, self.arrival = rid, kind, scale, arrival
@@ -225,15 +229,16 @@ class Request:
         self.resp_view = None
         self.result = None
         self.error = None
+        self.cls = "s"
 
 
 class Slot:
     """The private arrays of one request of a kind, at full size."""
 
-    __slots__ = ("kind", "tensors", "A", "host", "nbytes", "programs", "tainted")
+    __slots__ = ("kind", "cls", "ctx", "tensors", "A", "host", "nbytes", "programs", "tainted")
 
-    def __init__(self, kind):
-        self.kind = kind
+    def __init__(self, kind, cls, ctx):
+        self.kind, self.cls, self.ctx = kind, cls, ctx
         self.tensors = {}
         self.A = {}
         self.host = None  # pinned response buffer (host view of the response arrays)
@@ -247,7 +252,8 @@ class Server:
 
     def __init__(self, inputs, budget_bytes=40 << 30, max_streams=32, device="cuda", fuse_max=None,
                  backend="cuda", record_log=False, fake_fail_op=-1, fake_fail_sticky=False, fake_complete=None,
-                 request_timeout_s=120.0, trim_nodes=0, window_ms=None, keep_results=False):
+                 request_timeout_s=120.0, trim_nodes=0, window_ms=None, keep_results=False, split_ms=None,
+                 short_priority=-5):
         """``fuse_max``: {kind: largest node size (elements) that is fused
         across requests}; None or {} turns fusion off.  ``window_ms``: the
         largest estimated GPU time of admitted, unfinished requests (None:
@@ -263,7 +269,10 @@ class Server:
         no limit).  ``trim_nodes``: the context's node-table threshold for
         dropping retired elements (0: the library default).
         ``keep_results``: copy every request's whole result to the host when
-        it completes (``request.result``)."""
+        it completes (``request.result``).  ``split_ms``: requests estimated
+        above it form the long class (its own queue, window and context);
+        the short class's context creates its streams at CUDA priority
+        ``short_priority`` (None: one class)."""
         self.inp = inputs
         self.full = inputs.full
         self.fuse_max = dict(fuse_max or {})
@@ -273,42 +282,52 @@ class Server:
         self.device = device
         self.window_ms = window_ms
         self.keep_results = keep_results
-        self.ctx = G.Context(max_streams=max_streams, retire_by_query=True, backend=backend,
+        self.split_ms = split_ms
+
+        def context(priority):
+            return G.Context(max_streams=max_streams, retire_by_query=True, backend=backend,
                              fake_complete=(backend == "fake") if fake_complete is None else fake_complete,
                              record_log=record_log, fake_fail_op=fake_fail_op, fake_fail_sticky=fake_fail_sticky,
-                             trim_nodes=trim_nodes)
+                             trim_nodes=trim_nodes, stream_priority=priority)
+        # class "s" (short; the only class without split_ms) and "l" (long)
+        self.ctxs = {"s": context(short_priority if split_ms is not None else 0)}
+        if split_ms is not None:
+            self.ctxs["l"] = context(0)
+        self.ctx = self.ctxs["s"]
         self.request_timeout_s = request_timeout_s
         self.shared = {}
-        self.pools = {k: [] for k in KINDS}
+        self.pools = {(k, c): [] for k in KINDS for c in self.ctxs}
         self.cost = {k: (1.0, 0.0) for k in KINDS}   # est ms = a + b * work scale
         self._partitions = {}
         self._slot_bytes = {}
 
     # ------------------------------------------------------------ shared
-    def _shared(self, key, t):
-        """Register a resident read-only input once."""
-        if key not in self.shared:
-            self.shared[key] = self.ctx.array(t)
-        return self.shared[key]
+    def _shared(self, ctx, key, t):
+        """Register a resident read-only input once per context."""
+        k = (id(ctx), key)
+        if k not in self.shared:
+            self.shared[k] = ctx.array(t)
+        return self.shared[k]
 
-    def _hits_shared(self, k):
-        """Arrays of HITS graph k: the CSR of A and A^T, their merge-path
-        partitions (computed once, by a DAG element that later requests
-        read), and the all-ones start vector."""
+    def _hits_shared(self, ctx, k):
+        """Arrays of HITS graph k in a context: the CSR of A and A^T, their
+        merge-path partitions (computed once per context, by a DAG element
+        that later requests read), and the all-ones start vector."""
         g = self.inp.data["HITS"][k]
-        A = [self._shared(("A", k, i), t) for i, t in enumerate(g["A"])]
-        AT = [self._shared(("AT", k, i), t) for i, t in enumerate(g["AT"])]
-        if k not in self._partitions:
+        A = [self._shared(ctx, ("A", k, i), t) for i, t in enumerate(g["A"])]
+        AT = [self._shared(ctx, ("AT", k, i), t) for i, t in enumerate(g["AT"])]
+        pk = (id(ctx), k)
+        if pk not in self._partitions:
             n, nnz = g["n"], g["nnz"]
             pb = G.gdag_scratch_bytes("spmv_partition", n + nnz)
             pa = torch.zeros(pb, dtype=torch.uint8, device=self.device)
             pat = torch.zeros(pb, dtype=torch.uint8, device=self.device)
-            PA, PAT = self.ctx.array(pa), self.ctx.array(pat)
-            self.ctx.launch("spmv_partition", A[0], PA, n, nnz)
-            self.ctx.launch("spmv_partition", AT[0], PAT, n, nnz)
-            self._partitions[k] = (PA, PAT, pa, pat)
-        ones = self._shared("ones", self.inp.data["HITS_ones"])
-        return A, AT, self._partitions[k][0], self._partitions[k][1], ones
+            PA, PAT = ctx.array(pa), ctx.array(pat)
+            ctx.launch("spmv_partition", A[0], PA, n, nnz)
+            ctx.launch("spmv_partition", AT[0], PAT, n, nnz)
+            self._partitions[pk] = (PA, PAT, pa, pat)
+        ones = self._shared(ctx, "ones", self.inp.data["HITS_ones"])
+        return A, AT, self._partitions[pk][0], self._partitions[pk][1], ones
 
     # ------------------------------------------------------------- slots
     def slot_bytes(self, kind):
@@ -349,8 +368,8 @@ class Server:
         gs = self.inp.data["HITS"].values()
         return max(g["n"] for g in gs), max(g["nnz"] for g in gs)
 
-    def _new_slot(self, kind):
-        sl = Slot(kind)
+    def _new_slot(self, kind, cls):
+        sl = Slot(kind, cls, self.ctxs[cls])
         dtypes = {1: torch.uint8, 2: torch.bfloat16, 4: F32}
         pin = self.device != "cpu"
         sl.host = torch.zeros(RESPONSE_BYTES // 4, dtype=F32, pin_memory=pin)
@@ -370,24 +389,24 @@ class Server:
             elif kind == "DL" and nm in ("st1", "st2"):
                 # the status words after the logits in the response buffer
                 host = sl.host[self.full.dl_n * 10 + (nm == "st2"):].data_ptr()
-            sl.A[nm] = self.ctx.array(t, host=host)
+            sl.A[nm] = sl.ctx.array(t, host=host)
         sl.nbytes = self.slot_bytes(kind)
         return sl
 
     def _drop_slot(self, sl):
         """Unregister a slot's arrays (waits for their users) and free it."""
         for a in sl.A.values():
-            self.ctx.unregister(a)
+            sl.ctx.unregister(a)
         sl.A.clear()
         sl.tensors.clear()
         sl.programs.clear()
 
-    def _take_slot(self, kind, alone):
-        """A slot for a new request, or None if the budget has no room (an
-        idle slot of another kind is released first when that makes room;
-        a request admitted while nothing else is in flight always gets
-        one)."""
-        pool = self.pools[kind]
+    def _take_slot(self, kind, alone, cls="s"):
+        """A slot for a new request of class cls, or None if the budget has
+        no room (an idle slot of another kind or class is released first
+        when that makes room; a request admitted while nothing else is in
+        flight always gets one)."""
+        pool = self.pools[(kind, cls)]
         if pool:
             sl = pool.pop()
             self.cached -= sl.nbytes
@@ -395,13 +414,13 @@ class Server:
             return sl
         nb = self.slot_bytes(kind)
         while self.used + self.cached + nb > self.budget and self.cached:
-            other = max((k for k in KINDS if self.pools[k]), key=lambda k: self.slot_bytes(k))
+            other = max((k for k in self.pools if self.pools[k]), key=lambda k: self.slot_bytes(k[0]))
             victim = self.pools[other].pop()
             self.cached -= victim.nbytes
             self._drop_slot(victim)
         if self.used + self.cached + nb > self.budget and not alone:
             return None
-        sl = self._new_slot(kind)
+        sl = self._new_slot(kind, cls)
         self.used += sl.nbytes
         return sl
 
@@ -410,7 +429,7 @@ class Server:
         if sl.tainted:  # a failed request may have left a counter or status nonzero
             self._drop_slot(sl)
         else:
-            self.pools[sl.kind].append(sl)
+            self.pools[(sl.kind, sl.cls)].append(sl)
             self.cached += sl.nbytes
 
     # ----------------------------------------------------------- programs
@@ -422,7 +441,8 @@ class Server:
         got = sl.programs.get(key)
         if got is not None:
             return got
-        c, A, P = self.ctx, sl.A, G.Param
+        c, A, P = sl.ctx, sl.A, G.Param
+        sh = lambda key, t: self._shared(c, key, t)
         p = c.program()
         tails = []
         if r.kind == "VEC":
@@ -434,14 +454,14 @@ class Server:
             p.prefetch_host(A["z"], 0, 4)
         elif r.kind == "B&S":
             for i, St in enumerate(self.inp.data["B&S"]["S"]):
-                k = p.launch("bs_call", self._shared(("bs", i), St), A["C%d" % i], P("n"), *BS_PARAMS)
+                k = p.launch("bs_call", sh(("bs", i), St), A["C%d" % i], P("n"), *BS_PARAMS)
                 if i:
                     tails.append(k)
             p.prefetch_host(A["C0"], 0, P("resp"))
         elif r.kind == "IMG+ML":
             d = self.inp.data["IMG+ML"]
-            IMG = self._shared("img", d["img"])
-            w5, w9 = self._shared("w5", d["w5"]), self._shared("w9", d["w9"])
+            IMG = sh("img", d["img"])
+            w5, w9 = sh("w5", d["w5"]), sh("w9", d["w9"])
             side, npx = P("side"), P("npx")
             p.launch("gauss_blur", IMG, A["b5"], w5, side, side, IMG_R5)
             p.launch("gauss_blur", IMG, A["b9"], w9, side, side, IMG_R9)
@@ -453,13 +473,11 @@ class Server:
             p.launch("extend", A["e9"], A["mm9"], npx)
             p.launch("unsharp", IMG, A["b5"], A["sh"], IMG_ALPHA, npx)
             p.launch("combine", A["sh"], A["b5"], A["b9"], A["e5"], A["e9"], A["out"], npx)
-            X = self._shared("X", d["X"])
+            X = sh("X", d["X"])
             f, k_ = self.full.ml_feats, self.full.ml_classes
             rows = P("rows")
-            p.launch("dense_scores", X, self._shared("T1", d["T1"]), self._shared("b1", d["b1"]), A["s1"],
-                     rows, f, k_)
-            p.launch("dense_scores", X, self._shared("T2", d["T2"]), self._shared("b2", d["b2"]), A["s2"],
-                     rows, f, k_)
+            p.launch("dense_scores", X, sh("T1", d["T1"]), sh("b1", d["b1"]), A["s1"], rows, f, k_)
+            p.launch("dense_scores", X, sh("T2", d["T2"]), sh("b2", d["b2"]), A["s2"], rows, f, k_)
             p.launch("row_softmax", A["s1"], rows, k_)
             p.launch("row_softmax", A["s2"], rows, k_)
             tails.append(p.launch("argmax_combine", A["s1"], A["s2"], A["lab"], rows, k_))
@@ -468,7 +486,7 @@ class Server:
             k = r.size["bucket"]
             g = self.inp.data["HITS"][k]
             n, nnz = g["n"], g["nnz"]
-            GA, GAT, PA, PAT, ones = self._hits_shared(k)
+            GA, GAT, PA, PAT, ones = self._hits_shared(c, k)
             cur = (ones, ones)
             bufs = [(A["a2"], A["h2"]), (A["a"], A["h"])]
             for it in range(5):
@@ -487,7 +505,7 @@ class Server:
         else:
             d = self.inp.data["DL"]
             n, h, w = self.full.dl_n, self.full.dl_h, self.full.dl_w
-            S = lambda nm: self._shared(("dl", nm), d[nm])
+            S = lambda nm: sh(("dl", nm), d[nm])
             p.launch("conv3x3_relu_pool", S("x1"), S("w1"), S("b1"), A["p1"], A["st1"], n, h, w)
             p.launch("conv3x3_relu_pool", S("x2"), S("w2"), S("b2"), A["p2"], A["st2"], n, h, w)
             p.launch("avgpool_global", A["p1"], A["e1"], n * 64, (h // 2) * (w // 2))
@@ -528,13 +546,13 @@ class Server:
         requests as fused groups (when two or more share a kind), the rest
         one by one.  A call that fails fails the requests it was issuing
         (all members of a fused group) and no others."""
-        groups = {"VEC": [], "B&S": []}
+        groups = {}
         for r in rs:
             if self._fusable(r):
-                groups[r.kind].append(r)
+                groups.setdefault((r.kind, r.cls), []).append(r)
             else:
                 self._guarded([r], self.issue, r)
-        for kind, g in groups.items():
+        for g in groups.values():
             if len(g) == 1:
                 self._guarded(g, self.issue, g[0])
             elif g:
@@ -557,11 +575,11 @@ class Server:
                 r.slot.tainted = True
 
     def _issue_group(self, g):
-        """One program for a group of fusable requests of one kind: the
-        copies, one fused element per node kind, and one prefetch per
-        request (each request's sink; the fused elements are its
+        """One program for a group of fusable requests of one kind and
+        class: the copies, one fused element per node kind, and one prefetch
+        per request (each request's sink; the fused elements are its
         ancestors)."""
-        c = self.ctx
+        c = g[0].slot.ctx
         p = c.program()
         pref = []
         if g[0].kind == "VEC":
@@ -581,7 +599,7 @@ class Server:
             for r in g:
                 A, n = r.slot.A, r.size["n"]
                 for i, St in enumerate(self.inp.data["B&S"]["S"]):
-                    members.append((self._shared(("bs", i), St), A["C%d" % i], n) + BS_PARAMS)
+                    members.append((self._shared(c, ("bs", i), St), A["C%d" % i], n) + BS_PARAMS)
             p.launch_fused("bs_call", members)
             for r in g:
                 pref.append(p.prefetch_host(r.slot.A["C0"], 0, r.size["resp"]))
@@ -600,15 +618,15 @@ class Server:
             arr = sl.A[{"VEC": "z", "B&S": "C0", "IMG+ML": "out", "HITS": "a2", "DL": "logits"}[r.kind]]
             if r.kind == "DL":
                 # logits and the two status words, each from its own prefetch
-                self.ctx.read(arr, None, 0, nb - 8)
-                self.ctx.read(sl.A["st1"], None, 0, 4)
-                self.ctx.read(sl.A["st2"], None, 0, 4)
+                sl.ctx.read(arr, None, 0, nb - 8)
+                sl.ctx.read(sl.A["st1"], None, 0, 4)
+                sl.ctx.read(sl.A["st2"], None, 0, 4)
                 st = sl.host[self.full.dl_n * 10:self.full.dl_n * 10 + 2].view(torch.int32)
                 if int(st[0]) or int(st[1]):
                     r.error = G.GdagError(G.GDAG_ERR_TIMEOUT, "convolution status %d %d" % (int(st[0]), int(st[1])))
                     sl.tainted = True
             else:
-                self.ctx.read(arr, None, 0, nb)  # served from the completed prefetch
+                sl.ctx.read(arr, None, 0, nb)  # served from the completed prefetch
             r.resp_view = sl.host[: nb // 4].clone()
             if self.keep_results and r.error is None:
                 r.result = self._result(r)
@@ -647,8 +665,10 @@ class Server:
         for k in kinds:
             scales = [SCALE_MIN, 1.0] if k in SCALED else [1.0]
             for s in scales:
-                r = self._make(k, s)
-                self._run_alone(r)
+                for cls in self.ctxs:
+                    r = self._make(k, s)
+                    r.cls = cls
+                    self._run_alone(r)
         if calibrate:
             self.calibrate(kinds)
         gc.collect()
@@ -660,9 +680,9 @@ class Server:
         return r
 
     def _run_alone(self, r):
-        r.slot = self._take_slot(r.kind, True)
+        r.slot = self._take_slot(r.kind, True, r.cls)
         self.issue(r)
-        self.ctx.sync()
+        r.slot.ctx.sync()
         self.finish(r, 0.0)
 
     def calibrate(self, kinds=None, reps=3):
@@ -679,7 +699,7 @@ class Server:
                     r.slot = self._take_slot(k, True)
                     t0 = time.perf_counter()
                     self.issue(r)
-                    self.ctx.sync()
+                    r.slot.ctx.sync()
                     ts.append((time.perf_counter() - t0) * 1e3)
                     self.finish(r, 0.0)
                 pts.append((work_scale(self.full, k, s, self.inp.hits_buckets), float(np.median(ts))))
@@ -692,14 +712,20 @@ class Server:
         return dict(self.cost)
 
     # -------------------------------------------------------------- run
+    def classify(self, r):
+        """The request's class: "l" (long) if its estimate is above
+        split_ms, else "s"."""
+        return "l" if self.split_ms is not None and r.est > self.split_ms else "s"
+
     def run(self, requests, clock=time.perf_counter, spin=True):
         """Serve a list of requests (sorted by arrival, seconds from start)."""
-        pending = collections.deque()
+        pending = {c: collections.deque() for c in self.ctxs}
         inflight = []
         i = 0
         t0 = clock()
         done = 0
-        est_inflight = 0.0
+        est_inflight = {c: 0.0 for c in self.ctxs}
+        n_inflight = {c: 0 for c in self.ctxs}
         total = len(requests)
         full, B = self.full, self.inp.hits_buckets
         while done < total:
@@ -708,21 +734,26 @@ class Server:
                 r = requests[i]
                 r.size = sizes(full, r.kind, r.scale, B)
                 r.est = self.estimate(r)
-                pending.append(r)
+                r.cls = self.classify(r)
+                pending[r.cls].append(r)
                 i += 1
             batch = []
-            while pending:
-                r = pending[0]
-                busy = bool(inflight or batch)
-                if busy and self.window_ms is not None and est_inflight + r.est > self.window_ms:
-                    break
-                sl = self._take_slot(r.kind, not busy)
-                if sl is None:
-                    break
-                pending.popleft()
-                r.slot, r.need, r.admitted = sl, sl.nbytes, now
-                est_inflight += r.est
-                batch.append(r)
+            for c, q in pending.items():
+                # arrival order within the class; a class whose head cannot
+                # be admitted does not hold up the other class
+                while q:
+                    r = q[0]
+                    busy = n_inflight[c] > 0
+                    if busy and self.window_ms is not None and est_inflight[c] + r.est > self.window_ms:
+                        break
+                    sl = self._take_slot(r.kind, not (inflight or batch), c)
+                    if sl is None:
+                        break
+                    q.popleft()
+                    r.slot, r.need, r.admitted = sl, sl.nbytes, now
+                    est_inflight[c] += r.est
+                    n_inflight[c] += 1
+                    batch.append(r)
             if batch:
                 self.issue_batch(batch)
                 t = clock() - t0
@@ -730,28 +761,31 @@ class Server:
                     r.issued = t
                 inflight.extend(batch)
             if inflight:
-                flat = [n for r in inflight for n in r.sinks]
-                flags = self.ctx.done_many(flat) if flat else []
-                still, pos = [], 0
+                flags = {}
+                for c, ctx in self.ctxs.items():
+                    flat = [n for r in inflight if r.cls == c for n in r.sinks]
+                    flags[c] = iter(ctx.done_many(flat) if flat else [])
+                still = []
                 for r in inflight:
-                    k = len(r.sinks)
-                    if all(flags[pos:pos + k]):
-                        est_inflight -= r.est
+                    f = flags[r.cls]
+                    ok = all([next(f) for _ in r.sinks])
+                    if ok:
+                        est_inflight[r.cls] -= r.est
+                        n_inflight[r.cls] -= 1
+                        if not n_inflight[r.cls]:
+                            est_inflight[r.cls] = 0.0  # no drift from rounding
                         self.finish(r, clock() - t0)
                         done += 1
                     else:
                         still.append(r)
-                    pos += k
                 inflight = still
-                if not inflight:
-                    est_inflight = 0.0  # no drift from rounding
             if inflight and self.request_timeout_s is not None:
                 late = clock() - t0 - self.request_timeout_s
                 for r in inflight:
                     if r.admitted < late:
                         raise G.GdagError(G.GDAG_ERR_TIMEOUT, "request %d (%s) incomplete %.1f s after admission"
                                           % (r.rid, r.kind, self.request_timeout_s))
-            if not inflight and not pending and i < total:
+            if not inflight and not any(pending.values()) and i < total:
                 # idle until the next arrival
                 wait = requests[i].arrival - (clock() - t0)
                 if wait > 0 and not spin:
@@ -759,8 +793,9 @@ class Server:
         return requests
 
     def close(self):
-        self.ctx.sync()
-        self.ctx.close()
+        for ctx in self.ctxs.values():
+            ctx.sync()
+            ctx.close()
 
 
 def poisson_requests(rate, count, seed=0, kinds=KINDS):
@@ -799,5 +834,6 @@ def latency_summary(reqs, full=Full(), buckets=16):
     span = max(r.done_at for r in ok) - min(r.arrival for r in ok)
     out.update({"requests": len(ok), "failed": failed, "throughput_req_s": len(ok) / span,
                 "mean_work_scale": float(np.mean([work_scale(full, r.kind, r.scale, buckets) for r in ok])),
-                "by_kind": {k: stats([r for r in ok if r.kind == k]) for k in sorted({r.kind for r in ok})}})
+                "by_kind": {k: stats([r for r in ok if r.kind == k]) for k in sorted({r.kind for r in ok})},
+                "by_class": {c: stats([r for r in ok if r.cls == c]) for c in sorted({r.cls for r in ok})}})
     return out

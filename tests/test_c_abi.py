@@ -15,7 +15,7 @@ from paper_2012_09646_gb300 import gdag as G
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 INCLUDE = os.path.join(ROOT, "include")
 STRUCTS = [G.gdag_dim3, G.gdag_options, G.gdag_arg, G.gdag_argspec, G.gdag_edge, G.gdag_node_info, G.gdag_op,
-           G.gdag_trace_rec, G.gdag_stats]
+           G.gdag_trace_rec, G.gdag_stats, G.gdag_elem]
 
 PROGRAM = r"""
 #include "gdag.h"

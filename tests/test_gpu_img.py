@@ -19,6 +19,8 @@ TOL = 1e-5
 def check(got, ref, scale=1.0, what=""):
     got = np.asarray(got, np.float64).ravel()
     ref = np.asarray(ref, np.float64).ravel()
+    if np.ndim(scale):
+        scale = np.asarray(scale, np.float64).ravel()
     err = np.abs(got - ref) / np.maximum(np.abs(ref), scale)
     assert err.max() <= TOL, (what, err.max(), int(err.argmax()))
 

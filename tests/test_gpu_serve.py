@@ -175,7 +175,19 @@ def test_window_and_tiny_budget_serve_everything_in_order(inputs):
     srv = SV.Server(inputs, keep_results=True, window_ms=0.5)
     srv.warm(calibrate=True)
     assert all(a >= 0 and b >= 0 for a, b in srv.cost.values())
+    cost = dict(srv.cost)
     out = srv.run(fresh(reqs))
     srv.close()
+    for r in out:
+        check_with_oracle(inputs, r)
+    # two classes (long requests on their own context, short ones on
+    # high-priority streams): same results
+    split = sorted(a + b for a, b in cost.values())[len(cost) // 2]
+    srv = SV.Server(inputs, keep_results=True, window_ms=0.5, split_ms=split)
+    srv.warm()
+    srv.cost = cost
+    out = srv.run(fresh(SV.poisson_requests(50000.0, 30, seed=3)))
+    srv.close()
+    assert {r.cls for r in out} == {"s", "l"}
     for r in out:
         check_with_oracle(inputs, r)

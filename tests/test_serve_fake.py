@@ -333,3 +333,33 @@ def test_a_long_serving_run_holds_a_bounded_node_table(inputs):
     assert peak[0] <= 2 * trim and peak[1] <= 2 * trim, peak
     assert all(r.error is None for r in reqs)
     srv.close()
+
+
+def test_long_requests_do_not_hold_up_short_ones(inputs):
+    """With split_ms, requests estimated above it form their own class: a
+    long request at the head of the queue fills its window without holding
+    up the short ones behind it (each class keeps arrival order and its own
+    window); with one class the long request holds them up."""
+    burst = [SV.Request(0, "HITS", 1.0, 0.0)] + [SV.Request(i, "VEC", SCALES[0], 0.0) for i in range(1, 5)]
+    first = {}
+    for split in (None, 5.0):
+        srv = server(inputs, window_ms=2.0, split_ms=split)
+        srv.cost = {k: (1.0, 0.0) for k in SV.KINDS}
+        srv.cost["HITS"] = (10.0, 0.0)
+        batches = []
+        issue_batch = srv.issue_batch
+
+        def watched(batch, batches=batches, issue_batch=issue_batch):
+            batches.append([(r.kind, r.cls) for r in batch])
+            issue_batch(batch)
+        srv.issue_batch = watched
+        out = srv.run(fresh(burst))
+        assert all(r.done_at is not None and r.error is None for r in out)
+        first[split] = batches[0]
+        if split is not None:
+            assert {r.cls for r in out} == {"s", "l"} and out[0].cls == "l"
+            s = SV.latency_summary(out)
+            assert set(s["by_class"]) == {"s", "l"}
+        srv.close()
+    assert first[None] == [("HITS", "s")]
+    assert sorted(first[5.0]) == [("HITS", "l"), ("VEC", "s"), ("VEC", "s")]
