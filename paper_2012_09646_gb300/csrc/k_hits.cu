@@ -241,54 +241,107 @@ __global__ void __launch_bounds__(256) spmv_fixup_kernel(const int2 *__restrict_
     }
 }
 
-// norm[0] = sqrt(sum x_i^2): per thread Kahan fp32, per block fp64 tree,
-// blocks combined in order by the last one to arrive.
-__global__ void __launch_bounds__(kThreads) l2norm_kernel(const float *__restrict__ x, float *__restrict__ norm,
-                                                          double *scratch, int64_t n)
+// norm[0] = sqrt(sum x_i^2).  Each 128-thread block takes chunks of 2048
+// float4 (32 KB) and issues all sixteen 128-bit loads of a thread at once,
+// so a vector of a few tens of MB is requested in about one memory latency
+// (blocks that walked a grid-stride loop waited for several rounds).  A
+// thread sums its 64 squares as a fixed pairwise tree in fp32 (error a few
+// ulp of the chunk's sum, and no dependent chain as in compensated
+// summation) and its chunks in fp64; each block sums its threads in an fp64
+// tree.  The blocks' partials are combined in two levels so that no single
+// counter takes one atomic per block: the last block of each group of 32 to
+// arrive adds the group's partials (one per lane, a fixed warp tree), and
+// the last group adds the groups' sums the same way.  The grid depends only
+// on n, so the order of every addition, and the result, is the same on
+// every run.
+constexpr int kL2Threads = 128;
+constexpr int kL2V = 16;                               // float4 per thread per chunk
+constexpr int kL2Chunk4 = kL2Threads * kL2V;           // 2048 float4
+constexpr int kL2MaxBlocks = 4096;
+constexpr int kL2Group = 32;
+constexpr int kL2MaxGroups = kL2MaxBlocks / kL2Group;
+// scratch: block partials, group sums (doubles), group counters, the top
+// counter (32-bit, zero between launches)
+constexpr size_t kL2ScratchBytes = (size_t)(kL2MaxBlocks + kL2MaxGroups) * 8 + (size_t)(kL2MaxGroups + 1) * 4 + 16;
+
+inline unsigned l2norm_grid(int64_t n)
 {
-    __shared__ double sh[kThreads / 32];
-    Kahan acc;
+    const int64_t chunks = ceil_div(n >> 2, kL2Chunk4);
+    return (unsigned)(chunks < 1 ? 1 : (chunks < kL2MaxBlocks ? chunks : kL2MaxBlocks));
+}
+
+__global__ void __launch_bounds__(kL2Threads) l2norm_kernel(const float *__restrict__ x, float *__restrict__ norm,
+                                                            double *scratch, int64_t n)
+{
+    __shared__ double sh[kL2Threads / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const float4 *x4 = reinterpret_cast<const float4 *>(x);
+    const int64_t n4 = n >> 2, chunks = (n4 + kL2Chunk4 - 1) / kL2Chunk4;
+    double acc = 0.0;
     if ((reinterpret_cast<uintptr_t>(x) & 15) == 0) {
-        const float4 *x4 = reinterpret_cast<const float4 *>(x);
-        const int64_t n4 = n >> 2, tile = (int64_t)kThreads * kUnroll;
-        for (int64_t base = (int64_t)blockIdx.x * tile; base < n4; base += (int64_t)gridDim.x * tile) {
-            float4 v[kUnroll];
+        for (int64_t c = blockIdx.x; c < chunks; c += gridDim.x) {
+            float4 v[kL2V];
 #pragma unroll
-            for (int k = 0; k < kUnroll; ++k) {
-                int64_t i = base + threadIdx.x + (int64_t)k * kThreads;
-                if (i < n4) v[k] = x4[i];
+            for (int u = 0; u < kL2V; ++u) {
+                const int64_t i = c * kL2Chunk4 + threadIdx.x + (int64_t)u * kL2Threads;
+                v[u] = i < n4 ? __ldcs(x4 + i) : make_float4(0.f, 0.f, 0.f, 0.f);
             }
+            float q[kL2V];
 #pragma unroll
-            for (int k = 0; k < kUnroll; ++k) {
-                int64_t i = base + threadIdx.x + (int64_t)k * kThreads;
-                if (i < n4) {
-                    acc.add(v[k].x * v[k].x);
-                    acc.add(v[k].y * v[k].y);
-                    acc.add(v[k].z * v[k].z);
-                    acc.add(v[k].w * v[k].w);
-                }
-            }
+            for (int u = 0; u < kL2V; ++u) q[u] = (v[u].x * v[u].x + v[u].y * v[u].y) + (v[u].z * v[u].z + v[u].w * v[u].w);
+#pragma unroll
+            for (int w = kL2V / 2; w > 0; w >>= 1)
+#pragma unroll
+                for (int u = 0; u < w; ++u) q[u] += q[u + w];
+            acc += (double)q[0];
         }
         if (blockIdx.x == 0 && threadIdx.x < (n & 3)) {
             const float t = x[(n4 << 2) + threadIdx.x];
-            acc.add(t * t);
+            acc += (double)(t * t);
         }
     } else {
-        for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-            acc.add(x[i] * x[i]);
+        for (int64_t i = (int64_t)blockIdx.x * kL2Threads + threadIdx.x; i < n; i += (int64_t)gridDim.x * kL2Threads)
+            acc += (double)(x[i] * x[i]);
     }
-    const double bs = block_sum(acc.value(), sh);
-    if (threadIdx.x == 0) scratch[blockIdx.x] = bs;
-    unsigned *counter = reinterpret_cast<unsigned *>(scratch + kReduceMaxBlocks);
-    if (!arrive_last(counter)) return;
+    acc = warp_sum(acc);
+    if (lane == 0) sh[warp] = acc;
+    __syncthreads();
+    if (warp != 0) return;
+    double bsum = lane < kL2Threads / 32 ? sh[lane] : 0.0;
+    bsum = warp_sum(bsum);
+    double *part = scratch, *gpart = scratch + kL2MaxBlocks;
+    unsigned *gcnt = reinterpret_cast<unsigned *>(scratch + kL2MaxBlocks + kL2MaxGroups), *top = gcnt + kL2MaxGroups;
+    const unsigned b = blockIdx.x, grp = b / kL2Group, ngroups = (gridDim.x + kL2Group - 1) / kL2Group;
+    const unsigned gsize = gridDim.x - grp * kL2Group < (unsigned)kL2Group ? gridDim.x - grp * kL2Group : kL2Group;
+    int last = 0;
+    if (lane == 0) {
+        part[b] = bsum;
+        __threadfence();  // the partial visible device-wide before the arrival
+        last = atomicAdd(&gcnt[grp], 1u) == gsize - 1;
+    }
+    if (!__shfl_sync(0xffffffffu, last, 0)) return;
+    __threadfence();  // every partial of the group visible
+    double g = lane < (int)gsize ? ((volatile double *)part)[grp * kL2Group + lane] : 0.0;
+    g = warp_sum(g);
+    last = 0;
+    if (lane == 0) {
+        gpart[grp] = g;
+        gcnt[grp] = 0u;
+        __threadfence();
+        last = atomicAdd(top, 1u) == ngroups - 1;
+    }
+    if (!__shfl_sync(0xffffffffu, last, 0)) return;
+    __threadfence();
     double t = 0.0;
-    for (unsigned b = threadIdx.x; b < gridDim.x; b += kThreads) t += ((volatile double *)scratch)[b];
-    t = block_sum(t, sh);
-    if (threadIdx.x == 0) {
+    for (unsigned i = lane; i < ngroups; i += 32) t += ((volatile double *)gpart)[i];
+    t = warp_sum(t);
+    if (lane == 0) {
         norm[0] = (float)sqrt(t);
-        *counter = 0u;
+        *top = 0u;
     }
 }
+
+size_t l2norm_scratch_bytes() { return kL2ScratchBytes; }
 
 // x := x / norm[0], correctly rounded (div_by); a zero norm leaves x
 // unchanged.
@@ -327,9 +380,9 @@ __global__ void __launch_bounds__(1024) scale_kernel(float *__restrict__ x, cons
 
 size_t seg_norm_scratch_bytes(int64_t G);
 
-// Segments are cut into kSegSlices equal slices; block (slice, g) handles
-// one slice of segment g.  Segment bounds are clamped to [0, n], so a
-// malformed seg array cannot index outside x.
+// seg_scale cuts each segment into kSegSlices equal slices; block (slice,
+// g) handles one slice of segment g.  Segment bounds are clamped to [0, n],
+// so a malformed seg array cannot index outside x.
 constexpr int kSegSlices = 32;
 
 __device__ __forceinline__ void seg_slice(const int *__restrict__ seg, int g, int sl, int n, int &lo, int &hi)
@@ -342,60 +395,112 @@ __device__ __forceinline__ void seg_slice(const int *__restrict__ seg, int g, in
     hi = b + (int)(len * (sl + 1) / kSegSlices);
 }
 
-// norms[g] = sqrt(sum of x_i^2 over segment g): Kahan fp32 per thread, fp64
-// block tree per slice; the last slice of a segment to arrive adds the
-// slices' partials in slice order (the result does not depend on timing) and
-// resets the segment's arrival counter.
+// norms[g] = sqrt(sum of x_i^2 over segment g), as a segmented reduction
+// over fixed chunks of x: block b takes elements [b ch, (b+1) ch) whatever
+// the segments, so every block issues one round of 128-bit loads however
+// long the segments are (a slice per block of each segment made the blocks
+// of a million-vertex segment walk tens of dependent rounds).  A segment
+// inside the chunk is finished by the block; a segment that spans chunks
+// gets one partial from each of its chunks (its first chunk's in part_hi,
+// the others' in part_lo), and the last of those blocks to arrive adds them
+// in chunk order and resets the segment's arrival counter.  Kahan fp32 per
+// thread, fp64 block tree: the same sums on every run.  An empty segment is
+// written (0) by the block whose chunk holds its position (the last block
+// for a segment at n).  Segment bounds are clamped to [0, n], so a
+// malformed seg array cannot index outside x.
+constexpr int kSegChunk = 4096;          // elements per chunk unit (16 KB)
+constexpr int kSegMaxChunks = 65536;     // chunks per launch (the scratch's partials)
+
+__device__ __forceinline__ void seg_bounds(const int *__restrict__ seg, int g, int n, int &lo, int &hi)
+{
+    int b = seg[g], e = seg[g + 1];
+    b = b < 0 ? 0 : (b > n ? n : b);
+    e = e < b ? b : (e > n ? n : e);
+    lo = b;
+    hi = e;
+}
+
 __global__ void __launch_bounds__(kThreads) seg_l2norm_kernel(const float *__restrict__ x, const int *__restrict__ seg,
-                                                              float *__restrict__ norms, double *scratch, int G, int n)
+                                                              float *__restrict__ norms, double *scratch, int G, int n,
+                                                              int ch)
 {
     __shared__ double sh[kThreads / 32];
-    __shared__ bool last;
-    const int g = blockIdx.y, sl = blockIdx.x;
-    int lo, hi;
-    seg_slice(seg, g, sl, n, lo, hi);
-    Kahan acc;
-    // scalar head up to a 16-byte boundary, float4 body, scalar tail (x
-    // itself is 16-byte aligned: checked on the host)
-    const int a0 = min(hi, (lo + 3) & ~3), a1 = max(a0, hi & ~3);
-    for (int i = lo + threadIdx.x; i < a0; i += kThreads) acc.add(x[i] * x[i]);
-    const float4 *x4 = reinterpret_cast<const float4 *>(x);
-    int j = (a0 >> 2) + threadIdx.x;
-    for (; j + kThreads < (a1 >> 2); j += 2 * kThreads) {
-        const float4 u = x4[j], v = x4[j + kThreads];
-        acc.add(u.x * u.x);
-        acc.add(u.y * u.y);
-        acc.add(u.z * u.z);
-        acc.add(u.w * u.w);
-        acc.add(v.x * v.x);
-        acc.add(v.y * v.y);
-        acc.add(v.z * v.z);
-        acc.add(v.w * v.w);
-    }
-    for (; j < (a1 >> 2); j += kThreads) {
-        const float4 u = x4[j];
-        acc.add(u.x * u.x);
-        acc.add(u.y * u.y);
-        acc.add(u.z * u.z);
-        acc.add(u.w * u.w);
-    }
-    for (int i = a1 + threadIdx.x; i < hi; i += kThreads) acc.add(x[i] * x[i]);
-    const double bs = block_sum(acc.value(), sh);
-    double *part = scratch + (size_t)g * kSegSlices;
-    unsigned *counter = reinterpret_cast<unsigned *>(scratch + (size_t)G * kSegSlices) + g;
-    if (threadIdx.x == 0) part[sl] = bs;
-    __threadfence();  // the partial visible device-wide before the arrival
-    __syncthreads();
-    if (threadIdx.x == 0) last = atomicAdd(counter, 1u) == (unsigned)(kSegSlices - 1);
-    __syncthreads();
-    if (!last) return;
-    __threadfence();  // every slice's partial visible
+    __shared__ int s_first;
+    const int b = blockIdx.x, nb = gridDim.x;
+    const int c0 = (int)((int64_t)b * ch), c1 = (int)((int64_t)c0 + ch < n ? (int64_t)c0 + ch : n);
+    double *part_lo = scratch, *part_hi = scratch + kSegMaxChunks;
+    unsigned *cnt = reinterpret_cast<unsigned *>(scratch + 2 * kSegMaxChunks);
     if (threadIdx.x == 0) {
-        double t = 0.0;
-        for (int k = 0; k < kSegSlices; ++k) t += ((volatile double *)part)[k];
-        norms[g] = (float)sqrt(t);
-        *counter = 0u;
+        // the first segment whose (clamped) end is at or after c0
+        int lo = 0, hi = G;
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            int a, e;
+            seg_bounds(seg, mid, n, a, e);
+            if (e >= c0) hi = mid;
+            else lo = mid + 1;
+        }
+        s_first = lo;
     }
+    __syncthreads();
+    const float4 *x4 = reinterpret_cast<const float4 *>(x);
+    for (int g = s_first; g < G; ++g) {
+        int lo, hi;
+        seg_bounds(seg, g, n, lo, hi);  // the same values in every thread
+        if (lo > c1) break;
+        if (lo == hi) {
+            if (threadIdx.x == 0 && ((lo >= c0 && lo < c1) || (b == nb - 1 && lo == n))) norms[g] = 0.f;
+            continue;
+        }
+        if (hi <= c0 || lo >= c1) continue;
+        const int a = lo > c0 ? lo : c0, e = hi < c1 ? hi : c1;
+        Kahan acc;
+        // scalar head up to a 16-byte boundary, float4 body, scalar tail
+        const int a0 = min(e, (a + 3) & ~3), a1 = max(a0, e & ~3);
+        for (int i = a + threadIdx.x; i < a0; i += kThreads) acc.add(x[i] * x[i]);
+        for (int j = (a0 >> 2) + threadIdx.x; j < (a1 >> 2); j += kUnroll * kThreads) {
+            float4 v[kUnroll];
+#pragma unroll
+            for (int u = 0; u < kUnroll; ++u) {
+                const int q = j + u * kThreads;
+                v[u] = q < (a1 >> 2) ? x4[q] : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+#pragma unroll
+            for (int u = 0; u < kUnroll; ++u) {
+                acc.add(v[u].x * v[u].x);
+                acc.add(v[u].y * v[u].y);
+                acc.add(v[u].z * v[u].z);
+                acc.add(v[u].w * v[u].w);
+            }
+        }
+        for (int i = a1 + threadIdx.x; i < e; i += kThreads) acc.add(x[i] * x[i]);
+        const double sum = block_sum(acc.value(), sh);
+        if (threadIdx.x == 0) {
+            if (lo >= c0 && hi <= c1) {
+                norms[g] = (float)sqrt(sum);
+            } else {
+                const int bf = lo / ch, bl = (hi - 1) / ch;
+                if (b == bf) part_hi[b] = sum;
+                else part_lo[b] = sum;
+                __threadfence();  // the partial visible device-wide before the arrival
+                if (atomicAdd(&cnt[g], 1u) == (unsigned)(bl - bf)) {
+                    __threadfence();  // every chunk's partial visible
+                    double t = ((volatile double *)part_hi)[bf];
+                    for (int q = bf + 1; q <= bl; ++q) t += ((volatile double *)part_lo)[q];
+                    norms[g] = (float)sqrt(t);
+                    cnt[g] = 0u;
+                }
+            }
+        }
+    }
+}
+
+// Chunk length for n elements: a multiple of kSegChunk with at most
+// kSegMaxChunks chunks.
+inline int seg_chunk_len(int n)
+{
+    const int64_t units = ceil_div(n > 0 ? n : 1, (int64_t)kSegChunk * kSegMaxChunks);
+    return (int)(units * kSegChunk);
 }
 
 // x := x / norms[g] over segment g, correctly rounded (div_by); a zero norm
@@ -476,15 +581,15 @@ const char *validate_l2norm(const LaunchArgs &a)
     if (n < 0) return "n < 0";
     if (a.bytes[0] / 4 < (size_t)n) return "x smaller than n floats";
     if (a.bytes[1] < 4) return "norm smaller than one float";
-    if (a.bytes[2] < reduce_scratch_bytes<1>()) return "scratch smaller than gdag_scratch_bytes()";
+    if (a.bytes[2] < kL2ScratchBytes) return "scratch smaller than gdag_scratch_bytes()";
     return nullptr;
 }
 
 int launch_l2norm(const LaunchArgs &a, void *s)
 {
     const int64_t n = a.i64(3);
-    l2norm_kernel<<<reduce_grid(n >> 2), kThreads, 0, (cudaStream_t)s>>>(a.p<float>(0), a.p<float>(1),
-                                                                         a.p<double>(2), n);
+    l2norm_kernel<<<l2norm_grid(n), kL2Threads, 0, (cudaStream_t)s>>>(a.p<float>(0), a.p<float>(1), a.p<double>(2),
+                                                                     n);
     return cudaGetLastError();
 }
 
@@ -526,10 +631,12 @@ const char *validate_seg_l2norm(const LaunchArgs &a)
 
 int launch_seg_l2norm(const LaunchArgs &a, void *s)
 {
-    const int G = a.i32(4);
+    const int G = a.i32(4), n = a.i32(5);
     if (G == 0) return cudaSuccess;
-    seg_l2norm_kernel<<<dim3(kSegSlices, G), kThreads, 0, (cudaStream_t)s>>>(a.p<float>(0), a.p<int>(1), a.p<float>(2),
-                                                                           a.p<double>(3), G, a.i32(5));
+    const int ch = seg_chunk_len(n);
+    const int64_t chunks = ceil_div(n > 0 ? n : 1, ch);
+    seg_l2norm_kernel<<<(unsigned)chunks, kThreads, 0, (cudaStream_t)s>>>(a.p<float>(0), a.p<int>(1), a.p<float>(2),
+                                                                        a.p<double>(3), G, n, ch);
     return cudaGetLastError();
 }
 
@@ -560,7 +667,10 @@ KernelEntry entry(const char *name, const void *fn, std::initializer_list<gdag_a
 
 }  // namespace
 
-size_t seg_norm_scratch_bytes(int64_t G) { return (size_t)(G > 0 ? G : 0) * (kSegSlices * 8 + 4) + 16; }
+size_t seg_norm_scratch_bytes(int64_t G)
+{
+    return (size_t)2 * kSegMaxChunks * 8 + (size_t)(G > 0 ? G : 0) * 4 + 16;  // partials, counters
+}
 size_t spmv_part_bytes(int64_t rows_plus_nnz) { return (size_t)(ceil_div(rows_plus_nnz > 0 ? rows_plus_nnz : 1, kSpmvTile) + 1) * 8; }
 size_t spmv_carry_bytes(int64_t rows_plus_nnz) { return (size_t)ceil_div(rows_plus_nnz > 0 ? rows_plus_nnz : 1, kSpmvTile) * 4 + 16; }
 

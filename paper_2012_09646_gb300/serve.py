@@ -253,7 +253,7 @@ class Server:
     def __init__(self, inputs, budget_bytes=40 << 30, max_streams=32, device="cuda", fuse_max=None,
                  backend="cuda", record_log=False, fake_fail_op=-1, fake_fail_sticky=False, fake_complete=None,
                  request_timeout_s=120.0, trim_nodes=0, window_ms=None, keep_results=False, split_ms=None,
-                 short_priority=-5):
+                 short_priority=-5, long_window_ms=None):
         """``fuse_max``: {kind: largest node size (elements) that is fused
         across requests}; None or {} turns fusion off.  ``window_ms``: the
         largest estimated GPU time of admitted, unfinished requests (None:
@@ -272,7 +272,8 @@ class Server:
         it completes (``request.result``).  ``split_ms``: requests estimated
         above it form the long class (its own queue, window and context);
         the short class's context creates its streams at CUDA priority
-        ``short_priority`` (None: one class)."""
+        ``short_priority`` (None: one class); ``long_window_ms`` is the long
+        class's window (default: ``window_ms``)."""
         self.inp = inputs
         self.full = inputs.full
         self.fuse_max = dict(fuse_max or {})
@@ -281,6 +282,7 @@ class Server:
         self.cached = 0   # bytes of idle slots in the pools
         self.device = device
         self.window_ms = window_ms
+        self.windows = {"s": window_ms, "l": window_ms if long_window_ms is None else long_window_ms}
         self.keep_results = keep_results
         self.split_ms = split_ms
 
@@ -744,7 +746,8 @@ class Server:
                 while q:
                     r = q[0]
                     busy = n_inflight[c] > 0
-                    if busy and self.window_ms is not None and est_inflight[c] + r.est > self.window_ms:
+                    w = self.windows[c]
+                    if busy and w is not None and est_inflight[c] + r.est > w:
                         break
                     sl = self._take_slot(r.kind, not (inflight or batch), c)
                     if sl is None:
