@@ -409,7 +409,7 @@ __device__ __forceinline__ void seg_slice(const int *__restrict__ seg, int g, in
 // for a segment at n).  Segment bounds are clamped to [0, n], so a
 // malformed seg array cannot index outside x.
 constexpr int kSegChunk = 4096;          // elements per chunk unit (16 KB)
-constexpr int kSegMaxChunks = 65536;     // chunks per launch (the scratch's partials)
+constexpr int kSegMaxChunks = 65536;     // units of kSegChunk elements (the scratch's partials)
 
 __device__ __forceinline__ void seg_bounds(const int *__restrict__ seg, int g, int n, int &lo, int &hi)
 {
@@ -430,77 +430,100 @@ __global__ void __launch_bounds__(kThreads) seg_l2norm_kernel(const float *__res
     const int c0 = (int)((int64_t)b * ch), c1 = (int)((int64_t)c0 + ch < n ? (int64_t)c0 + ch : n);
     double *part_lo = scratch, *part_hi = scratch + kSegMaxChunks;
     unsigned *cnt = reinterpret_cast<unsigned *>(scratch + 2 * kSegMaxChunks);
-    if (threadIdx.x == 0) {
-        // the first segment whose (clamped) end is at or after c0
-        int lo = 0, hi = G;
-        while (lo < hi) {
-            const int mid = (lo + hi) >> 1;
-            int a, e;
-            seg_bounds(seg, mid, n, a, e);
-            if (e >= c0) hi = mid;
-            else lo = mid + 1;
-        }
-        s_first = lo;
-    }
-    __syncthreads();
     const float4 *x4 = reinterpret_cast<const float4 *>(x);
-    for (int g = s_first; g < G; ++g) {
-        int lo, hi;
-        seg_bounds(seg, g, n, lo, hi);  // the same values in every thread
-        if (lo > c1) break;
-        if (lo == hi) {
-            if (threadIdx.x == 0 && ((lo >= c0 && lo < c1) || (b == nb - 1 && lo == n))) norms[g] = 0.f;
-            continue;
-        }
-        if (hi <= c0 || lo >= c1) continue;
-        const int a = lo > c0 ? lo : c0, e = hi < c1 ? hi : c1;
-        Kahan acc;
-        // scalar head up to a 16-byte boundary, float4 body, scalar tail
-        const int a0 = min(e, (a + 3) & ~3), a1 = max(a0, e & ~3);
-        for (int i = a + threadIdx.x; i < a0; i += kThreads) acc.add(x[i] * x[i]);
-        for (int j = (a0 >> 2) + threadIdx.x; j < (a1 >> 2); j += kUnroll * kThreads) {
-            float4 v[kUnroll];
+    constexpr int kPer = kSegChunk / 4 / kThreads;  // float4 per thread per 4096-element unit
+    for (int u0 = c0; u0 < c1 || (u0 == c0 && c0 == c1); u0 += kSegChunk) {
+        const int u1 = u0 + kSegChunk < c1 ? u0 + kSegChunk : c1;
+        // the unit's loads first (they do not depend on the segments), so
+        // the segment lookup below overlaps their latency
+        float4 v[kPer];
 #pragma unroll
-            for (int u = 0; u < kUnroll; ++u) {
-                const int q = j + u * kThreads;
-                v[u] = q < (a1 >> 2) ? x4[q] : make_float4(0.f, 0.f, 0.f, 0.f);
-            }
-#pragma unroll
-            for (int u = 0; u < kUnroll; ++u) {
-                acc.add(v[u].x * v[u].x);
-                acc.add(v[u].y * v[u].y);
-                acc.add(v[u].z * v[u].z);
-                acc.add(v[u].w * v[u].w);
-            }
-        }
-        for (int i = a1 + threadIdx.x; i < e; i += kThreads) acc.add(x[i] * x[i]);
-        const double sum = block_sum(acc.value(), sh);
-        if (threadIdx.x == 0) {
-            if (lo >= c0 && hi <= c1) {
-                norms[g] = (float)sqrt(sum);
+        for (int k = 0; k < kPer; ++k) {
+            const int i = u0 + 4 * (threadIdx.x + k * kThreads);  // u0 is a multiple of 4096
+            if (i + 3 < u1) {
+                v[k] = x4[i >> 2];
             } else {
-                const int bf = lo / ch, bl = (hi - 1) / ch;
-                if (b == bf) part_hi[b] = sum;
-                else part_lo[b] = sum;
-                __threadfence();  // the partial visible device-wide before the arrival
-                if (atomicAdd(&cnt[g], 1u) == (unsigned)(bl - bf)) {
-                    __threadfence();  // every chunk's partial visible
-                    double t = ((volatile double *)part_hi)[bf];
-                    for (int q = bf + 1; q <= bl; ++q) t += ((volatile double *)part_lo)[q];
-                    norms[g] = (float)sqrt(t);
-                    cnt[g] = 0u;
+                v[k].x = i < u1 ? x[i] : 0.f;
+                v[k].y = i + 1 < u1 ? x[i + 1] : 0.f;
+                v[k].z = i + 2 < u1 ? x[i + 2] : 0.f;
+                v[k].w = 0.f;
+            }
+        }
+        if (threadIdx.x == 0) {
+            // the first segment whose (clamped) end is at or after u0
+            int lo = 0, hi = G;
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                int a, e;
+                seg_bounds(seg, mid, n, a, e);
+                if (e >= u0) hi = mid;
+                else lo = mid + 1;
+            }
+            s_first = lo;
+        }
+        __syncthreads();
+        const int first = s_first;
+        __syncthreads();  // s_first is rewritten by the next unit
+        for (int g = first; g < G; ++g) {
+            int lo, hi;
+            seg_bounds(seg, g, n, lo, hi);  // the same values in every thread
+            if (lo > u1) break;
+            if (lo == hi) {
+                // an empty segment: written by the block whose chunk holds
+                // its position (the last block for one at n)
+                if (threadIdx.x == 0 && ((lo >= u0 && lo < u1) || (b == nb - 1 && lo == n && u1 == c1))) norms[g] = 0.f;
+                continue;
+            }
+            if (hi <= u0 || lo >= u1) continue;
+            Kahan acc;
+#pragma unroll
+            for (int k = 0; k < kPer; ++k) {
+                const int i = u0 + 4 * (threadIdx.x + k * kThreads);
+                if (i >= lo && i + 3 < hi) {
+                    acc.add(v[k].x * v[k].x);
+                    acc.add(v[k].y * v[k].y);
+                    acc.add(v[k].z * v[k].z);
+                    acc.add(v[k].w * v[k].w);
+                } else {
+                    if (i >= lo && i < hi) acc.add(v[k].x * v[k].x);
+                    if (i + 1 >= lo && i + 1 < hi) acc.add(v[k].y * v[k].y);
+                    if (i + 2 >= lo && i + 2 < hi) acc.add(v[k].z * v[k].z);
+                    if (i + 3 >= lo && i + 3 < hi) acc.add(v[k].w * v[k].w);
+                }
+            }
+            const double sum = block_sum(acc.value(), sh);
+            if (threadIdx.x == 0) {
+                if (lo >= u0 && hi <= u1) {
+                    norms[g] = (float)sqrt(sum);
+                } else {
+                    // a segment spanning units: one partial per unit, in
+                    // unit order (a unit is kSegChunk elements)
+                    const int uf = lo / kSegChunk, ul = (hi - 1) / kSegChunk, me = u0 / kSegChunk;
+                    if (me == uf) part_hi[me] = sum;
+                    else part_lo[me] = sum;
+                    __threadfence();  // the partial visible device-wide before the arrival
+                    if (atomicAdd(&cnt[g], 1u) == (unsigned)(ul - uf)) {
+                        __threadfence();  // every unit's partial visible
+                        double t = ((volatile double *)part_hi)[uf];
+                        for (int q = uf + 1; q <= ul; ++q) t += ((volatile double *)part_lo)[q];
+                        norms[g] = (float)sqrt(t);
+                        cnt[g] = 0u;
+                    }
                 }
             }
         }
+        if (c0 == c1) break;
     }
 }
 
-// Chunk length for n elements: a multiple of kSegChunk with at most
-// kSegMaxChunks chunks.
+// Chunk length for n elements: a multiple of kSegChunk, one unit a block
+// while the grid stays within about 8 resident waves, more units a block
+// beyond that.
 inline int seg_chunk_len(int n)
 {
-    const int64_t units = ceil_div(n > 0 ? n : 1, (int64_t)kSegChunk * kSegMaxChunks);
-    return (int)(units * kSegChunk);
+    const int64_t units = ceil_div(n > 0 ? n : 1, kSegChunk);
+    const int64_t per = ceil_div(units, (int64_t)sm_count() * 64);
+    return (int)(per * kSegChunk);
 }
 
 // x := x / norms[g] over segment g, correctly rounded (div_by); a zero norm
@@ -625,6 +648,7 @@ const char *validate_seg_common(const LaunchArgs &a, int gi, int ni)
 const char *validate_seg_l2norm(const LaunchArgs &a)
 {
     if (const char *m = validate_seg_common(a, 4, 5)) return m;
+    if ((int64_t)a.i32(5) > (int64_t)kSegChunk * kSegMaxChunks) return "n above 268435456 elements";
     if (a.bytes[3] < seg_norm_scratch_bytes(a.i32(4))) return "scratch smaller than gdag_scratch_bytes(\"seg_l2norm\", G)";
     return nullptr;
 }

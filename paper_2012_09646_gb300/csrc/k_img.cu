@@ -17,208 +17,147 @@
 
 namespace gdag {
 
-constexpr int kTileW = 64, kTileH = 32;   // output tile of one 256-thread block
-constexpr int kImgThreads = 256;
 constexpr int kMaxRadius = 8;
 
 __device__ __forceinline__ int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
 
-// Stage rows y0-R .. y0+kTileH+R-1 and columns x0-HALO .. x0+kTileW+HALO-1 of
-// the image into s (row stride IW = kTileW + 2 HALO, HALO a multiple of 4),
-// clamping coordinates to the image.  Interior blocks of an image whose
-// rows are 16-byte aligned use 128-bit loads; border blocks clamp per pixel.
-template <int R, int HALO, int IW>
-__device__ __forceinline__ void stage_tile(const float *__restrict__ in, float *s, int rows, int cols, int x0, int y0)
+// Warp-strip stencils.  Each warp owns a strip of image columns, four per
+// lane (one 128-bit load per row and lane), and slides down a band of rows:
+// the vertical taps come from a window of rows kept in registers (each input
+// row is loaded once), the horizontal taps from the neighbouring lanes'
+// registers by warp shuffles, so there is no shared memory and no block
+// barrier.  The HL lanes at each end of a warp are halo lanes: they load
+// and filter the columns next to the strip (replicated at the image edge)
+// but store nothing, so a strip is 4 (32 - 2 HL) columns wide.  Rows and
+// columns outside the image take the nearest edge value (clamp-to-edge).
+constexpr int kStWarps = 4;
+constexpr int kStThreads = 32 * kStWarps;
+constexpr unsigned kFull = 0xffffffffu;
+
+// Pixels x .. x+3 of row y, clamped to the image; one 128-bit load when the
+// four lie inside the image and rows are 16-byte aligned (vec).
+__device__ __forceinline__ float4 load4_clamped(const float *__restrict__ in, int rows, int cols, bool vec, int y, int x)
 {
-    constexpr int IH = kTileH + 2 * R;
-    const bool fast = (cols & 3) == 0 && (reinterpret_cast<uintptr_t>(in) & 15) == 0 && x0 >= HALO &&
-                      x0 + kTileW + HALO <= cols;
-    if (fast) {
-        constexpr int V = IW / 4;  // float4 per staged row
-        constexpr int PER = (IH * V + kImgThreads - 1) / kImgThreads;
-        float4 v[PER];  // every load of the thread in flight before any store
-#pragma unroll
-        for (int k = 0; k < PER; ++k) {
-            const int i = threadIdx.x + k * kImgThreads;
-            if (i < IH * V) {
-                const int r = i / V, c4 = i - r * V;
-                const int y = clampi(y0 + r - R, 0, rows - 1);
-                v[k] = *reinterpret_cast<const float4 *>(in + (size_t)y * cols + (x0 - HALO) + 4 * c4);
-            }
-        }
-#pragma unroll
-        for (int k = 0; k < PER; ++k) {
-            const int i = threadIdx.x + k * kImgThreads;
-            if (i < IH * V) {
-                const int r = i / V, c4 = i - r * V;
-                *reinterpret_cast<float4 *>(s + r * IW + 4 * c4) = v[k];
-            }
-        }
+    const float *row = in + (size_t)clampi(y, 0, rows - 1) * cols;
+    if (vec && x >= 0 && x + 3 < cols) return __ldg(reinterpret_cast<const float4 *>(row + x));
+    return make_float4(__ldg(row + clampi(x, 0, cols - 1)), __ldg(row + clampi(x + 1, 0, cols - 1)),
+                       __ldg(row + clampi(x + 2, 0, cols - 1)), __ldg(row + clampi(x + 3, 0, cols - 1)));
+}
+
+// Store pixels x .. x+3 (x >= 0) of row y, those inside the image.
+__device__ __forceinline__ void store4(float *__restrict__ out, int rows, int cols, bool vec, int y, int x, float4 v)
+{
+    if (y >= rows || x >= cols) return;
+    float *o = out + (size_t)y * cols + x;
+    if (vec && x + 3 < cols) {
+        *reinterpret_cast<float4 *>(o) = v;
     } else {
-        for (int i = threadIdx.x; i < IH * IW; i += kImgThreads) {
-            const int r = i / IW, c = i - r * IW;
-            const int y = clampi(y0 + r - R, 0, rows - 1);
-            s[r * IW + c] = in[(size_t)y * cols + clampi(x0 + c - HALO, 0, cols - 1)];
-        }
+        o[0] = v.x;
+        if (x + 1 < cols) o[1] = v.y;
+        if (x + 2 < cols) o[2] = v.z;
+        if (x + 3 < cols) o[3] = v.w;
     }
 }
 
-__device__ __forceinline__ void img_cp_async16(float *dst, const float *src)
-{
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src)
-                 : "memory");
-}
+__device__ __forceinline__ bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
 
-// The same staged tile as stage_tile, copied asynchronously (cp.async,
-// 16 bytes a copy, completion per thread by cp.async.wait_group) when the
-// tile's columns plus halo lie inside an image whose rows are 16-byte
-// aligned (rows are clamped whole, so only the columns decide); returns
-// false, having issued nothing, for the other tiles, which the caller stages
-// with stage_tile.  Uniform across the block.
-template <int R, int HALO, int IW>
-__device__ __forceinline__ bool stage_tile_async(const float *__restrict__ in, float *s, int rows, int cols, int x0,
-                                                 int y0)
-{
-    constexpr int IH = kTileH + 2 * R;
-    const bool fast = (cols & 3) == 0 && (reinterpret_cast<uintptr_t>(in) & 15) == 0 && x0 >= HALO &&
-                      x0 + kTileW + HALO <= cols;
-    if (!fast) return false;
-    constexpr int V = IW / 4;
-    for (int i = threadIdx.x; i < IH * V; i += kImgThreads) {
-        const int r = i / V, c4 = i - r * V;
-        const int y = clampi(y0 + r - R, 0, rows - 1);
-        img_cp_async16(s + r * IW + 4 * c4, in + (size_t)y * cols + (x0 - HALO) + 4 * c4);
-    }
-    return true;
-}
+// Separable Gaussian blur of radius R.  Per output row a lane makes four
+// outputs: the vertical pass (2R+1 taps on the row window, packed fp32x2
+// FMAs) gives the four columns' vertical sums, the horizontal pass combines
+// them with the 4 HL neighbouring columns on each side taken from the
+// neighbour lanes.  The rows live in a ring of 2R+1+P registers slots: the
+// row that output row y needs last, y + R, was loaded P rows earlier, so P
+// loads per lane are always in flight.  The band of output rows is a
+// multiple of the ring size and the row loop is unrolled by it, so every
+// slot index is a compile-time constant.
+template <int R> struct BlurShape {
+    static constexpr int HL = (R + 3) / 4;             // halo lanes per side
+    static constexpr int HALO = 4 * HL;                // halo columns per side
+    static constexpr int OUTL = 32 - 2 * HL;           // lanes that store
+    static constexpr int W = 2 * R + 1;
+    // rows loaded ahead, and output rows per warp (a multiple of the
+    // ring): a 4096 x 4096 image then gives each SM about 20 warps with P
+    // rows in flight each, in one wave of resident blocks (the wider ring
+    // of a larger radius costs registers, so fewer blocks fit an SM)
+    static constexpr int P = R <= 2 ? 6 : 4;
+    static constexpr int RING = W + P;
+    static constexpr int TH = RING * (R <= 2 ? (45 / RING > 0 ? 45 / RING : 1) : (52 / RING > 0 ? 52 / RING : 1));
+};
 
-// Persistent blur blocks walk tiles t = blockIdx.x, + gridDim.x, ...
-// (row-major tile order, so neighbouring tiles share their halos in L2),
-// double-buffering the staged input: tile t+gridDim.x is copied while tile t
-// is computed.  (Sobel, whose tile costs less arithmetic, measured faster
-// with one tile per block and the hardware's block scheduler.)
-__device__ __forceinline__ void tile_origin(int t, int ntx, int &x0, int &y0)
-{
-    x0 = (t % ntx) * kTileW;
-    y0 = (t / ntx) * kTileH;
-}
-
-// Store two rows of four outputs (x .. x+3, rows y, y+1) with bounds checks.
-__device__ __forceinline__ void store_2x4(float *__restrict__ out, int rows, int cols, int x, int y, float4 a, float4 b)
-{
-    const bool vec = (cols & 3) == 0 && (reinterpret_cast<uintptr_t>(out) & 15) == 0 && x + 3 < cols;
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-        const int yy = y + h;
-        if (yy >= rows) break;
-        const float4 v = h ? b : a;
-        float *o = out + (size_t)yy * cols + x;
-        if (vec) {
-            *reinterpret_cast<float4 *>(o) = v;
-        } else {
-            if (x < cols) o[0] = v.x;
-            if (x + 1 < cols) o[1] = v.y;
-            if (x + 2 < cols) o[2] = v.z;
-            if (x + 3 < cols) o[3] = v.w;
-        }
-    }
-}
-
-// Separable Gaussian blur with radius R.  Horizontal pass: each thread makes
-// four adjacent outputs of one staged row from 4 + 2R inputs (packed fp32x2
-// FMAs); vertical pass: each thread makes a 4-column x 2-row block from
-// 2 + 2R rows of the horizontal result.  Per output 2(2R+1) FMAs and about
-// one 32-bit shared-memory access; DRAM: one read and one write of the image.
 template <int R>
-__global__ void __launch_bounds__(kImgThreads) gauss_blur_kernel(const float *__restrict__ in, float *__restrict__ out,
-                                                                 const float *__restrict__ w, int rows, int cols)
+__global__ void __launch_bounds__(kStThreads) gauss_blur_kernel(const float *__restrict__ in, float *__restrict__ out,
+                                                                const float *__restrict__ w, int rows, int cols)
 {
-    constexpr int HALO = (R + 3) / 4 * 4;
-    constexpr int IW = kTileW + 2 * HALO, IH = kTileH + 2 * R;
-    __shared__ __align__(16) float s_in[2][IH * IW];
-    __shared__ __align__(16) float s_h[IH * kTileW];
-    float wr[2 * R + 1];
+    using S = BlurShape<R>;
+    constexpr int W = S::W, HL = S::HL, HALO = S::HALO, P = S::P, RING = S::RING;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int x0 = (blockIdx.x * kStWarps + warp) * 4 * S::OUTL;
+    if (x0 >= cols) return;  // the whole warp
+    const int x = x0 + 4 * (lane - HL);
+    const int y0 = blockIdx.y * S::TH;
+    const bool vin = (cols & 3) == 0 && aligned16(in), vout = (cols & 3) == 0 && aligned16(out);
+    const bool stores = lane >= HL && lane < 32 - HL;
+    float wr[W];
 #pragma unroll
-    for (int k = 0; k <= 2 * R; ++k) wr[k] = w[k];
-    const int ntx = (cols + kTileW - 1) / kTileW;
-    const int ntiles = ntx * ((rows + kTileH - 1) / kTileH);
-    int t = blockIdx.x, x0, y0;
-    if (t >= ntiles) return;
-    tile_origin(t, ntx, x0, y0);
-    bool staged = stage_tile_async<R, HALO, IW>(in, s_in[0], rows, cols, x0, y0);
-    asm volatile("cp.async.commit_group;" ::: "memory");
-    for (int buf = 0; t < ntiles; t += gridDim.x, buf ^= 1) {
-        tile_origin(t, ntx, x0, y0);
-        // the next tile's copies go into the other buffer (last read before
-        // the previous tile's second barrier)
-        bool staged_next = false;
-        if (t + (int)gridDim.x < ntiles) {
-            int nx0, ny0;
-            tile_origin(t + gridDim.x, ntx, nx0, ny0);
-            staged_next = stage_tile_async<R, HALO, IW>(in, s_in[buf ^ 1], rows, cols, nx0, ny0);
-        }
-        asm volatile("cp.async.commit_group;" ::: "memory");
-        asm volatile("cp.async.wait_group 1;" ::: "memory");  // this tile's copies (this thread's) landed
-        if (!staged) stage_tile<R, HALO, IW>(in, s_in[buf], rows, cols, x0, y0);  // border tile: clamped columns
-        __syncthreads();
-        const float *si = s_in[buf];
-        // horizontal: IH rows x 16 groups of four columns
-        for (int q = threadIdx.x; q < IH * (kTileW / 4); q += kImgThreads) {
-            const int r = q >> 4, g = q & 15;
-            const float *row = si + r * IW + 4 * g;  // inputs 4g .. 4g + 4 + 2 HALO
+    for (int k = 0; k < W; ++k) wr[k] = __ldg(w + k);
+    float4 ring[RING];  // slot (y - y0 + R) % RING holds input row y
+#pragma unroll
+    for (int k = 0; k < W - 1 + P; ++k) ring[k] = load4_clamped(in, rows, cols, vin, y0 - R + k, x);
+    for (int r0 = 0; r0 < S::TH; r0 += RING) {
+        if (y0 + r0 >= rows) break;  // the whole warp
+#pragma unroll
+        for (int k = 0; k < RING; ++k) {
+            const int y = y0 + r0 + k;
+            // row y + R + P, P rows ahead, into slot (k + W - 1 + P) % RING
+            ring[(k + W - 1 + P) % RING] = load4_clamped(in, rows, cols, vin, y + R + P, x);
+            float2 lo = make_float2(0.f, 0.f), hi = lo;
+#pragma unroll
+            for (int j = 0; j < W; ++j) {  // input row y - R + j
+                const float4 p = ring[(k + j) % RING];
+                const float2 wj = make_float2(wr[j], wr[j]);
+                lo = __ffma2_rn(wj, make_float2(p.x, p.y), lo);
+                hi = __ffma2_rn(wj, make_float2(p.z, p.w), hi);
+            }
+            // columns x - HALO .. x + 3 + HALO of the vertical result
             float v[4 + 2 * HALO];
+            v[HALO] = lo.x;
+            v[HALO + 1] = lo.y;
+            v[HALO + 2] = hi.x;
+            v[HALO + 3] = hi.y;
 #pragma unroll
-            for (int k = 0; k < (4 + 2 * HALO) / 4; ++k) {
-                const float4 p = reinterpret_cast<const float4 *>(row)[k];
-                v[4 * k] = p.x;
-                v[4 * k + 1] = p.y;
-                v[4 * k + 2] = p.z;
-                v[4 * k + 3] = p.w;
+            for (int h = 1; h <= HL; ++h) {
+                v[HALO - 4 * h] = __shfl_up_sync(kFull, lo.x, h);
+                v[HALO - 4 * h + 1] = __shfl_up_sync(kFull, lo.y, h);
+                v[HALO - 4 * h + 2] = __shfl_up_sync(kFull, hi.x, h);
+                v[HALO - 4 * h + 3] = __shfl_up_sync(kFull, hi.y, h);
+                v[HALO + 4 * h] = __shfl_down_sync(kFull, lo.x, h);
+                v[HALO + 4 * h + 1] = __shfl_down_sync(kFull, lo.y, h);
+                v[HALO + 4 * h + 2] = __shfl_down_sync(kFull, hi.x, h);
+                v[HALO + 4 * h + 3] = __shfl_down_sync(kFull, hi.y, h);
             }
             // outputs (0,1) and (2,3) take the taps whose input offset o is
             // even: their operand pairs (v[o], v[o+1]) sit in aligned
             // register pairs.  For odd o the aligned pair is (v[o+1],
             // v[o+2]), which feeds outputs (1,2); outputs 0 and 3 take that
-            // tap with scalar FMAs.  (Building misaligned pairs would cost two
-            // register moves per pair.)  The parities are compile-time.
-            float2 lo = make_float2(0.f, 0.f), hi = lo, mid = lo;
+            // tap with scalar FMAs.  The parities are compile-time.
+            float2 a01 = make_float2(0.f, 0.f), a23 = a01, mid = a01;
             float e0 = 0.f, e3 = 0.f;
 #pragma unroll
-            for (int k = 0; k <= 2 * R; ++k) {
-                const int o = HALO - R + k;
+            for (int k2 = 0; k2 < W; ++k2) {
+                const int o = HALO - R + k2;
+                const float2 wk = make_float2(wr[k2], wr[k2]);
                 if ((o & 1) == 0) {
-                    const float2 wk = make_float2(wr[k], wr[k]);
-                    lo = __ffma2_rn(wk, make_float2(v[o], v[o + 1]), lo);
-                    hi = __ffma2_rn(wk, make_float2(v[o + 2], v[o + 3]), hi);
+                    a01 = __ffma2_rn(wk, make_float2(v[o], v[o + 1]), a01);
+                    a23 = __ffma2_rn(wk, make_float2(v[o + 2], v[o + 3]), a23);
                 } else {
-                    mid = __ffma2_rn(make_float2(wr[k], wr[k]), make_float2(v[o + 1], v[o + 2]), mid);
-                    e0 = fmaf(wr[k], v[o], e0);
-                    e3 = fmaf(wr[k], v[o + 3], e3);
+                    mid = __ffma2_rn(wk, make_float2(v[o + 1], v[o + 2]), mid);
+                    e0 = fmaf(wr[k2], v[o], e0);
+                    e3 = fmaf(wr[k2], v[o + 3], e3);
                 }
             }
-            reinterpret_cast<float4 *>(s_h + r * kTileW)[g] =
-                make_float4(lo.x + e0, lo.y + mid.x, hi.x + mid.y, hi.y + e3);
+            if (stores) store4(out, rows, cols, vout, y, x, make_float4(a01.x + e0, a01.y + mid.x, a23.x + mid.y, a23.y + e3));
         }
-        __syncthreads();
-        // vertical: 16 column groups x 16 row pairs, one block per thread
-        const int g = threadIdx.x & 15, rp = threadIdx.x >> 4;
-        float4 col[2 + 2 * R];
-#pragma unroll
-        for (int k = 0; k < 2 + 2 * R; ++k) col[k] = reinterpret_cast<const float4 *>(s_h + (2 * rp + k) * kTileW)[g];
-        float2 a01 = make_float2(0.f, 0.f), a23 = a01, b01 = a01, b23 = a01;
-#pragma unroll
-        for (int k = 0; k <= 2 * R; ++k) {
-            const float2 wk = make_float2(wr[k], wr[k]);
-            a01 = __ffma2_rn(wk, make_float2(col[k].x, col[k].y), a01);
-            a23 = __ffma2_rn(wk, make_float2(col[k].z, col[k].w), a23);
-            b01 = __ffma2_rn(wk, make_float2(col[k + 1].x, col[k + 1].y), b01);
-            b23 = __ffma2_rn(wk, make_float2(col[k + 1].z, col[k + 1].w), b23);
-        }
-        store_2x4(out, rows, cols, x0 + 4 * g, y0 + 2 * rp, make_float4(a01.x, a01.y, a23.x, a23.y),
-                  make_float4(b01.x, b01.y, b23.x, b23.y));
-        staged = staged_next;
     }
-    asm volatile("cp.async.wait_group 0;" ::: "memory");
 }
 
 // sqrt(gx^2 + gy^2) with the single-instruction approximate square root
@@ -233,44 +172,47 @@ __device__ __forceinline__ float sobel_mag(float gx, float gy)
     return g2 > 0.f ? r : 0.f;
 }
 
-// Sobel magnitude: gx = right column - left column with weights (1, 2, 1),
-// gy = bottom row - top row with weights (1, 2, 1); out = sqrt(gx^2 + gy^2).
-// Each thread makes a 4-column x 2-row block from a 6 x 4 window.
-__global__ void __launch_bounds__(kImgThreads) sobel_kernel(const float *__restrict__ in, float *__restrict__ out,
-                                                            int rows, int cols)
+// Sobel magnitude, separably: per column the vertical smoothing
+// sv = top + 2 mid + bottom and difference dv = bottom - top of three rows
+// in registers; gx = sv(c+1) - sv(c-1), gy = dv(c-1) + 2 dv(c) + dv(c+1),
+// the neighbouring columns of a lane's four from the next lanes (one halo
+// lane per side).  Rows are loaded two ahead of their use.
+constexpr int kSobelRows = 32;  // output rows per warp
+
+__global__ void __launch_bounds__(kStThreads) sobel_kernel(const float *__restrict__ in, float *__restrict__ out,
+                                                           int rows, int cols)
 {
-    constexpr int HALO = 4, IW = kTileW + 2 * HALO, IH = kTileH + 2;
-    __shared__ __align__(16) float s[IH * IW];
-    const int x0 = blockIdx.x * kTileW, y0 = blockIdx.y * kTileH;
-    stage_tile<1, HALO, IW>(in, s, rows, cols, x0, y0);
-    __syncthreads();
-    const int g = threadIdx.x & 15, rp = threadIdx.x >> 4;
-    float m[4][12];  // staged rows 2rp .. 2rp+3, columns 4g .. 4g+11 (pixel 4g+c-HALO)
-#pragma unroll
-    for (int r = 0; r < 4; ++r)
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            const float4 q = reinterpret_cast<const float4 *>(s + (2 * rp + r) * IW + 4 * g)[k];
-            m[r][4 * k] = q.x;
-            m[r][4 * k + 1] = q.y;
-            m[r][4 * k + 2] = q.z;
-            m[r][4 * k + 3] = q.w;
-        }
-    float o[2][4];
-#pragma unroll
-    for (int h = 0; h < 2; ++h)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const int c = HALO + j;  // the output pixel's column in m
-            const float a = m[h][c - 1], b = m[h][c], cc = m[h][c + 1];
-            const float d = m[h + 1][c - 1], f = m[h + 1][c + 1];
-            const float gg = m[h + 2][c - 1], hh = m[h + 2][c], i = m[h + 2][c + 1];
-            const float gx = (cc + 2.f * f + i) - (a + 2.f * d + gg);
-            const float gy = (gg + 2.f * hh + i) - (a + 2.f * b + cc);
-            o[h][j] = sobel_mag(gx, gy);
-        }
-    store_2x4(out, rows, cols, x0 + 4 * g, y0 + 2 * rp, make_float4(o[0][0], o[0][1], o[0][2], o[0][3]),
-              make_float4(o[1][0], o[1][1], o[1][2], o[1][3]));
+    constexpr int HL = 1, OUTL = 32 - 2 * HL;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int x0 = (blockIdx.x * kStWarps + warp) * 4 * OUTL;
+    if (x0 >= cols) return;  // the whole warp
+    const int x = x0 + 4 * (lane - HL);
+    const int y0 = blockIdx.y * kSobelRows;
+    const bool vin = (cols & 3) == 0 && aligned16(in), vout = (cols & 3) == 0 && aligned16(out);
+    const bool stores = lane >= HL && lane < 32 - HL;
+    float4 a = load4_clamped(in, rows, cols, vin, y0 - 1, x);
+    float4 b = load4_clamped(in, rows, cols, vin, y0, x);
+    float4 c1 = load4_clamped(in, rows, cols, vin, y0 + 1, x);
+    float4 c2 = load4_clamped(in, rows, cols, vin, y0 + 2, x);
+    for (int r = 0; r < kSobelRows; ++r) {
+        const int y = y0 + r;
+        if (y >= rows) break;  // the whole warp
+        const float4 c = c1;
+        c1 = c2;
+        c2 = load4_clamped(in, rows, cols, vin, y + 3, x);
+        const float4 sv = make_float4(fmaf(2.f, b.x, a.x + c.x), fmaf(2.f, b.y, a.y + c.y), fmaf(2.f, b.z, a.z + c.z),
+                                      fmaf(2.f, b.w, a.w + c.w));
+        const float4 dv = make_float4(c.x - a.x, c.y - a.y, c.z - a.z, c.w - a.w);
+        const float svl = __shfl_up_sync(kFull, sv.w, 1), svr = __shfl_down_sync(kFull, sv.x, 1);
+        const float dvl = __shfl_up_sync(kFull, dv.w, 1), dvr = __shfl_down_sync(kFull, dv.x, 1);
+        const float4 m = make_float4(sobel_mag(sv.y - svl, fmaf(2.f, dv.x, dvl + dv.y)),
+                                     sobel_mag(sv.z - sv.x, fmaf(2.f, dv.y, dv.x + dv.z)),
+                                     sobel_mag(sv.w - sv.y, fmaf(2.f, dv.z, dv.y + dv.w)),
+                                     sobel_mag(svr - sv.z, fmaf(2.f, dv.w, dv.z + dvr)));
+        if (stores) store4(out, rows, cols, vout, y, x, m);
+        a = b;
+        b = c;
+    }
 }
 
 // (min, max) of n floats -> mm[0], mm[1].  Exact (min and max round
@@ -495,20 +437,13 @@ const char *validate_blur(const LaunchArgs &a)
 }
 
 // one resident wave of persistent blocks (at most one per tile)
-unsigned stencil_grid(const void *fn, int &per_sm, int rows, int cols)
-{
-    const int64_t tiles = ceil_div(cols, kTileW) * ceil_div(rows, kTileH);
-    return fused_grid(fn, kImgThreads, tiles, per_sm);
-}
-
 template <int R> void blur_launch(const LaunchArgs &a, cudaStream_t s)
 {
-    int rows = a.i32(3), cols = a.i32(4);
-    static int per_sm = 0;
-    const unsigned g = stencil_grid((const void *)gauss_blur_kernel<R>, per_sm, rows, cols);
-    gauss_blur_kernel<R><<<g, kImgThreads, 0, s>>>(a.p<float>(0), a.p<float>(1), a.p<float>(2), rows, cols);
+    using S = BlurShape<R>;
+    const int rows = a.i32(3), cols = a.i32(4);
+    const dim3 g((unsigned)ceil_div(ceil_div(cols, 4 * S::OUTL), kStWarps), (unsigned)ceil_div(rows, S::TH));
+    gauss_blur_kernel<R><<<g, kStThreads, 0, s>>>(a.p<float>(0), a.p<float>(1), a.p<float>(2), rows, cols);
 }
-
 int launch_blur(const LaunchArgs &a, void *sv)
 {
     cudaStream_t s = (cudaStream_t)sv;
@@ -536,8 +471,8 @@ const char *validate_sobel(const LaunchArgs &a)
 int launch_sobel(const LaunchArgs &a, void *s)
 {
     int rows = a.i32(2), cols = a.i32(3);
-    dim3 g((unsigned)ceil_div(cols, kTileW), (unsigned)ceil_div(rows, kTileH));
-    sobel_kernel<<<g, kImgThreads, 0, (cudaStream_t)s>>>(a.p<float>(0), a.p<float>(1), rows, cols);
+    const dim3 g((unsigned)ceil_div(ceil_div(cols, 4 * 30), kStWarps), (unsigned)ceil_div(rows, kSobelRows));
+    sobel_kernel<<<g, kStThreads, 0, (cudaStream_t)s>>>(a.p<float>(0), a.p<float>(1), rows, cols);
     return cudaGetLastError();
 }
 
