@@ -113,7 +113,16 @@ class BsDag(_Issuer):
     the other chains' kernels) and reads every result back."""
 
     def __init__(self, ctx, n, count=10, K=60.0, r=0.1, sigma=0.2, T=1.0, device="cuda", host=True,
-                 batched=True):
+                 batched=True, chunks=1):
+        """``chunks`` > 1 (with ``host``): each vector's copy-price-copy
+        chain of step_e2e is issued as `chunks` independent chains over
+        consecutive ranges of the vector (each range registered as its own
+        array over the same memory), so the copies of different ranges
+        overlap on both directions of the host link with a short fill and
+        drain; the prices are the same.  The range arrays share memory with
+        the whole-vector arrays (S, C), which the library tracks as other
+        arrays: a program that mixes step_e2e with the whole-vector steps
+        must order them itself (e.g. a sync between them)."""
         self.ctx, self.n, self.count = ctx, n, count
         self._init_issuer(ctx, batched)
         self.params = (float(K), float(r), float(sigma), float(T))
@@ -123,6 +132,22 @@ class BsDag(_Issuer):
         self.hC = [_pinned(max(n, 1), F32) for _ in range(count)] if host else [None] * count
         self.SA = [ctx.array(t, host=h, name="S%d" % i) for i, (t, h) in enumerate(zip(self.S, self.hS))]
         self.CA = [ctx.array(t, host=h, name="C%d" % i) for i, (t, h) in enumerate(zip(self.C, self.hC))]
+        self.chunks = max(1, chunks) if host else 1
+        self.parts = []  # per vector: [(lo, hi, S range array, C range array)]
+        if self.chunks > 1:
+            # a multiple of 4 floats, so every range is 16-byte aligned
+            step = max(4, ((n + self.chunks - 1) // self.chunks + 3) // 4 * 4)
+            for i in range(count):
+                rs = []
+                for lo in range(0, n, step):
+                    hi = min(n, lo + step)
+                    nb = 4 * (hi - lo)
+                    sa = ctx.array(dev=self.S[i].data_ptr() + 4 * lo, nbytes=nb, host=self.hS[i].data_ptr() + 4 * lo,
+                                   name="S%d[%d:%d]" % (i, lo, hi))
+                    ca = ctx.array(dev=self.C[i].data_ptr() + 4 * lo, nbytes=nb, host=self.hC[i].data_ptr() + 4 * lo,
+                                   name="C%d[%d:%d]" % (i, lo, hi))
+                    rs.append((lo, hi, sa, ca))
+                self.parts.append(rs)
 
     def load_host(self, prices):
         for h, p in zip(self.hS, prices):
@@ -154,11 +179,26 @@ class BsDag(_Issuer):
             if prefetch:
                 c.prefetch_host(Ca, 0, nb)
 
+    def _range_chains(self, c, prefetch):
+        K, r, s, T = self.params
+        for rs in self.parts:
+            for lo, hi, sa, ca in rs:
+                c.write(sa, 0, 4 * (hi - lo))
+                c.launch("bs_call", sa, ca, hi - lo, K, r, s, T)
+                if prefetch:
+                    c.prefetch_host(ca, 0, 4 * (hi - lo))
+
     def step_e2e(self, prefetch=True):
         """Host write of every price vector, all kernels, host read of every
         result (the paper's streaming form of the benchmark).  With
         ``prefetch`` each result's copy to the host is started right after its
         kernel, so it overlaps the other chains' input copies."""
+        if self.chunks > 1:
+            self._run(("e2e_ranges", prefetch), lambda c: self._range_chains(c, prefetch))
+            for rs in self.parts:
+                for lo, hi, sa, ca in rs:
+                    self.ctx.read(ca, None, 0, 4 * (hi - lo))
+            return
         self._run(("e2e", prefetch), lambda c: self._chains(c, prefetch))
         for Ca in self.CA:
             self.ctx.read(Ca, None, 0, 4 * self.n)

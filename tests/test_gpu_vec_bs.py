@@ -158,6 +158,28 @@ def test_bs_full_config(policy):
             assert torch.equal(c0, c1)
 
 
+@pytest.mark.parametrize("chunks", [2, 4, 7])
+def test_bs_e2e_in_ranges_equals_whole_chains(chunks):
+    """The end-to-end step issued as chunks of each vector (independent
+    copy-price-copy chains over 16-byte aligned ranges) gives the same bits
+    as whole-vector chains, and the oracle's prices."""
+    n, count = 1_000_003, 3
+    prices = datagen.bs_inputs(n, count=count, seed=9)
+    out = {}
+    for c in (1, chunks):
+        with G.Context() as ctx:
+            b = BsDag(ctx, n, count=count, chunks=c)
+            b.load_host(prices)
+            b.step_e2e()
+            b.step_e2e()  # a second step reuses the recorded program
+            out[c] = [h[:n].clone() for h in b.hC]
+            ctx.sync()
+    for whole, part, p in zip(out[1], out[chunks], prices):
+        assert torch.equal(whole, part)
+        ok, worst = close(part.numpy(), N.bs_call(p))
+        assert ok, worst
+
+
 def test_bs_dag_streams_and_overlap_structure():
     n = 1 << 20
     with G.Context(record_log=True) as ctx:
