@@ -369,7 +369,6 @@ int gdag_array_prefetch_host(gdag_ctx *ctx, gdag_array a, size_t off,
  *                         scratch INOUT, G i32, n i32)
  *                         norms[g] = ||x[seg[g] .. seg[g+1])||, for a batch
  *                         of graphs stored block-diagonally; G <= 65535,
- *                         n <= 2^28,
  *                         x 16-byte aligned (also for seg_scale)
  *        seg_scale       (x INOUT f32[n], seg IN i32[G+1], norms IN f32[G],
  *                         G i32, n i32)  x := x/norms[g] on segment g

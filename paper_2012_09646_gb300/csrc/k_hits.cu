@@ -241,28 +241,27 @@ __global__ void __launch_bounds__(256) spmv_fixup_kernel(const int2 *__restrict_
     }
 }
 
-// norm[0] = sqrt(sum x_i^2).  Each 128-thread block takes chunks of 2048
-// float4 (32 KB) and issues all sixteen 128-bit loads of a thread at once,
-// so a vector of a few tens of MB is requested in about one memory latency
-// (blocks that walked a grid-stride loop waited for several rounds).  A
-// thread sums its 64 squares as a fixed pairwise tree in fp32 (error a few
-// ulp of the chunk's sum, and no dependent chain as in compensated
-// summation) and its chunks in fp64; each block sums its threads in an fp64
-// tree.  The blocks' partials are combined in two levels so that no single
-// counter takes one atomic per block: the last block of each group of 32 to
-// arrive adds the group's partials (one per lane, a fixed warp tree), and
-// the last group adds the groups' sums the same way.  The grid depends only
-// on n, so the order of every addition, and the result, is the same on
-// every run.
+// norm[0] = sqrt(sum x_i^2), as two kernels on the node's stream.  The first:
+// each 128-thread block takes chunks of 2048 float4 (32 KB) and issues all
+// sixteen 128-bit loads of a thread at once, so a vector of a few tens of MB
+// is requested in about one memory latency (blocks that walked a grid-stride
+// loop waited for several rounds); a thread sums its 64 squares as a fixed
+// pairwise tree in fp32 (error a few ulp of the chunk's sum, and no
+// dependent chain as in compensated summation) and its chunks in fp64; each
+// block sums its threads in an fp64 tree and writes its partial.  The
+// second, one block, adds the partials in a fixed order and writes the norm.
+// It is launched as a programmatic dependent of the first: it becomes
+// resident while the first runs and waits (griddepcontrol.wait) for the
+// first grid to complete and its writes to be visible, so no block of the
+// first takes an arrival atomic and the combine starts as the last partial
+// lands.  The grid depends only on n: the same sum on every run.
 constexpr int kL2Threads = 128;
 constexpr int kL2V = 16;                               // float4 per thread per chunk
 constexpr int kL2Chunk4 = kL2Threads * kL2V;           // 2048 float4
 constexpr int kL2MaxBlocks = 4096;
-constexpr int kL2Group = 32;
-constexpr int kL2MaxGroups = kL2MaxBlocks / kL2Group;
-// scratch: block partials, group sums (doubles), group counters, the top
-// counter (32-bit, zero between launches)
-constexpr size_t kL2ScratchBytes = (size_t)(kL2MaxBlocks + kL2MaxGroups) * 8 + (size_t)(kL2MaxGroups + 1) * 4 + 16;
+constexpr int kL2CombineThreads = 256;
+// scratch: the block partials (doubles)
+constexpr size_t kL2ScratchBytes = (size_t)kL2MaxBlocks * 8 + 16;
 
 inline unsigned l2norm_grid(int64_t n)
 {
@@ -270,9 +269,11 @@ inline unsigned l2norm_grid(int64_t n)
     return (unsigned)(chunks < 1 ? 1 : (chunks < kL2MaxBlocks ? chunks : kL2MaxBlocks));
 }
 
-__global__ void __launch_bounds__(kL2Threads) l2norm_kernel(const float *__restrict__ x, float *__restrict__ norm,
-                                                            double *scratch, int64_t n)
+__global__ void __launch_bounds__(kL2Threads) l2norm_kernel(const float *__restrict__ x, double *__restrict__ part,
+                                                            int64_t n)
 {
+    // the combine kernel may start now: it waits for this grid to finish
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     __shared__ double sh[kL2Threads / 32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const float4 *x4 = reinterpret_cast<const float4 *>(x);
@@ -306,38 +307,28 @@ __global__ void __launch_bounds__(kL2Threads) l2norm_kernel(const float *__restr
     acc = warp_sum(acc);
     if (lane == 0) sh[warp] = acc;
     __syncthreads();
-    if (warp != 0) return;
-    double bsum = lane < kL2Threads / 32 ? sh[lane] : 0.0;
-    bsum = warp_sum(bsum);
-    double *part = scratch, *gpart = scratch + kL2MaxBlocks;
-    unsigned *gcnt = reinterpret_cast<unsigned *>(scratch + kL2MaxBlocks + kL2MaxGroups), *top = gcnt + kL2MaxGroups;
-    const unsigned b = blockIdx.x, grp = b / kL2Group, ngroups = (gridDim.x + kL2Group - 1) / kL2Group;
-    const unsigned gsize = gridDim.x - grp * kL2Group < (unsigned)kL2Group ? gridDim.x - grp * kL2Group : kL2Group;
-    int last = 0;
-    if (lane == 0) {
-        part[b] = bsum;
-        __threadfence();  // the partial visible device-wide before the arrival
-        last = atomicAdd(&gcnt[grp], 1u) == gsize - 1;
+    if (warp == 0) {
+        double b = lane < kL2Threads / 32 ? sh[lane] : 0.0;
+        b = warp_sum(b);
+        if (lane == 0) part[blockIdx.x] = b;
     }
-    if (!__shfl_sync(0xffffffffu, last, 0)) return;
-    __threadfence();  // every partial of the group visible
-    double g = lane < (int)gsize ? ((volatile double *)part)[grp * kL2Group + lane] : 0.0;
-    g = warp_sum(g);
-    last = 0;
-    if (lane == 0) {
-        gpart[grp] = g;
-        gcnt[grp] = 0u;
-        __threadfence();
-        last = atomicAdd(top, 1u) == ngroups - 1;
-    }
-    if (!__shfl_sync(0xffffffffu, last, 0)) return;
-    __threadfence();
+}
+
+__global__ void __launch_bounds__(kL2CombineThreads) l2norm_combine_kernel(const double *__restrict__ part,
+                                                                           float *__restrict__ norm, int blocks)
+{
+    __shared__ double sh[kL2CombineThreads / 32];
+    // the partial-sum grid has completed and its writes are visible
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     double t = 0.0;
-    for (unsigned i = lane; i < ngroups; i += 32) t += ((volatile double *)gpart)[i];
+    for (int b = threadIdx.x; b < blocks; b += kL2CombineThreads) t += part[b];
     t = warp_sum(t);
-    if (lane == 0) {
-        norm[0] = (float)sqrt(t);
-        *top = 0u;
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = t;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        double q = threadIdx.x < kL2CombineThreads / 32 ? sh[threadIdx.x] : 0.0;
+        q = warp_sum(q);
+        if (threadIdx.x == 0) norm[0] = (float)sqrt(q);
     }
 }
 
@@ -380,9 +371,9 @@ __global__ void __launch_bounds__(1024) scale_kernel(float *__restrict__ x, cons
 
 size_t seg_norm_scratch_bytes(int64_t G);
 
-// seg_scale cuts each segment into kSegSlices equal slices; block (slice,
-// g) handles one slice of segment g.  Segment bounds are clamped to [0, n],
-// so a malformed seg array cannot index outside x.
+// Segments are cut into kSegSlices equal slices; block (slice, g) handles
+// one slice of segment g.  Segment bounds are clamped to [0, n], so a
+// malformed seg array cannot index outside x.
 constexpr int kSegSlices = 32;
 
 __device__ __forceinline__ void seg_slice(const int *__restrict__ seg, int g, int sl, int n, int &lo, int &hi)
@@ -395,135 +386,61 @@ __device__ __forceinline__ void seg_slice(const int *__restrict__ seg, int g, in
     hi = b + (int)(len * (sl + 1) / kSegSlices);
 }
 
-// norms[g] = sqrt(sum of x_i^2 over segment g), as a segmented reduction
-// over fixed chunks of x: block b takes elements [b ch, (b+1) ch) whatever
-// the segments, so every block issues one round of 128-bit loads however
-// long the segments are (a slice per block of each segment made the blocks
-// of a million-vertex segment walk tens of dependent rounds).  A segment
-// inside the chunk is finished by the block; a segment that spans chunks
-// gets one partial from each of its chunks (its first chunk's in part_hi,
-// the others' in part_lo), and the last of those blocks to arrive adds them
-// in chunk order and resets the segment's arrival counter.  Kahan fp32 per
-// thread, fp64 block tree: the same sums on every run.  An empty segment is
-// written (0) by the block whose chunk holds its position (the last block
-// for a segment at n).  Segment bounds are clamped to [0, n], so a
-// malformed seg array cannot index outside x.
-constexpr int kSegChunk = 4096;          // elements per chunk unit (16 KB)
-constexpr int kSegMaxChunks = 65536;     // units of kSegChunk elements (the scratch's partials)
-
-__device__ __forceinline__ void seg_bounds(const int *__restrict__ seg, int g, int n, int &lo, int &hi)
-{
-    int b = seg[g], e = seg[g + 1];
-    b = b < 0 ? 0 : (b > n ? n : b);
-    e = e < b ? b : (e > n ? n : e);
-    lo = b;
-    hi = e;
-}
+// norms[g] = sqrt(sum of x_i^2 over segment g): per thread, rounds of eight
+// 128-bit loads in flight, each round's 32 squares summed as a fixed fp32
+// pairwise tree and the rounds in fp64; fp64 block tree per slice; the last
+// slice of a segment to arrive adds the slices' partials in slice order (the
+// result does not depend on timing) and resets the segment's arrival
+// counter.
+constexpr int kSegV = 8;  // float4 in flight per thread
 
 __global__ void __launch_bounds__(kThreads) seg_l2norm_kernel(const float *__restrict__ x, const int *__restrict__ seg,
-                                                              float *__restrict__ norms, double *scratch, int G, int n,
-                                                              int ch)
+                                                              float *__restrict__ norms, double *scratch, int G, int n)
 {
     __shared__ double sh[kThreads / 32];
-    __shared__ int s_first;
-    const int b = blockIdx.x, nb = gridDim.x;
-    const int c0 = (int)((int64_t)b * ch), c1 = (int)((int64_t)c0 + ch < n ? (int64_t)c0 + ch : n);
-    double *part_lo = scratch, *part_hi = scratch + kSegMaxChunks;
-    unsigned *cnt = reinterpret_cast<unsigned *>(scratch + 2 * kSegMaxChunks);
+    __shared__ bool last;
+    const int g = blockIdx.y, sl = blockIdx.x;
+    int lo, hi;
+    seg_slice(seg, g, sl, n, lo, hi);
+    double acc = 0.0;
+    // scalar head up to a 16-byte boundary, float4 body, scalar tail (x
+    // itself is 16-byte aligned: checked on the host)
+    const int a0 = min(hi, (lo + 3) & ~3), a1 = max(a0, hi & ~3);
+    for (int i = lo + threadIdx.x; i < a0; i += kThreads) acc += (double)(x[i] * x[i]);
     const float4 *x4 = reinterpret_cast<const float4 *>(x);
-    constexpr int kPer = kSegChunk / 4 / kThreads;  // float4 per thread per 4096-element unit
-    for (int u0 = c0; u0 < c1 || (u0 == c0 && c0 == c1); u0 += kSegChunk) {
-        const int u1 = u0 + kSegChunk < c1 ? u0 + kSegChunk : c1;
-        // the unit's loads first (they do not depend on the segments), so
-        // the segment lookup below overlaps their latency
-        float4 v[kPer];
+    for (int j = (a0 >> 2) + threadIdx.x; j < (a1 >> 2); j += kSegV * kThreads) {
+        float4 v[kSegV];
 #pragma unroll
-        for (int k = 0; k < kPer; ++k) {
-            const int i = u0 + 4 * (threadIdx.x + k * kThreads);  // u0 is a multiple of 4096
-            if (i + 3 < u1) {
-                v[k] = x4[i >> 2];
-            } else {
-                v[k].x = i < u1 ? x[i] : 0.f;
-                v[k].y = i + 1 < u1 ? x[i + 1] : 0.f;
-                v[k].z = i + 2 < u1 ? x[i + 2] : 0.f;
-                v[k].w = 0.f;
-            }
+        for (int u = 0; u < kSegV; ++u) {
+            const int q = j + u * kThreads;
+            v[u] = q < (a1 >> 2) ? x4[q] : make_float4(0.f, 0.f, 0.f, 0.f);
         }
-        if (threadIdx.x == 0) {
-            // the first segment whose (clamped) end is at or after u0
-            int lo = 0, hi = G;
-            while (lo < hi) {
-                const int mid = (lo + hi) >> 1;
-                int a, e;
-                seg_bounds(seg, mid, n, a, e);
-                if (e >= u0) hi = mid;
-                else lo = mid + 1;
-            }
-            s_first = lo;
-        }
-        __syncthreads();
-        const int first = s_first;
-        __syncthreads();  // s_first is rewritten by the next unit
-        for (int g = first; g < G; ++g) {
-            int lo, hi;
-            seg_bounds(seg, g, n, lo, hi);  // the same values in every thread
-            if (lo > u1) break;
-            if (lo == hi) {
-                // an empty segment: written by the block whose chunk holds
-                // its position (the last block for one at n)
-                if (threadIdx.x == 0 && ((lo >= u0 && lo < u1) || (b == nb - 1 && lo == n && u1 == c1))) norms[g] = 0.f;
-                continue;
-            }
-            if (hi <= u0 || lo >= u1) continue;
-            Kahan acc;
+        float qs[kSegV];
 #pragma unroll
-            for (int k = 0; k < kPer; ++k) {
-                const int i = u0 + 4 * (threadIdx.x + k * kThreads);
-                if (i >= lo && i + 3 < hi) {
-                    acc.add(v[k].x * v[k].x);
-                    acc.add(v[k].y * v[k].y);
-                    acc.add(v[k].z * v[k].z);
-                    acc.add(v[k].w * v[k].w);
-                } else {
-                    if (i >= lo && i < hi) acc.add(v[k].x * v[k].x);
-                    if (i + 1 >= lo && i + 1 < hi) acc.add(v[k].y * v[k].y);
-                    if (i + 2 >= lo && i + 2 < hi) acc.add(v[k].z * v[k].z);
-                    if (i + 3 >= lo && i + 3 < hi) acc.add(v[k].w * v[k].w);
-                }
-            }
-            const double sum = block_sum(acc.value(), sh);
-            if (threadIdx.x == 0) {
-                if (lo >= u0 && hi <= u1) {
-                    norms[g] = (float)sqrt(sum);
-                } else {
-                    // a segment spanning units: one partial per unit, in
-                    // unit order (a unit is kSegChunk elements)
-                    const int uf = lo / kSegChunk, ul = (hi - 1) / kSegChunk, me = u0 / kSegChunk;
-                    if (me == uf) part_hi[me] = sum;
-                    else part_lo[me] = sum;
-                    __threadfence();  // the partial visible device-wide before the arrival
-                    if (atomicAdd(&cnt[g], 1u) == (unsigned)(ul - uf)) {
-                        __threadfence();  // every unit's partial visible
-                        double t = ((volatile double *)part_hi)[uf];
-                        for (int q = uf + 1; q <= ul; ++q) t += ((volatile double *)part_lo)[q];
-                        norms[g] = (float)sqrt(t);
-                        cnt[g] = 0u;
-                    }
-                }
-            }
-        }
-        if (c0 == c1) break;
+        for (int u = 0; u < kSegV; ++u) qs[u] = (v[u].x * v[u].x + v[u].y * v[u].y) + (v[u].z * v[u].z + v[u].w * v[u].w);
+#pragma unroll
+        for (int w = kSegV / 2; w > 0; w >>= 1)
+#pragma unroll
+            for (int u = 0; u < w; ++u) qs[u] += qs[u + w];
+        acc += (double)qs[0];
     }
-}
-
-// Chunk length for n elements: a multiple of kSegChunk, one unit a block
-// while the grid stays within about 8 resident waves, more units a block
-// beyond that.
-inline int seg_chunk_len(int n)
-{
-    const int64_t units = ceil_div(n > 0 ? n : 1, kSegChunk);
-    const int64_t per = ceil_div(units, (int64_t)sm_count() * 64);
-    return (int)(per * kSegChunk);
+    for (int i = a1 + threadIdx.x; i < hi; i += kThreads) acc += (double)(x[i] * x[i]);
+    const double bs = block_sum(acc, sh);
+    double *part = scratch + (size_t)g * kSegSlices;
+    unsigned *counter = reinterpret_cast<unsigned *>(scratch + (size_t)G * kSegSlices) + g;
+    if (threadIdx.x == 0) part[sl] = bs;
+    __threadfence();  // the partial visible device-wide before the arrival
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicAdd(counter, 1u) == (unsigned)(kSegSlices - 1);
+    __syncthreads();
+    if (!last) return;
+    __threadfence();  // every slice's partial visible
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int k = 0; k < kSegSlices; ++k) t += ((volatile double *)part)[k];
+        norms[g] = (float)sqrt(t);
+        *counter = 0u;
+    }
 }
 
 // x := x / norms[g] over segment g, correctly rounded (div_by); a zero norm
@@ -611,9 +528,23 @@ const char *validate_l2norm(const LaunchArgs &a)
 int launch_l2norm(const LaunchArgs &a, void *s)
 {
     const int64_t n = a.i64(3);
-    l2norm_kernel<<<l2norm_grid(n), kL2Threads, 0, (cudaStream_t)s>>>(a.p<float>(0), a.p<float>(1), a.p<double>(2),
-                                                                     n);
-    return cudaGetLastError();
+    const unsigned g = l2norm_grid(n);
+    double *part = a.p<double>(2);
+    l2norm_kernel<<<g, kL2Threads, 0, (cudaStream_t)s>>>(a.p<float>(0), part, n);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    // the combine as a programmatic dependent of the partial sums
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(1);
+    cfg.blockDim = dim3(kL2CombineThreads);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = (cudaStream_t)s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, l2norm_combine_kernel, (const double *)part, a.p<float>(1), (int)g);
 }
 
 const char *validate_scale(const LaunchArgs &a)
@@ -648,19 +579,16 @@ const char *validate_seg_common(const LaunchArgs &a, int gi, int ni)
 const char *validate_seg_l2norm(const LaunchArgs &a)
 {
     if (const char *m = validate_seg_common(a, 4, 5)) return m;
-    if ((int64_t)a.i32(5) > (int64_t)kSegChunk * kSegMaxChunks) return "n above 268435456 elements";
     if (a.bytes[3] < seg_norm_scratch_bytes(a.i32(4))) return "scratch smaller than gdag_scratch_bytes(\"seg_l2norm\", G)";
     return nullptr;
 }
 
 int launch_seg_l2norm(const LaunchArgs &a, void *s)
 {
-    const int G = a.i32(4), n = a.i32(5);
+    const int G = a.i32(4);
     if (G == 0) return cudaSuccess;
-    const int ch = seg_chunk_len(n);
-    const int64_t chunks = ceil_div(n > 0 ? n : 1, ch);
-    seg_l2norm_kernel<<<(unsigned)chunks, kThreads, 0, (cudaStream_t)s>>>(a.p<float>(0), a.p<int>(1), a.p<float>(2),
-                                                                        a.p<double>(3), G, n, ch);
+    seg_l2norm_kernel<<<dim3(kSegSlices, G), kThreads, 0, (cudaStream_t)s>>>(a.p<float>(0), a.p<int>(1), a.p<float>(2),
+                                                                           a.p<double>(3), G, a.i32(5));
     return cudaGetLastError();
 }
 
@@ -691,10 +619,7 @@ KernelEntry entry(const char *name, const void *fn, std::initializer_list<gdag_a
 
 }  // namespace
 
-size_t seg_norm_scratch_bytes(int64_t G)
-{
-    return (size_t)2 * kSegMaxChunks * 8 + (size_t)(G > 0 ? G : 0) * 4 + 16;  // partials, counters
-}
+size_t seg_norm_scratch_bytes(int64_t G) { return (size_t)(G > 0 ? G : 0) * (kSegSlices * 8 + 4) + 16; }
 size_t spmv_part_bytes(int64_t rows_plus_nnz) { return (size_t)(ceil_div(rows_plus_nnz > 0 ? rows_plus_nnz : 1, kSpmvTile) + 1) * 8; }
 size_t spmv_carry_bytes(int64_t rows_plus_nnz) { return (size_t)ceil_div(rows_plus_nnz > 0 ? rows_plus_nnz : 1, kSpmvTile) * 4 + 16; }
 

@@ -57,8 +57,8 @@ def test_segment_kernels(lens):
         assert abs(got_n[k] - want) <= TOL * want + 1e-30, (k, got_n[k], want)
         want_x = N.scale(part, got_n[k]) if part.size else part
         assert np.all(np.abs(got_x[seg[k]:seg[k + 1]] - want_x) <= TOL * np.maximum(np.abs(want_x), 1.0))
-    # the per-segment arrival counters (after the 2 x 65536 partials) are zero again
-    off = 2 * 65536 * 8
+    # the per-segment arrival counters (after the G x 32 slice partials) are zero again
+    off = G_ * 32 * 8
     assert np.all(scratch.cpu().numpy()[off:off + 4 * G_] == 0)
 
 

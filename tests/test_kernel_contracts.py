@@ -175,7 +175,6 @@ LIMITS = [
     ("seg_l2norm", (65535, 100), True, None, {}),
     ("seg_l2norm", (65536, 100), False, None, {}),
     ("seg_l2norm", (4, 100), False, None, {0: 4}),  # x not 16-byte aligned
-    ("seg_l2norm", (4, 268435457), False, None, {}),  # more elements than the per-unit partials hold
     ("seg_scale", (65536, 100), False, None, {}),
     ("seg_scale", (4, 100), False, None, {0: 4}),
     ("bs_call", (100, 60.0, 0.1, 0.2, 1.0), True, ((4, 1, 1), (256, 1, 1)), {}),
