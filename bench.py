@@ -721,7 +721,9 @@ def measure_dag(torch, G, spec, steps, peak_gbs, link):
             spec.step(obj)
         ctx.sync()
         torch.cuda.synchronize()
-        if policy == G.GDAG_POLICY_SERIAL_SYNC:
+        if policy == G.GDAG_POLICY_SERIAL_SYNC or spec.host_sync:
+            # a step that ends with a host read is complete when it returns:
+            # timed on the host, like the hand-built graph's replay + sync
             t0 = time.perf_counter()
             for _ in range(steps):
                 spec.step(obj)
@@ -781,16 +783,24 @@ def measure_dag(torch, G, spec, steps, peak_gbs, link):
         spec.after_replay(ctx, obj)
     ctx.sync()
     torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(s0)
-    ctx.fork(s0.cuda_stream)
-    for _ in range(steps):
-        ctx.replay(gid)
-        spec.after_replay(ctx, obj)
-    ctx.wait_all(s0.cuda_stream)
-    e1.record(s0)
-    torch.cuda.synchronize()
-    out["library_graph"] = e0.elapsed_time(e1) / steps
+    if spec.host_sync:
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            ctx.replay(gid)
+            spec.after_replay(ctx, obj)
+        ctx.sync()
+        out["library_graph"] = (time.perf_counter() - t0) * 1e3 / steps
+    else:
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s0)
+        ctx.fork(s0.cuda_stream)
+        for _ in range(steps):
+            ctx.replay(gid)
+            spec.after_replay(ctx, obj)
+        ctx.wait_all(s0.cuda_stream)
+        e1.record(s0)
+        torch.cuda.synchronize()
+        out["library_graph"] = e0.elapsed_time(e1) / steps
     ctx.drop_graph(gid)
     c2, o2, out["serial_async_one_stream"] = timed_ctx(G.GDAG_POLICY_SERIAL_ASYNC)
     c2.close()
@@ -958,15 +968,18 @@ def run_serving(args, torch, datagen, data):
                     fused_members=fused)
     # the admission window (estimated GPU ms in flight) and the class split
     # (requests estimated above split_ms form the long class, short ones run
-    # on high-priority streams): picked by p99 at the configured rate among
-    # the settings that keep up with it
+    # on high-priority streams): among the settings that keep up with the
+    # configured rate, those whose p99 is within 15% of the best p99 (one
+    # short sweep run's noise), and of those the lowest p50
     sweep = {}
     for w, split, lw in ((1.0, None, None), (2.0, None, None), (4.0, None, None), (1.0, 0.5, 2.0), (2.0, 0.5, 2.0),
                          (1.0, 0.5, 4.0), (2.0, 0.5, 4.0)):
         q = one(rate0, w, fuse_max, split, seed=8, long_window=lw)
         sweep[(w, split, lw)] = {k: q[k] for k in ("p50_ms", "p99_ms", "throughput_req_s")}
     keeps_up = [k for k in sweep if sweep[k]["throughput_req_s"] >= 0.97 * rate0] or list(sweep)
-    best_w, best_split, best_lw = min(keeps_up, key=lambda k: sweep[k]["p99_ms"])
+    p99_best = min(sweep[k]["p99_ms"] for k in keeps_up)
+    near = [k for k in keeps_up if sweep[k]["p99_ms"] <= 1.15 * p99_best]
+    best_w, best_split, best_lw = min(near, key=lambda k: sweep[k]["p50_ms"])
     out["cost_model_ms"] = {k: {"a": a, "b": b} for k, (a, b) in cost.items()}
     out["sweep_2000_req_s"] = {"window %s split %s long window %s" % k: v for k, v in sweep.items()}
     out["window_ms"] = best_w
@@ -1084,6 +1097,28 @@ def run_ours(args, rank, world, local_rank):
             torch.cuda.synchronize()
             link[kind] = 3 * 4 * N_OPTS / (time.perf_counter() - t0) / 1e9
         del hb, db
+        # both directions at once, as in the e2e step but with nothing else
+        # to do: N_VEC vectors in on one stream while N_VEC vectors go out
+        # on another
+        hb_in = torch.empty(N_VEC * N_OPTS, dtype=torch.float32, pin_memory=True)
+        hb_out = torch.empty(N_VEC * N_OPTS, dtype=torch.float32, pin_memory=True)
+        db_in = torch.empty(N_VEC * N_OPTS, dtype=torch.float32, device=dev)
+        db_out = torch.zeros(N_VEC * N_OPTS, dtype=torch.float32, device=dev)
+        s_in, s_out = torch.cuda.Stream(), torch.cuda.Stream()
+        duplex_ms = []
+        for rep in range(4):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            with torch.cuda.stream(s_in):
+                db_in.copy_(hb_in, non_blocking=True)
+            with torch.cuda.stream(s_out):
+                hb_out.copy_(db_out, non_blocking=True)
+            torch.cuda.synchronize()
+            if rep:
+                duplex_ms.append((time.perf_counter() - t0) * 1e3)
+        link["duplex_ms"] = statistics.median(duplex_ms)
+        link["duplex_gbs"] = 2 * N_VEC * 4 * N_OPTS / (link["duplex_ms"] * 1e-3) / 1e9
+        del hb_in, hb_out, db_in, db_out
 
         # ---- every DAG of the suite: policies, hand-built CUDA Graph, bounds
         specs = [BsSpec(G, W, data)]
@@ -1220,9 +1255,11 @@ def run_ours(args, rank, world, local_rank):
                     "chains_per_vector": e2e_chunks, "ms_per_step_by_chains_per_vector": e2e_by_chunks,
                     "h2d_bytes_per_step": N_VEC * 4 * N_OPTS, "d2h_bytes_per_step": N_VEC * 4 * N_OPTS,
                     "max_rel_err_sampled": e2e_err, "overlap": overlap,
-                    "link_gbs": link,
+                    "link_gbs": {k: v for k, v in link.items() if k != "duplex_ms"},
                     "link_bound_ms": max(N_VEC * 4 * N_OPTS / (link["h2d"] * 1e9),
-                                         N_VEC * 4 * N_OPTS / (link["d2h"] * 1e9)) * 1e3},
+                                         N_VEC * 4 * N_OPTS / (link["d2h"] * 1e9)) * 1e3,
+                    "duplex_copy_ms": link["duplex_ms"],
+                    "frac_of_duplex_copy": link["duplex_ms"] / ms_e2e},
             "dags": dags,
             "serve": serve_out,
             "cpu_baseline": {"value": cpu_val, "unit": UNIT, "cores": 1, "kind": "oracle",
@@ -1248,9 +1285,13 @@ def run_ours(args, rank, world, local_rank):
 def print_summary(out):
     """A short human-readable digest of the bench line on stderr."""
     w = sys.stderr.write
-    w("summary: %s %.0f %s resident (%.3f ms/step), e2e %.1f %s; %s %.3f of HBM peak\n" % (
-        out["config"]["workload"].split(":")[0], out["value"], out["unit"], out["ms_per_step"], out["e2e"]["value"],
-        out["unit"], out["roofline"]["kernel"], out["roofline"]["frac"]))
+    e2e = out["e2e"]
+    w("summary: %s %.0f %s resident (%.3f ms/step), e2e %.1f %s (%.3f ms/step, %s of a duplex copy); "
+      "%s %.3f of HBM peak\n" % (
+        out["config"]["workload"].split(":")[0], out["value"], out["unit"], out["ms_per_step"], e2e["value"],
+        out["unit"], e2e.get("ms_per_step", 0.0),
+        "%.2f" % e2e["frac_of_duplex_copy"] if "frac_of_duplex_copy" in e2e else "n/a",
+        out["roofline"]["kernel"], out["roofline"]["frac"]))
     w("%-11s %8s %8s %8s %8s %8s %8s\n" % ("DAG", "par_ms", "vsSYNC", "vsGraph", "1call/G", "ofCP", "ofRes"))
     for name, d in (out.get("dags") or {}).items():
         m = d["makespan_ms"]

@@ -16,6 +16,7 @@ void append_dl_kernels(std::vector<KernelEntry> &v);
 size_t spmv_part_bytes(int64_t rows_plus_nnz);
 size_t seg_norm_scratch_bytes(int64_t G);
 size_t l2norm_scratch_bytes();
+size_t minmax_scratch_bytes();
 size_t spmv_carry_bytes(int64_t rows_plus_nnz);
 
 namespace {
@@ -41,7 +42,7 @@ const KernelEntry &builtin(int i) { return table()[(size_t)i]; }
 size_t scratch_bytes(const char *kernel, int64_t n)
 {
     if (!std::strcmp(kernel, "vec_reduce_diff")) return reduce_scratch_bytes<1>();
-    if (!std::strcmp(kernel, "minmax")) return reduce_scratch_bytes<2>();
+    if (!std::strcmp(kernel, "minmax")) return minmax_scratch_bytes();
     if (!std::strcmp(kernel, "l2norm")) return l2norm_scratch_bytes();
     // for seg_l2norm n is the number of segments
     if (!std::strcmp(kernel, "seg_l2norm")) return seg_norm_scratch_bytes(n);

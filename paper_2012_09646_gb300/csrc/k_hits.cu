@@ -534,17 +534,8 @@ int launch_l2norm(const LaunchArgs &a, void *s)
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     // the combine as a programmatic dependent of the partial sums
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(1);
-    cfg.blockDim = dim3(kL2CombineThreads);
-    cfg.dynamicSmemBytes = 0;
-    cfg.stream = (cudaStream_t)s;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    attr[0].val.programmaticStreamSerializationAllowed = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, l2norm_combine_kernel, (const double *)part, a.p<float>(1), (int)g);
+    return launch_dependent(l2norm_combine_kernel, kL2CombineThreads, (cudaStream_t)s, (const double *)part,
+                            a.p<float>(1), (int)g);
 }
 
 const char *validate_scale(const LaunchArgs &a)

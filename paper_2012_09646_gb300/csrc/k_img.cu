@@ -215,40 +215,60 @@ __global__ void __launch_bounds__(kStThreads) sobel_kernel(const float *__restri
     }
 }
 
-// (min, max) of n floats -> mm[0], mm[1].  Exact (min and max round
-// nothing); blocks publish their pair, the last block combines in order.
-__global__ void __launch_bounds__(kThreads) minmax_kernel(const float *__restrict__ x, float *__restrict__ mm,
-                                                          double *scratch, int64_t n)
+// (min, max) of n floats -> mm[0], mm[1], in two kernels.  The first gives
+// each block one chunk of sixteen 128-bit loads per thread, all issued
+// before any is used (past kMmMaxBlocks chunks a block takes several,
+// grid-strided), and writes the block's (min, max) pair; no block takes an
+// arrival atomic.  The second, one block launched as a programmatic
+// dependent, becomes resident early and waits on the device for the first
+// grid to complete before it combines the pairs.  min and max round
+// nothing, so the result is exact whatever the order.
+constexpr int kMmThreads = 128;
+constexpr int kMmV = 16;                      // float4 per thread per chunk
+constexpr int kMmChunk4 = kMmThreads * kMmV;  // 2048 float4
+constexpr int kMmMaxBlocks = 4096;
+constexpr int kMmCombineThreads = 256;
+
+inline unsigned minmax_grid(int64_t n)
 {
-    __shared__ float smin[kThreads / 32], smax[kThreads / 32];
+    const int64_t chunks = ceil_div(n >> 2, kMmChunk4);
+    return (unsigned)(chunks < 1 ? 1 : (chunks < kMmMaxBlocks ? chunks : kMmMaxBlocks));
+}
+
+size_t minmax_scratch_bytes() { return (size_t)kMmMaxBlocks * sizeof(float2) + 16; }
+
+__global__ void __launch_bounds__(kMmThreads) minmax_kernel(const float *__restrict__ x, float2 *__restrict__ part,
+                                                            int64_t n)
+{
+    // the combine kernel may start now: it waits for this grid to finish
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    __shared__ float smin[kMmThreads / 32], smax[kMmThreads / 32];
+    const float kNaN = __int_as_float(0x7fffffff);
     float lo = INFINITY, hi = -INFINITY;
     if ((reinterpret_cast<uintptr_t>(x) & 15) == 0) {
         const float4 *x4 = reinterpret_cast<const float4 *>(x);
-        const int64_t n4 = n >> 2;
-        const int64_t tile = (int64_t)kThreads * kUnroll;
-        for (int64_t base = (int64_t)blockIdx.x * tile; base < n4; base += (int64_t)gridDim.x * tile) {
-            float4 v[kUnroll];
+        const int64_t n4 = n >> 2, chunks = (n4 + kMmChunk4 - 1) / kMmChunk4;
+        for (int64_t c = blockIdx.x; c < chunks; c += gridDim.x) {
+            float4 v[kMmV];
 #pragma unroll
-            for (int k = 0; k < kUnroll; ++k) {
-                int64_t i = base + threadIdx.x + (int64_t)k * kThreads;
-                if (i < n4) v[k] = x4[i];
+            for (int u = 0; u < kMmV; ++u) {
+                const int64_t i = c * kMmChunk4 + threadIdx.x + (int64_t)u * kMmThreads;
+                v[u] = i < n4 ? x4[i] : make_float4(kNaN, kNaN, kNaN, kNaN);
             }
 #pragma unroll
-            for (int k = 0; k < kUnroll; ++k) {
-                int64_t i = base + threadIdx.x + (int64_t)k * kThreads;
-                if (i < n4) {
-                    lo = fminf(lo, fminf(fminf(v[k].x, v[k].y), fminf(v[k].z, v[k].w)));
-                    hi = fmaxf(hi, fmaxf(fmaxf(v[k].x, v[k].y), fmaxf(v[k].z, v[k].w)));
-                }
+            for (int u = 0; u < kMmV; ++u) {
+                // padding is NaN, which fminf and fmaxf pass over
+                lo = fminf(lo, fminf(fminf(v[u].x, v[u].y), fminf(v[u].z, v[u].w)));
+                hi = fmaxf(hi, fmaxf(fmaxf(v[u].x, v[u].y), fmaxf(v[u].z, v[u].w)));
             }
         }
         if (blockIdx.x == 0 && threadIdx.x < (n & 3)) {
-            float t = x[(n4 << 2) + threadIdx.x];
+            const float t = x[(n4 << 2) + threadIdx.x];
             lo = fminf(lo, t);
             hi = fmaxf(hi, t);
         }
     } else {
-        for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        for (int64_t i = (int64_t)blockIdx.x * kMmThreads + threadIdx.x; i < n; i += (int64_t)gridDim.x * kMmThreads) {
             lo = fminf(lo, x[i]);
             hi = fmaxf(hi, x[i]);
         }
@@ -261,30 +281,43 @@ __global__ void __launch_bounds__(kThreads) minmax_kernel(const float *__restric
         smax[warp] = hi;
     }
     __syncthreads();
-    float2 *part = reinterpret_cast<float2 *>(scratch);
-    if (threadIdx.x < 32) {
-        lo = lane < kThreads / 32 ? smin[lane] : INFINITY;
-        hi = lane < kThreads / 32 ? smax[lane] : -INFINITY;
+    if (warp == 0) {
+        lo = lane < kMmThreads / 32 ? smin[lane] : INFINITY;
+        hi = lane < kMmThreads / 32 ? smax[lane] : -INFINITY;
         lo = warp_min(lo);
         hi = warp_max(hi);
         if (lane == 0) part[blockIdx.x] = make_float2(lo, hi);
     }
-    unsigned *counter = reinterpret_cast<unsigned *>(scratch + 2 * kReduceMaxBlocks);
-    if (!arrive_last(counter)) return;
-    if (threadIdx.x < 32) {
-        lo = INFINITY;
-        hi = -INFINITY;
-        for (unsigned b = lane; b < gridDim.x; b += 32) {
-            const volatile float *pv = reinterpret_cast<volatile float *>(part + b);
-            lo = fminf(lo, pv[0]);
-            hi = fmaxf(hi, pv[1]);
-        }
+}
+
+__global__ void __launch_bounds__(kMmCombineThreads) minmax_combine_kernel(const float2 *__restrict__ part,
+                                                                           float *__restrict__ mm, int blocks)
+{
+    __shared__ float smin[kMmCombineThreads / 32], smax[kMmCombineThreads / 32];
+    // the first grid has completed and its writes are visible
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    float lo = INFINITY, hi = -INFINITY;
+    for (int b = threadIdx.x; b < blocks; b += kMmCombineThreads) {
+        const float2 p = part[b];
+        lo = fminf(lo, p.x);
+        hi = fmaxf(hi, p.y);
+    }
+    lo = warp_min(lo);
+    hi = warp_max(hi);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) {
+        smin[warp] = lo;
+        smax[warp] = hi;
+    }
+    __syncthreads();
+    if (warp == 0) {
+        lo = lane < kMmCombineThreads / 32 ? smin[lane] : INFINITY;
+        hi = lane < kMmCombineThreads / 32 ? smax[lane] : -INFINITY;
         lo = warp_min(lo);
         hi = warp_max(hi);
         if (lane == 0) {
             mm[0] = lo;
             mm[1] = hi;
-            *counter = 0u;
         }
     }
 }
@@ -482,16 +515,21 @@ const char *validate_minmax(const LaunchArgs &a)
     if (n <= 0) return "n must be > 0";
     if (a.bytes[0] / 4 < (size_t)n) return "input smaller than n floats";
     if (a.bytes[1] < 8) return "mm smaller than two floats";
-    if (a.bytes[2] < reduce_scratch_bytes<2>()) return "scratch smaller than gdag_scratch_bytes()";
+    if (a.bytes[2] < minmax_scratch_bytes()) return "scratch smaller than gdag_scratch_bytes()";
     return nullptr;
 }
 
 int launch_minmax(const LaunchArgs &a, void *s)
 {
-    int64_t n = a.i64(3);
-    minmax_kernel<<<reduce_grid(n >> 2), kThreads, 0, (cudaStream_t)s>>>(a.p<float>(0), a.p<float>(1),
-                                                                         a.p<double>(2), n);
-    return cudaGetLastError();
+    const int64_t n = a.i64(3);
+    const unsigned g = minmax_grid(n);
+    float2 *part = reinterpret_cast<float2 *>(a.p<double>(2));
+    minmax_kernel<<<g, kMmThreads, 0, (cudaStream_t)s>>>(a.p<float>(0), part, n);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    // the combine as a programmatic dependent of the block pairs
+    return launch_dependent(minmax_combine_kernel, kMmCombineThreads, (cudaStream_t)s, (const float2 *)part,
+                            a.p<float>(1), (int)g);
 }
 
 const char *validate_extend(const LaunchArgs &a)

@@ -76,6 +76,28 @@ template <int Width> constexpr size_t reduce_scratch_bytes()
 }
 
 #ifdef __CUDACC__
+// One block of `threads` threads of `kernel` on stream s, launched as a
+// programmatic dependent of the kernel before it on s: it may become
+// resident while that kernel runs (once every block of it has executed
+// griddepcontrol.launch_dependents) and must execute griddepcontrol.wait,
+// which returns when that kernel has completed and its writes are visible,
+// before it reads anything that kernel wrote.
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_dependent(void (*kernel)(KArgs...), int threads, cudaStream_t s, Args... args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(1);
+    cfg.blockDim = dim3((unsigned)threads);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 __device__ __forceinline__ double warp_sum(double v)
 {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);

@@ -74,6 +74,29 @@ def test_img_nodes_stepwise(shape):
         check(d.h_out.numpy().reshape(shape), out, what="host read")
 
 
+# one float; a ragged tail; one chunk and a bit; 2^25 + 7 floats (4097 chunks
+# of 8192 floats, more than the 4096 blocks, so a block takes two); 4e7
+# floats; a start 12 bytes past a 16-byte boundary (the scalar path)
+@pytest.mark.parametrize("n,off", [(1, 0), (3, 0), (8193, 0), ((1 << 25) + 7, 0), (40_000_003, 0), (1_000_001, 3)])
+def test_minmax_sizes_and_alignment(n, off):
+    """minmax alone, bit-exact against the oracle's min and max, with the
+    extremes placed in the ragged tail and in a middle chunk."""
+    rng = np.random.default_rng(n + off)
+    x = (rng.standard_normal(n + off) * 100.0).astype(np.float32)
+    x[off + n // 2] = 3.0e30
+    x[off + n - 1] = -3.0e30
+    mn, mx = N.minmax(x[off:].astype(np.float64))
+    with G.Context() as ctx:
+        buf = torch.from_numpy(x).cuda()
+        mm = torch.full((2,), 7.0, device="cuda")
+        sc = torch.zeros(G.gdag_scratch_bytes("minmax", n), dtype=torch.uint8, device="cuda")
+        X = ctx.array(dev=buf.data_ptr() + 4 * off, nbytes=4 * n)
+        ctx.launch("minmax", X, ctx.array(mm), ctx.array(sc), n)
+        ctx.sync()
+        got = mm.cpu().numpy()
+    assert (got[0], got[1]) == (np.float32(mn), np.float32(mx)), (got, mn, mx)
+
+
 @pytest.mark.parametrize("shape,policy", [(sh, p) for sh in ((64, 64), (129, 300), (1024, 1024))
                                           for p in (G.GDAG_POLICY_PARALLEL, G.GDAG_POLICY_SERIAL_SYNC)]
                          + [((4096, 4096), G.GDAG_POLICY_PARALLEL)])
