@@ -713,12 +713,33 @@ def measure_dag(torch, G, spec, steps, peak_gbs, link):
     import numpy as np
     s0 = torch.cuda.Stream()
     out = {}
+    # a timed region of at least about 50 ms for every variant: small DAGs
+    # (VEC, DL) take hundreds of steps, so that no single slow step (an OS
+    # or allocator hiccup on the host) moves their mean
+    cal = G.Context()
+    cobj = spec.build(cal)
+    for _ in range(5):
+        spec.step(cobj)
+    cal.sync()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(5):
+        spec.step(cobj)
+    cal.sync()
+    est_ms = (time.perf_counter() - t0) * 1e3 / 5
+    cal.close()
+    del cobj
+    steps = max(steps, min(2000, int(50.0 / max(est_ms, 1e-3))))
 
     def timed_ctx(policy, batched=True):
         ctx = G.Context(policy=policy)
         obj = spec.build(ctx, batched=batched)
-        for _ in range(3):
+        # warm-up: at least 10 steps and 20 ms, so that the context's stream
+        # and event pools have reached their steady size
+        t0, k = time.perf_counter(), 0
+        while k < 10 or time.perf_counter() - t0 < 0.02:
             spec.step(obj)
+            k += 1
         ctx.sync()
         torch.cuda.synchronize()
         if policy == G.GDAG_POLICY_SERIAL_SYNC or spec.host_sync:
@@ -902,7 +923,8 @@ def measure_dag(torch, G, spec, steps, peak_gbs, link):
     tctx.close()
     del tobj
     return {
-        "makespan_ms": out, "nodes": len(elems) - first, "kernels": kern, "streams": streams_used,
+        "makespan_ms": out, "steps_timed": steps, "nodes": len(elems) - first, "kernels": kern,
+        "streams": streams_used,
         "algorithmic_hbm_bytes": hbm, "h2d_bytes": h2d, "d2h_bytes": d2h,
         "speedup_vs_serial_async": out["serial_async_one_stream"] / out["parallel"],
         "speedup_vs_serial_sync": out["serial_sync"] / out["parallel"],
