@@ -43,7 +43,10 @@
 //   warps 1-4 (producers): wait for the tile's halo and for the MMAs of tile
 //     t-2 to have read A set s, build A set s (thread m writes row m of the
 //     four operands), and arrive on "A full", one arrival per warp.
-//   warps 5-12 (epilogue): wait for "full", read the accumulators with
+//   warps 5-12 (epilogue): stage the weights once (one round of loads of the
+//     raw weights and bias into a staging buffer, then the two B operands
+//     in the K order, one 16-byte core-matrix row per store); per tile wait
+//     for "full", read the accumulators with
 //     tcgen05.ld (warp w reads lanes 32*(w%4).. and channels 32*((w-5)/4)..),
 //     signal "empty", take the maximum of the four (bias included; ReLU
 //     commutes with the maximum), convert channel pairs to bf16 with ReLU in
@@ -99,6 +102,8 @@ constexpr size_t kConvSmemUsed = kOffBars + kNumBars * 8 + 16;
 // one CTA (holding all 512 tensor-memory columns) owns an SM
 constexpr size_t kConvSmem = 160 * 1024;
 static_assert(kConvSmemUsed <= kConvSmem, "conv shared memory");
+static_assert(2 * kConvN * kConvTaps + 4 * kConvN <= kStageBytes, "raw weights must fit one staging buffer");
+static_assert((2 * kConvN * (kConvK / 8)) % kEpiThreads == 0, "B rows split evenly over the epilogue");
 static_assert(kOffHalo % 128 == 0 && kHaloBoxStride % 128 == 0 && kHaloBytes % 128 == 0 && kOffStage % 128 == 0 &&
                   kStageBytes % 128 == 0 && (kHaloBox * 2) % 16 == 0,
               "TMA shared-memory addresses must be 128-byte aligned, box rows multiples of 16 bytes");
@@ -351,28 +356,53 @@ __global__ void __launch_bounds__(kConvThreads, 1)
         // 32*quad.., channels 32*chalf .. +31, pooled column x0/2 + mo
         const int etid = tid - kCtlThreads - kProdThreads;
         {
-            constexpr int kPer = 2 * kConvN * kConvK / kEpiThreads;
-            __nv_bfloat16 wv[kPer];
+            // the weights and the bias, raw, into staging buffer 1 (which the
+            // epilogue of tile 1 writes first): one round of independent loads
+            constexpr int kW = kConvN * kConvTaps, kWPer = (kW + kEpiThreads - 1) / kEpiThreads;
+            uint16_t *wraw = reinterpret_cast<uint16_t *>(stage + kStageBytes);
+            float *braw = reinterpret_cast<float *>(stage + kStageBytes + 2 * kW);
+            const unsigned short *wsrc = reinterpret_cast<const unsigned short *>(wt);
+            unsigned short wl[kWPer];
 #pragma unroll
-            for (int r = 0; r < kPer; ++r) {
+            for (int r = 0; r < kWPer; ++r) {
                 const int i = etid + r * kEpiThreads;
-                const int p = i / (kConvN * kConvK), co = (i / kConvK) % kConvN, k = i % kConvK;
-                const int tap = conv_tap(p, k);
-                __nv_bfloat16 v = __float2bfloat16(0.f);
-                if (tap >= 0) {
-                    v = wt[co * kConvTaps + tap];
-                } else if (k == 27 || k == 28) {
-                    const float bb = bias[co];
-                    const __nv_bfloat16 hi = __float2bfloat16_rn(bb);
-                    v = k == 27 ? hi : __float2bfloat16_rn(bb - __bfloat162float(hi));
-                }
-                wv[r] = v;
+                wl[r] = i < kW ? __ldg(wsrc + i) : (unsigned short)0;
             }
+            const float bl = etid < kConvN ? __ldg(bias + etid) : 0.f;
 #pragma unroll
-            for (int r = 0; r < kPer; ++r) {
+            for (int r = 0; r < kWPer; ++r) {
                 const int i = etid + r * kEpiThreads;
-                const int p = i / (kConvN * kConvK), co = (i / kConvK) % kConvN, k = i % kConvK;
-                *reinterpret_cast<__nv_bfloat16 *>(sb + p * kOpBBytes + umma_off(co, k)) = wv[r];
+                if (i < kW) wraw[i] = wl[r];
+            }
+            if (etid < kConvN) braw[etid] = bl;
+            asm volatile("bar.sync 2, %0;" ::"n"(kEpiThreads) : "memory");
+            // the two B operands in the K order from the raw copy, one 16-byte
+            // core-matrix row (eight K positions of one channel) per store
+            constexpr int kRows = 2 * kConvN * (kConvK / 8);
+#pragma unroll
+            for (int r = 0; r < kRows / kEpiThreads; ++r) {
+                const int i = etid + r * kEpiThreads;
+                const int p = i / (kConvN * (kConvK / 8)), co = (i / (kConvK / 8)) % kConvN, kc = i % (kConvK / 8);
+                uint32_t q[4];
+#pragma unroll
+                for (int j = 0; j < 8; j += 2) {
+                    uint32_t two = 0;
+#pragma unroll
+                    for (int h2 = 0; h2 < 2; ++h2) {
+                        const int k = 8 * kc + j + h2, tap = conv_tap(p, k);
+                        uint32_t v = 0;
+                        if (tap >= 0) {
+                            v = wraw[co * kConvTaps + tap];
+                        } else if (k == 27 || k == 28) {
+                            const float bb = braw[co];
+                            const __nv_bfloat16 hi = __float2bfloat16_rn(bb);
+                            v = __bfloat16_as_ushort(k == 27 ? hi : __float2bfloat16_rn(bb - __bfloat162float(hi)));
+                        }
+                        two |= v << (16 * h2);
+                    }
+                    q[j / 2] = two;
+                }
+                *reinterpret_cast<uint4 *>(sb + p * kOpBBytes + umma_off(co, 8 * kc)) = make_uint4(q[0], q[1], q[2], q[3]);
             }
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // B: generic stores -> tensor-core reads
             asm volatile("bar.sync 3, %0;" ::"n"(kCtlThreads + kEpiThreads) : "memory");
