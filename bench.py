@@ -1294,6 +1294,7 @@ def run_ours(args, rank, world, local_rank):
             "gpu_launches": gpu_launches,
             "clocks": dict(clocks.summary(), window="warm-up through the last GPU measurement"),
         }
+        out["summary"] = compact_summary(out)
     clocks.__exit__(None, None, None)
     ctx.close()
     if dist:
@@ -1302,6 +1303,34 @@ def run_ours(args, rank, world, local_rank):
     if out is not None:
         print(json.dumps(out), flush=True)
         print_summary(out)
+
+
+def compact_summary(out):
+    """The bench line's headline results in a few hundred characters, placed
+    last on the line so that a reader who keeps only the line's end still has
+    them: per DAG the PARALLEL makespan (ms) and its speedups over
+    SERIAL_SYNC and over the hand-built CUDA Graph, with the fractions of the
+    critical-path and resource bounds; per served rate the p50 / p99 latency
+    (ms) and the served rate, with and without fusion and the admission
+    window; the kernels' cold solo fractions of HBM."""
+    r3 = lambda v: None if v is None else round(float(v), 3)
+    dags = {}
+    for name, d in (out.get("dags") or {}).items():
+        dags[name] = [r3(d["makespan_ms"]["parallel"]), r3(d["speedup_vs_serial_sync"]),
+                      r3(d["vs_hand_cuda_graph"]), r3(d["frac_of_cp_bound"]), r3(d["frac_of_resource_bound"])]
+    kern = {}
+    for d in (out.get("dags") or {}).values():
+        for k, v in d.get("per_kernel_solo", {}).items():
+            if v.get("frac_of_hbm_peak") is not None:
+                kern[k] = max(kern.get(k, 0.0), round(v["frac_of_hbm_peak"], 2))
+    serve = []
+    for rr in ((out.get("serve") or {}).get("runs") or []):
+        serve.append([rr["offered_req_s"], int(rr["fusion"]), int(rr.get("window_ms") is not None),
+                      r3(rr["throughput_req_s"]), r3(rr["p50_ms"]), r3(rr["p99_ms"])])
+    return {"dag_cols": ["parallel_ms", "vs_serial_sync", "vs_hand_graph", "of_cp_bound", "of_resource_bound"],
+            "dags": dags, "serve_cols": ["offered_req_s", "fusion", "admission_window", "served_req_s", "p50_ms", "p99_ms"],
+            "serve": serve, "kernel_cold_frac_of_hbm": kern,
+            "bs_call_frac": r3(out["roofline"]["frac"]), "e2e_ms": r3(out["e2e"]["ms_per_step"])}
 
 
 def print_summary(out):

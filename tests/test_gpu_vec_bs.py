@@ -136,6 +136,49 @@ def test_bs_other_parameters(K, r, sigma, T):
             assert ok, worst
 
 
+@pytest.mark.parametrize("n", [4, 7, 2047, 8195, 65539, 1_000_003, 5_000_001, 10_000_000, 20_000_002])
+def test_bs_automatic_and_explicit_launch_shapes(n):
+    """The automatic launch shape (a compile-time block size, four resident
+    waves) and an explicit one (run-time block size, another grid) price
+    every option with the same arithmetic, so the bits agree, and both are
+    within tolerance of the oracle.  The sizes cover fewer options than one
+    float4, ragged chunks and scalar tails, one chunk per block, and several
+    chunks per block."""
+    p = datagen.bs_inputs(n, count=1, seed=n % 1000)[0]
+    K, r, sg, T = 60.0, 0.1, 0.2, 1.0
+    S = torch.from_numpy(p).cuda()
+    C1 = torch.full_like(S, float("nan"))
+    C2 = torch.full_like(S, float("nan"))
+    with G.Context() as ctx:
+        a, c1, c2 = ctx.array(S), ctx.array(C1), ctx.array(C2)
+        ctx.launch("bs_call", a, c1, n, K, r, sg, T)
+        ctx.launch("bs_call", a, c2, n, K, r, sg, T, grid=(600, 1, 1), block=(256, 1, 1))
+        ctx.sync()
+    assert torch.equal(C1, C2)
+    ok, worst = close(C1.cpu().numpy(), N.bs_call(p))
+    assert ok, worst
+
+
+@pytest.mark.parametrize("off", [1, 2, 3])
+def test_bs_unaligned_arrays(off):
+    """Arrays that start off a 16-byte boundary take the scalar path of the
+    grid-stride kernel; prices within tolerance, nothing outside written."""
+    n = 100_003
+    p = datagen.bs_inputs(n, count=1, seed=off)[0]
+    base_s = torch.zeros(n + 4, dtype=torch.float32, device="cuda")
+    base_c = torch.full((n + 8,), -1.0, dtype=torch.float32, device="cuda")
+    base_s[off:off + n].copy_(torch.from_numpy(p))
+    with G.Context() as ctx:
+        a = ctx.array(dev=base_s.data_ptr() + 4 * off, nbytes=4 * n)
+        c = ctx.array(dev=base_c.data_ptr() + 4 * off, nbytes=4 * n)
+        ctx.launch("bs_call", a, c, n, 60.0, 0.1, 0.2, 1.0)
+        ctx.sync()
+    got = base_c.cpu().numpy()
+    ok, worst = close(got[off:off + n], N.bs_call(p))
+    assert ok, worst
+    assert (got[:off] == -1.0).all() and (got[off + n:] == -1.0).all()
+
+
 @pytest.mark.parametrize("policy", [G.GDAG_POLICY_PARALLEL, G.GDAG_POLICY_SERIAL_SYNC])
 def test_bs_full_config(policy):
     """B&S at the benchmark size (10 x 1e7), in the launch shape the bench
