@@ -731,8 +731,10 @@ def measure_dag(torch, G, spec, steps, peak_gbs, link):
     del cobj
     steps = max(steps, min(2000, int(50.0 / max(est_ms, 1e-3))))
 
-    def timed_ctx(policy, batched=True):
-        ctx = G.Context(policy=policy)
+    elements_per_step = {}
+
+    def timed_ctx(policy, batched=True, auto_graph=0, label=None):
+        ctx = G.Context(policy=policy, auto_graph=auto_graph)
         obj = spec.build(ctx, batched=batched)
         # warm-up: at least 10 steps and 20 ms, so that the context's stream
         # and event pools have reached their steady size
@@ -742,6 +744,7 @@ def measure_dag(torch, G, spec, steps, peak_gbs, link):
             k += 1
         ctx.sync()
         torch.cuda.synchronize()
+        nodes0 = G.gdag_stats_get(ctx.h).nodes
         if policy == G.GDAG_POLICY_SERIAL_SYNC or spec.host_sync:
             # a step that ends with a host read is complete when it returns:
             # timed on the host, like the hand-built graph's replay + sync
@@ -760,6 +763,8 @@ def measure_dag(torch, G, spec, steps, peak_gbs, link):
             e1.record(s0)
             torch.cuda.synchronize()
             ms = e0.elapsed_time(e1) / steps
+        if label:
+            elements_per_step[label] = (G.gdag_stats_get(ctx.h).nodes - nodes0) / steps
         ctx.sync()
         return ctx, obj, ms
 
@@ -769,7 +774,12 @@ def measure_dag(torch, G, spec, steps, peak_gbs, link):
     c1, o1, out["parallel_single_calls"] = timed_ctx(G.GDAG_POLICY_PARALLEL, batched=False)
     c1.close()
     del o1
-    ctx, obj, out["parallel"] = timed_ctx(G.GDAG_POLICY_PARALLEL)
+    # the same steps with the library's automatic capture of repeated
+    # sequences: after two issues a step's sequence replays as one graph
+    ca, oa, out["parallel_auto_graph"] = timed_ctx(G.GDAG_POLICY_PARALLEL, auto_graph=2, label="auto_graph")
+    ca.close()
+    del oa
+    ctx, obj, out["parallel"] = timed_ctx(G.GDAG_POLICY_PARALLEL, label="parallel")
     streams_used = ctx.stats()["streams"]
 
     def single_runs(c, o, policy, runs=30):
@@ -931,6 +941,8 @@ def measure_dag(torch, G, spec, steps, peak_gbs, link):
         "vs_hand_cuda_graph": out["hand_cuda_graph"] / out["parallel"],
         "library_graph_vs_hand_cuda_graph": out["hand_cuda_graph"] / out["library_graph"],
         "single_calls_vs_hand_cuda_graph": out["hand_cuda_graph"] / out["parallel_single_calls"],
+        "auto_graph_vs_hand_cuda_graph": out["hand_cuda_graph"] / out["parallel_auto_graph"],
+        "elements_per_step": elements_per_step,
         "frac_of_cp_bound": cp / out["parallel"], "frac_of_resource_bound": res / out["parallel"],
         "launches_per_step": kern, "per_kernel_solo": per_kernel,
         "makespan_single_run_ms": single, "overlap": overlap,
@@ -1309,7 +1321,8 @@ def compact_summary(out):
     """The bench line's headline results in a few hundred characters, placed
     last on the line so that a reader who keeps only the line's end still has
     them: per DAG the PARALLEL makespan (ms) and its speedups over
-    SERIAL_SYNC and over the hand-built CUDA Graph, with the fractions of the
+    SERIAL_SYNC and over the hand-built CUDA Graph, the automatically
+    captured and replayed steps against that graph, with the fractions of the
     critical-path and resource bounds; per served rate the p50 / p99 latency
     (ms) and the served rate, with and without fusion and the admission
     window; the kernels' cold solo fractions of HBM."""
@@ -1317,7 +1330,8 @@ def compact_summary(out):
     dags = {}
     for name, d in (out.get("dags") or {}).items():
         dags[name] = [r3(d["makespan_ms"]["parallel"]), r3(d["speedup_vs_serial_sync"]),
-                      r3(d["vs_hand_cuda_graph"]), r3(d["frac_of_cp_bound"]), r3(d["frac_of_resource_bound"])]
+                      r3(d["vs_hand_cuda_graph"]), r3(d.get("auto_graph_vs_hand_cuda_graph")),
+                      r3(d["frac_of_cp_bound"]), r3(d["frac_of_resource_bound"])]
     kern = {}
     for d in (out.get("dags") or {}).values():
         for k, v in d.get("per_kernel_solo", {}).items():
@@ -1327,7 +1341,8 @@ def compact_summary(out):
     for rr in ((out.get("serve") or {}).get("runs") or []):
         serve.append([rr["offered_req_s"], int(rr["fusion"]), int(rr.get("window_ms") is not None),
                       r3(rr["throughput_req_s"]), r3(rr["p50_ms"]), r3(rr["p99_ms"])])
-    return {"dag_cols": ["parallel_ms", "vs_serial_sync", "vs_hand_graph", "of_cp_bound", "of_resource_bound"],
+    return {"dag_cols": ["parallel_ms", "vs_serial_sync", "vs_hand_graph", "auto_graph_vs_hand_graph", "of_cp_bound",
+                         "of_resource_bound"],
             "dags": dags, "serve_cols": ["offered_req_s", "fusion", "admission_window", "served_req_s", "p50_ms", "p99_ms"],
             "serve": serve, "kernel_cold_frac_of_hbm": kern,
             "bs_call_frac": r3(out["roofline"]["frac"]), "e2e_ms": r3(out["e2e"]["ms_per_step"])}
@@ -1343,12 +1358,14 @@ def print_summary(out):
         out["unit"], e2e.get("ms_per_step", 0.0),
         "%.2f" % e2e["frac_of_duplex_copy"] if "frac_of_duplex_copy" in e2e else "n/a",
         out["roofline"]["kernel"], out["roofline"]["frac"]))
-    w("%-11s %8s %8s %8s %8s %8s %8s\n" % ("DAG", "par_ms", "vsSYNC", "vsGraph", "1call/G", "ofCP", "ofRes"))
+    w("%-11s %8s %8s %8s %8s %8s %8s %8s\n" % ("DAG", "par_ms", "vsSYNC", "vsGraph", "1call/G", "auto/G", "ofCP",
+                                                "ofRes"))
     for name, d in (out.get("dags") or {}).items():
         m = d["makespan_ms"]
-        w("%-11s %8.3f %8.2f %8.2f %8.2f %8.2f %8.2f\n" % (
+        w("%-11s %8.3f %8.2f %8.2f %8.2f %8.2f %8.2f %8.2f\n" % (
             name, m["parallel"], d["speedup_vs_serial_sync"], d["vs_hand_cuda_graph"],
-            d["single_calls_vs_hand_cuda_graph"], d["frac_of_cp_bound"], d["frac_of_resource_bound"]))
+            d["single_calls_vs_hand_cuda_graph"], d["auto_graph_vs_hand_cuda_graph"], d["frac_of_cp_bound"],
+            d["frac_of_resource_bound"]))
     sv = out.get("serve")
     if sv:
         for r in sv["runs"]:

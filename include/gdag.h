@@ -144,7 +144,11 @@ typedef struct {
                                 then prefers this context's pending work, e.g.
                                 a context serving short requests beside one
                                 serving long ones; default 0                  */
-    int32_t reserved0;       /* must be 0                                     */
+    int32_t auto_graph;      /* N > 0: gdag_issue captures a sequence it has
+                                been given N times (the same elements, arrays,
+                                scalar values and copy ranges) into a CUDA
+                                graph and replays it from then on; see
+                                gdag_issue.  0 = off (default)               */
 } gdag_options;
 
 /* Array argument or scalar argument of a launch. */
@@ -500,6 +504,30 @@ typedef struct {
  * both staging uses of a view in flight).  Errors: INVALID (an element
  * type, index range, or anything its single call rejects), CUDA, TIMEOUT,
  * POISONED. */
+/* Automatic capture of repeated sequences (options.auto_graph = N > 0; the
+ * repeated DAG shapes of Section IV-D's CUDA-graph comparison, captured and
+ * replayed without the caller marking them).  gdag_issue keys each sequence
+ * by its elements and the argument entries they use (arg0 itself excluded):
+ *   - the first N - 1 successful issues of a key run as described above;
+ *   - the N-th issue waits for all work (as gdag_capture_begin does), records
+ *     the sequence into a graph (nothing runs) and replays it; every later
+ *     issue of the key replays the graph (gdag_graph_launch: one DAG element
+ *     whose accesses are the union of the sequence's, so a later element
+ *     that touches any array of the sequence waits for the whole replay);
+ *     nodes_out then receives the replay's node for every element, and
+ *     *issued is n on success, 0 on failure;
+ *   - host writes in a replay copy what the array's host view holds when the
+ *     copy runs, as their single calls do;
+ *   - a graph whose arrays were registered again at another address or size
+ *     is dropped (after a wait for all work) and its key starts over; a
+ *     sequence that fails inside its capture is issued as above, now and
+ *     from then on;
+ *   - at most GDAG_AUTO_GRAPH_SEQS keys are kept: a new key beyond that
+ *     drops the least recently used one and its graph (after a wait for all
+ *     work);
+ *   - never captured: sequences holding a prefetch to the host, issues under
+ *     SERIAL_SYNC, with trace = 1, or inside an open gdag_capture_begin. */
+#define GDAG_AUTO_GRAPH_SEQS 64
 int gdag_issue(gdag_ctx *ctx, const gdag_elem *elems, int32_t n,
                const gdag_arg *args, int64_t nargs_total, int64_t *nodes_out,
                int32_t *issued);

@@ -147,6 +147,32 @@ struct Ctx {
     };
     std::vector<Graph> graphs;
 
+    // automatic capture of repeated gdag_issue sequences (options.auto_graph)
+    struct AutoSeq {
+        uint64_t hash = 0;
+        std::vector<uint64_t> key;  // the sequence's elements and the arguments they use
+        int32_t seen = 0;           // dynamic issues of it so far
+        int32_t graph = -1;         // its graph, once captured
+        bool never = false;         // its capture failed: always issued dynamically
+        uint64_t used = 0;          // last use, for least-recently-used eviction
+    };
+    std::vector<AutoSeq> auto_seqs;
+    uint64_t auto_clock = 0;
+
+    // the graph still holds the addresses and sizes its arrays have now
+    bool graph_current(int32_t g) const
+    {
+        if (g < 0 || (size_t)g >= graphs.size() || !graphs[(size_t)g].live) return false;
+        const Graph &gr = graphs[(size_t)g];
+        for (size_t i = 0; i < gr.access.size(); ++i) {
+            const int32_t a = gr.access[i].array;
+            if (a < 0 || (size_t)a >= arrays.size() || !arrays[(size_t)a].live) return false;
+            const ArrayState &st = arrays[(size_t)a];
+            if (st.dev != gr.dev[i] || (gr.host[i] && st.host != gr.host[i]) || st.bytes != gr.bytes[i]) return false;
+        }
+        return true;
+    }
+
     void capture_note(const Access *acc, int n)
     {
         if (!capturing) return;
@@ -740,7 +766,7 @@ int gdag_create(gdag_ctx **out, const gdag_options *opts)
     else
         gdag_options_default(&o);
     if (o.policy < 0 || o.policy > 2 || o.max_streams < 1 || o.max_streams > 1024 || o.timeout_ms <= 0 ||
-        o.record_log < 0 || o.record_log > 2 || o.trim_nodes < 0 || o.reserved0 != 0 ||
+        o.record_log < 0 || o.record_log > 2 || o.trim_nodes < 0 || o.auto_graph < 0 ||
         (o.backend != GDAG_BACKEND_CUDA && o.backend != GDAG_BACKEND_FAKE))
         return GDAG_ERR_INVALID;
     gdag_ctx *c = new (std::nothrow) gdag_ctx();
@@ -1252,13 +1278,11 @@ int gdag_array_prefetch_host(gdag_ctx *c, gdag_array a, size_t off, size_t bytes
     return c->finish(id, st);
 }
 
-int gdag_issue(gdag_ctx *c, const gdag_elem *elems, int32_t n, const gdag_arg *args, int64_t nargs_total,
-               int64_t *nodes_out, int32_t *issued)
+// gdag_issue without the automatic capture: each element as its own call
+static int issue_each(gdag_ctx *c, const gdag_elem *elems, int32_t n, const gdag_arg *args, int64_t nargs_total,
+                      int64_t *nodes_out, int32_t *issued)
 {
     if (issued) *issued = 0;
-    if (!c) return GDAG_ERR_INVALID;
-    if (n < 0 || (n && !elems) || nargs_total < 0 || (nargs_total && !args))
-        return c->fail(GDAG_ERR_INVALID, "bad element or argument list");
     if (nodes_out)
         for (int32_t i = 0; i < n; ++i) nodes_out[i] = -1;
     for (int32_t i = 0; i < n; ++i) {
@@ -1300,6 +1324,126 @@ int gdag_issue(gdag_ctx *c, const gdag_elem *elems, int32_t n, const gdag_arg *a
         if (issued) *issued = i + 1;
     }
     return GDAG_OK;
+}
+
+// The key of a sequence for the automatic capture: every field of every
+// element but arg0, then the argument entries each launch element uses (so
+// that the same elements with other scalar values or arrays make another
+// key).  False for a sequence that is never captured: one holding a
+// prefetch to the host (not allowed in a capture) or an argument range
+// outside the list (the dynamic issue reports it).
+static bool auto_key(const gdag_elem *elems, int32_t n, const gdag_arg *args, int64_t nargs_total,
+                     std::vector<uint64_t> &key, uint64_t &hash)
+{
+    key.clear();
+    auto u = [](int32_t a, int32_t b) { return ((uint64_t)(uint32_t)a << 32) | (uint32_t)b; };
+    for (int32_t i = 0; i < n; ++i) {
+        const gdag_elem &e = elems[i];
+        if (e.type != GDAG_ELEM_LAUNCH && e.type != GDAG_ELEM_LAUNCH_FUSED && e.type != GDAG_ELEM_WRITE) return false;
+        key.push_back(u(e.type, e.kernel));
+        key.push_back(u(e.array, e.nargs));
+        key.push_back(u(e.count, (int32_t)e.smem));
+        key.push_back(e.off);
+        key.push_back(e.bytes);
+        key.push_back(u((int32_t)e.grid.x, (int32_t)e.grid.y));
+        key.push_back(u((int32_t)e.grid.z, (int32_t)e.block.x));
+        key.push_back(u((int32_t)e.block.y, (int32_t)e.block.z));
+        if (e.type == GDAG_ELEM_WRITE) continue;
+        const int64_t count = e.type == GDAG_ELEM_LAUNCH ? 1 : (int64_t)e.count;
+        if (e.nargs < 0 || count < 1 || e.arg0 < 0 || e.arg0 > nargs_total ||
+            (int64_t)e.nargs * count > nargs_total - e.arg0)
+            return false;
+        for (int64_t j = 0; j < (int64_t)e.nargs * count; ++j) {
+            const gdag_arg &a = args[e.arg0 + j];
+            key.push_back(u(a.kind, a.mode));
+            key.push_back(u(a.array, a.size));
+            key.push_back(a.value);
+        }
+    }
+    hash = 1469598103934665603ull;  // FNV-1a over the words
+    for (uint64_t w : key) hash = (hash ^ w) * 1099511628211ull;
+    return true;
+}
+
+// Replay graph g as the whole sequence: every element's node is the graph's.
+static int auto_replay(gdag_ctx *c, int32_t g, int32_t n, int64_t *nodes_out, int32_t *issued)
+{
+    const int64_t before = c->next_id();
+    int64_t node = -1;
+    const int r = gdag_graph_launch(c, g, &node);
+    if (c->next_id() == before) node = -1;
+    if (nodes_out)
+        for (int32_t i = 0; i < n; ++i) nodes_out[i] = node;
+    if (issued) *issued = r ? 0 : n;
+    return r;
+}
+
+int gdag_issue(gdag_ctx *c, const gdag_elem *elems, int32_t n, const gdag_arg *args, int64_t nargs_total,
+               int64_t *nodes_out, int32_t *issued)
+{
+    if (issued) *issued = 0;
+    if (!c) return GDAG_ERR_INVALID;
+    if (n < 0 || (n && !elems) || nargs_total < 0 || (nargs_total && !args))
+        return c->fail(GDAG_ERR_INVALID, "bad element or argument list");
+    if (c->opt.auto_graph <= 0 || c->capturing || c->opt.trace || c->opt.policy == GDAG_POLICY_SERIAL_SYNC ||
+        n == 0 || c->poisoned)
+        return issue_each(c, elems, n, args, nargs_total, nodes_out, issued);
+    std::vector<uint64_t> key;
+    uint64_t hash = 0;
+    if (!auto_key(elems, n, args, nargs_total, key, hash))
+        return issue_each(c, elems, n, args, nargs_total, nodes_out, issued);
+    size_t i = 0;
+    while (i < c->auto_seqs.size() && !(c->auto_seqs[i].hash == hash && c->auto_seqs[i].key == key)) ++i;
+    if (i == c->auto_seqs.size()) {
+        if (c->auto_seqs.size() >= (size_t)GDAG_AUTO_GRAPH_SEQS) {
+            // the least recently used sequence leaves, with its graph
+            size_t lru = 0;
+            for (size_t j = 1; j < c->auto_seqs.size(); ++j)
+                if (c->auto_seqs[j].used < c->auto_seqs[lru].used) lru = j;
+            if (c->auto_seqs[lru].graph >= 0) {
+                const int r = gdag_graph_destroy(c, c->auto_seqs[lru].graph);
+                if (r) return r;
+            }
+            c->auto_seqs.erase(c->auto_seqs.begin() + (std::ptrdiff_t)lru);
+            i = c->auto_seqs.size();
+        }
+        Ctx::AutoSeq q;
+        q.hash = hash;
+        q.key.swap(key);
+        c->auto_seqs.push_back(std::move(q));
+    }
+    c->auto_seqs[i].used = ++c->auto_clock;
+    if (c->auto_seqs[i].graph >= 0) {
+        if (c->graph_current(c->auto_seqs[i].graph)) return auto_replay(c, c->auto_seqs[i].graph, n, nodes_out, issued);
+        // an array moved since the capture: drop the graph and start over
+        const int r = gdag_graph_destroy(c, c->auto_seqs[i].graph);
+        c->auto_seqs[i].graph = -1;
+        c->auto_seqs[i].seen = 0;
+        if (r) return r;
+    }
+    if (c->auto_seqs[i].never || c->auto_seqs[i].seen + 1 < c->opt.auto_graph) {
+        const int r = issue_each(c, elems, n, args, nargs_total, nodes_out, issued);
+        if (!r) ++c->auto_seqs[i].seen;
+        return r;
+    }
+    // the auto_graph-th issue: capture the sequence (nothing runs), then
+    // replay it; a sequence that fails inside the capture is issued
+    // dynamically now and from then on, where it succeeds or fails as its
+    // single calls would
+    int r = gdag_capture_begin(c);
+    if (r) return r;
+    int32_t cap_issued = 0;
+    const int rc = issue_each(c, elems, n, args, nargs_total, nullptr, &cap_issued);
+    gdag_graph g = -1;
+    const int re = gdag_capture_end(c, &g);
+    if (rc || re) {
+        if (!re && g >= 0) gdag_graph_destroy(c, g);
+        if (c->poisoned) return re ? re : rc;
+        c->auto_seqs[i].never = true;
+        return issue_each(c, elems, n, args, nargs_total, nodes_out, issued);
+    }
+    c->auto_seqs[i].graph = g;
+    return auto_replay(c, g, n, nodes_out, issued);
 }
 
 int gdag_sync(gdag_ctx *c)

@@ -58,6 +58,7 @@ GDAG_ARG_ARRAY, GDAG_ARG_SCALAR = 0, 1
 GDAG_ELEM_LAUNCH, GDAG_ELEM_LAUNCH_FUSED, GDAG_ELEM_WRITE, GDAG_ELEM_PREFETCH_HOST = 0, 1, 2, 3
 GDAG_FUSED_MAX = 4096     # members per gdag_launch_fused call
 GDAG_FUSED_TABLE = 128    # members per persistent launch of a fused element
+GDAG_AUTO_GRAPH_SEQS = 64 # sequences the automatic capture keeps (options.auto_graph)
 (GDAG_OP_LAUNCH, GDAG_OP_COPY_H2D, GDAG_OP_COPY_D2H, GDAG_OP_EXTERNAL, GDAG_OP_RECORD, GDAG_OP_WAIT,
  GDAG_OP_HOST_WAIT, GDAG_OP_STREAM_SYNC, GDAG_OP_HOST_NODE, GDAG_OP_QUERY_DONE) = range(10)
 
@@ -73,7 +74,7 @@ class gdag_options(ctypes.Structure):
                 ("retire_by_query", ctypes.c_int32), ("record_log", ctypes.c_int32),
                 ("trace", ctypes.c_int32), ("timeout_ms", ctypes.c_int32), ("trim_nodes", ctypes.c_int32),
                 ("fake_complete", ctypes.c_int32), ("fake_fail_sticky", ctypes.c_int32),
-                ("fake_fail_op", ctypes.c_int64), ("stream_priority", ctypes.c_int32), ("reserved0", ctypes.c_int32)]
+                ("fake_fail_op", ctypes.c_int64), ("stream_priority", ctypes.c_int32), ("auto_graph", ctypes.c_int32)]
 
 
 class gdag_arg(ctypes.Structure):
@@ -477,7 +478,7 @@ class Context:
 
     def __init__(self, policy=GDAG_POLICY_PARALLEL, backend="cuda", device=0, max_streams=16, prefetch=True,
                  retire_by_query=False, record_log=False, trace=False, timeout_ms=60000, trim_nodes=0,
-                 fake_complete=False, fake_fail_op=-1, fake_fail_sticky=False, stream_priority=0):
+                 fake_complete=False, fake_fail_op=-1, fake_fail_sticky=False, stream_priority=0, auto_graph=0):
         o = gdag_options_default()
         o.policy = policy
         o.backend = GDAG_BACKEND_FAKE if backend == "fake" else GDAG_BACKEND_CUDA
@@ -493,6 +494,7 @@ class Context:
         o.fake_fail_op = fake_fail_op
         o.fake_fail_sticky = int(fake_fail_sticky)
         o.stream_priority = stream_priority
+        o.auto_graph = auto_graph
         self.options = o
         self.h = gdag_create(o)
         self._kernels = {}

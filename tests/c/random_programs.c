@@ -6,6 +6,7 @@
  * end state are checked.  Usage: random_programs <programs> <steps> <seed>. */
 #include <stdint.h>
 #include <stdio.h>
+#include <string.h>
 #include <stdlib.h>
 
 #include "gdag.h"
@@ -50,6 +51,7 @@ int main(int argc, char **argv)
         o.trim_nodes = trims[rnd(6)];
         o.fake_fail_op = rnd(3) == 0 ? (int64_t)rnd(400) : -1;
         o.fake_fail_sticky = rnd(4) == 0;
+        o.auto_graph = (int32_t)rnd(3);
         gdag_ctx *c = NULL;
         if (gdag_create(&c, &o)) {
             printf("create failed\n");
@@ -133,6 +135,33 @@ int main(int argc, char **argv)
                 }
             } else if (r < 44) {
                 gdag_sync(c);
+            } else if (r < 48) {
+                /* a two-element sequence through gdag_issue: repeated keys are
+                   captured and replayed under auto_graph, many keys evict */
+                gdag_elem e[2];
+                memset(e, 0, sizeof e);
+                gdag_arg g[2];
+                e[0].type = GDAG_ELEM_WRITE;
+                e[0].array = arr[a];
+                e[0].off = off;
+                e[0].bytes = bytes;
+                e[1].type = GDAG_ELEM_LAUNCH;
+                e[1].kernel = kern[2];
+                e[1].nargs = 2;
+                e[1].arg0 = 0;
+                e[1].grid = one;
+                e[1].block = warp;
+                for (int i = 0; i < 2; ++i) {
+                    const int32_t modes[4] = {GDAG_MODE_IN, GDAG_MODE_IN, GDAG_MODE_OUT, GDAG_MODE_INOUT};
+                    g[i].kind = GDAG_ARG_ARRAY;
+                    g[i].mode = modes[rnd(4)];
+                    g[i].array = arr[(a + i) % na];
+                    g[i].size = 0;
+                    g[i].value = 0;
+                }
+                int64_t nodes[2];
+                int32_t issued = 0;
+                gdag_issue(c, e, 2, g, 2, nodes, &issued);
             } else if (r < 52) {
                 gdag_stats st;
                 gdag_stats_get(c, &st);

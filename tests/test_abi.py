@@ -38,3 +38,15 @@ def test_builtin_kernel_table():
 def test_scratch_sizes():
     assert G.gdag_scratch_bytes("vec_reduce_diff", 10) >= 8 * 1024 + 4
     assert G.gdag_scratch_bytes("bs_call", 10) == 0
+
+
+def test_binding_constants_match_the_header():
+    """Every integer #define of gdag.h that the binding mirrors has the
+    header's value (the ctypes binding cannot include the header)."""
+    hdr = open(HEADER).read()
+    seen = 0
+    for name, val in re.findall(r"^#define (GDAG_\w+)\s+(-?\d+)\b", hdr, flags=re.M):
+        if hasattr(G, name):
+            assert getattr(G, name) == int(val), name
+            seen += 1
+    assert seen >= 40 and G.GDAG_AUTO_GRAPH_SEQS == 64

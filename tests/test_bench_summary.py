@@ -9,7 +9,8 @@ import bench
 
 def fake_line():
     dag = lambda ms: {"makespan_ms": {"parallel": ms}, "speedup_vs_serial_sync": 1.5, "vs_hand_cuda_graph": 1.01,
-                      "frac_of_cp_bound": 0.5, "frac_of_resource_bound": 0.9,
+                      "auto_graph_vs_hand_cuda_graph": 1.02, "frac_of_cp_bound": 0.5,
+                      "frac_of_resource_bound": 0.9,
                       "per_kernel_solo": {"k%d" % i: {"frac_of_hbm_peak": 0.1 * i} for i in range(1, 4)}}
     names = ["B&S", "VEC", "IMG", "ML", "HITS", "DL", "HITS-batch"]
     out = {"metric": "m", "value": 1.0, "roofline": {"frac": 0.7471}, "e2e": {"ms_per_step": 2.6601},
@@ -36,7 +37,7 @@ def test_summary_is_last_and_fits_the_tail():
 def test_summary_values_come_from_the_detailed_keys():
     out = fake_line()
     s = out["summary"]
-    assert s["dags"]["DL"] == [0.6, 1.5, 1.01, 0.5, 0.9]
+    assert s["dags"]["DL"] == [0.6, 1.5, 1.01, 1.02, 0.5, 0.9]
     assert [r[:3] for r in s["serve"]] == [[2000.0, 1, 1], [2000.0, 0, 1], [1000.0, 1, 1], [2000.0, 1, 0]]
     assert s["serve"][0][3:] == [1999.0, 0.3, 19.0]
     assert s["kernel_cold_frac_of_hbm"]["k3"] == 0.3
