@@ -81,6 +81,10 @@ class VecDag(_Issuer):
         self.y = torch.zeros(max(n, 1), dtype=F32, device=device)
         self.z = torch.zeros(1, dtype=F32, device=device)
         self.hx, self.hy, self.hz = _pinned(max(n, 1), F32), _pinned(max(n, 1), F32), _pinned(1, F32)
+        # the result is read through a numpy view of the pinned scalar: a
+        # torch element access costs the host several microseconds, which a
+        # host-synchronised step of this size would pay on its critical path
+        self._hz_np = self.hz.numpy()
         self.X = ctx.array(self.x, host=self.hx, name="x")
         self.Y = ctx.array(self.y, host=self.hy, name="y")
         self.Z = ctx.array(self.z, host=self.hz, name="z")
@@ -103,7 +107,7 @@ class VecDag(_Issuer):
         self._run("step", self._elements)
         if read:
             self.ctx.read(self.Z)
-            return float(self.hz[0])
+            return float(self._hz_np[0])
         return None
 
 
