@@ -35,8 +35,11 @@ def run(rows, feats, classes, seed, inputs=None, scores_only=False):
 
 # feats a multiple of 64 up to 1024 runs on the tensor cores, the others on
 # CUDA cores
+# 19457 and 40001 rows split over 152 CTAs leave each a partial last tile
+# (127 or 128 rows; 7 past two full tiles), copied in 8-row boxes
 @pytest.mark.parametrize("rows,feats,classes", [(1, 32, 10), (7, 64, 3), (100, 1024, 10), (1001, 256, 12),
-                                                (333, 96, 1), (64, 32, 16), (129, 1024, 16), (300, 640, 1)])
+                                                (333, 96, 1), (64, 32, 16), (129, 1024, 16), (300, 640, 1),
+                                                (19457, 1024, 10), (40001, 512, 10)])
 def test_scores_bit_exact_with_dyadic_tables(rows, feats, classes):
     ctx, d, (X, T1, b1, T2, b2) = run(rows, feats, classes, seed=rows, scores_only=True)
     s1 = d.S1[:rows].cpu().numpy()
@@ -61,9 +64,10 @@ def test_scores_general_tables_within_tolerance():
 
 
 def test_scores_out_of_bf16_range_rows_fall_back_exactly():
-    """Feature values beyond +-256 (not exact in bf16) send their 128-row
-    tile to the CUDA-core path: those rows meet the tolerance, every other
-    row stays bit-exact (dyadic tables)."""
+    """Feature values beyond +-256 (not exact in bf16) send their tile (at
+    most 128 rows) to the CUDA-core path: those rows meet the tolerance, and
+    every row further than a tile from such a row stays bit-exact (dyadic
+    tables)."""
     rows, feats, classes = 1000, 1024, 10
     X, T1, b1, T2, b2 = datagen.ml_inputs(rows, feats=feats, classes=classes, seed=11)
     X = X.copy()
@@ -78,7 +82,7 @@ def test_scores_out_of_bf16_range_rows_fall_back_exactly():
     assert np.all(np.abs(got - ref) <= TOL * np.maximum(scale, 1.0))
     clean = np.ones(rows, bool)
     for r in (5, 300, 999, 640):
-        clean[(r // 128) * 128:(r // 128 + 1) * 128] = False
+        clean[max(0, r - 127):r + 128] = False
     assert np.array_equal(got[clean], ref[clean])
     ctx.close()
 
