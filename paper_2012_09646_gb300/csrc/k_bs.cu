@@ -17,9 +17,10 @@
 //  - d1 and d2 travel as one float2 through the packed fp32x2 FMA/MUL of
 //    sm_100+ (__ffma2_rn, __fmul2_rn): both CDFs cost one Horner chain;
 //  - the transcendentals are single MUFU operations written as PTX:
-//    lg2.approx for the logarithm, ex2.approx for phi, rcp.approx for
-//    1/(Q(z1) Q(z2)), from which both 1/Q follow by one packed multiply
-//    (Q stays below 1e8 for |d| <= 40, so the product cannot overflow);
+//    lg2.approx for the logarithm, ex2.approx for phi, rcp.approx for each
+//    1/Q (five per option: the multiply pipe, not the MUFU pipe, is the
+//    busier one, so one reciprocal of Q(z1) Q(z2) and a packed multiply to
+//    split it would cost more than the reciprocal they save);
 //  - d1 = lg2(S) (ln2 / (sigma sqrt T)) + (drift - ln K) / (sigma sqrt T) is
 //    one FMA, with both constants computed in double on the host.
 // Error: a shift e common to d1 and d2 (the logarithm's error, the rounding
@@ -83,8 +84,7 @@ __device__ __forceinline__ float2 norm_cdf2(float2 d)
     q = __ffma2_rn(q, z, f2(1.000000000e+00f));
     const float2 t = __fmul2_rn(__fmul2_rn(z, z), f2(-7.213475204e-01f));  // -z^2 log2(e) / 2
     const float2 e = make_float2(ex2_approx(t.x), ex2_approx(t.y));
-    const float rq = rcp_approx(q.x * q.y);                                // 1 / (Q(z1) Q(z2))
-    const float2 inv_q = __fmul2_rn(make_float2(q.y, q.x), f2(rq));
+    const float2 inv_q = make_float2(rcp_approx(q.x), rcp_approx(q.y));
     const float2 tail = __fmul2_rn(__fmul2_rn(p, inv_q), e);                // phi(z) R(z)
     return make_float2(d.x < 0.f ? tail.x : 1.0f - tail.x, d.y < 0.f ? tail.y : 1.0f - tail.y);
 }
