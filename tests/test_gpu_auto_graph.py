@@ -99,3 +99,44 @@ def test_replay_follows_a_moved_array():
             assert v.step() == z0  # the host view still holds y
         ctx.sync()
         assert torch.equal(y2.cpu(), torch.from_numpy(y * y))
+
+
+def test_ml_hits_dl_replayed_equal_dynamic_and_oracle():
+    """The other DAGs of the suite with automatic graphs: ML (two score
+    nodes, softmaxes, labels), HITS (two alternating iteration sequences,
+    each captured at its second issue) and DL (two tensor-core branches):
+    every output bit-identical to the dynamic path's, and within tolerance
+    of the oracle."""
+    from paper_2012_09646_gb300.workloads import DlDag, HitsDag, MlDag
+    rows = 4097
+    ml_in = datagen.ml_inputs(rows, feats=1024, classes=10, seed=21)
+    csr, csc = datagen.hits_graph(20000, 150000, seed=22)
+    dl_in, _bits = datagen.dl_inputs(n=2, h=34, w=192, seed=23)
+    outs = {}
+    for auto in (0, 2):
+        with G.Context(auto_graph=auto) as ctx:
+            m = MlDag(ctx, rows)
+            m.load(*ml_in)
+            for _ in range(4):
+                m.step()
+            ctx.sync()
+            h = HitsDag(ctx, csr, csc)
+            ka, kh = h.run(iters=5)
+            d = DlDag(ctx, 2, 34, 192)
+            d.load(*dl_in)
+            for _ in range(3):
+                d.step()
+            ctx.sync()
+            assert d.status.tolist() == [0, 0]
+            outs[auto] = [m.S1.clone(), m.S2.clone(), m.labels.clone(), h.vec[ka].clone(), h.vec[kh].clone(),
+                          d.p1.clone(), d.p2.clone(), d.logits.clone()]
+    for a, b in zip(outs[0], outs[2]):
+        assert torch.equal(a, b)
+    ref = P.ml(*ml_in)
+    # the score arrays hold the row softmaxes after a step (in place)
+    p1 = outs[2][0][:rows].cpu().numpy().astype(np.float64)
+    assert np.all(np.abs(p1 - ref["p1"]) <= TOL * np.maximum(np.abs(ref["p1"]), 1.0))
+    hits = P.hits(csr, csc, iters=5)
+    for got, want in ((outs[2][3], hits["a"][-1]), (outs[2][4], hits["h"][-1])):
+        got = got[:20000].cpu().numpy().astype(np.float64)
+        assert np.all(np.abs(got - want) <= TOL * np.maximum(np.abs(want), 1.0))
