@@ -231,10 +231,9 @@ typedef struct {
 /* Fill *o with the defaults listed in gdag_options, then apply environment
  * overrides where set to an integer: GDAG_POLICY, GDAG_MAX_STREAMS,
  * GDAG_PREFETCH, GDAG_RETIRE_BY_QUERY, GDAG_RECORD_LOG, GDAG_TRACE,
- * GDAG_TIMEOUT_MS, GDAG_DEVICE, GDAG_TRIM_NODES, GDAG_STREAM_PRIORITY (a
- * caller may still change
- * any field before
- * gdag_create, which validates them). */
+ * GDAG_TIMEOUT_MS, GDAG_DEVICE, GDAG_TRIM_NODES, GDAG_STREAM_PRIORITY,
+ * GDAG_AUTO_GRAPH (a caller may still change any field before gdag_create,
+ * which validates them). */
 void gdag_options_default(gdag_options *o);
 
 /* Create a context.  opts may be NULL (defaults).  With the CUDA backend the

@@ -746,7 +746,8 @@ void gdag_options_default(gdag_options *o)
                {"GDAG_PREFETCH", &o->prefetch},       {"GDAG_RETIRE_BY_QUERY", &o->retire_by_query},
                {"GDAG_RECORD_LOG", &o->record_log},   {"GDAG_TRACE", &o->trace},
                {"GDAG_TIMEOUT_MS", &o->timeout_ms}, {"GDAG_DEVICE", &o->device},
-               {"GDAG_TRIM_NODES", &o->trim_nodes}, {"GDAG_STREAM_PRIORITY", &o->stream_priority}};
+               {"GDAG_TRIM_NODES", &o->trim_nodes}, {"GDAG_STREAM_PRIORITY", &o->stream_priority},
+               {"GDAG_AUTO_GRAPH", &o->auto_graph}};
     for (const auto &e : env) {
         const char *v = std::getenv(e.name);
         if (!v || !*v) continue;

@@ -448,9 +448,10 @@ def test_option_environment_overrides(monkeypatch):
     monkeypatch.setenv("GDAG_PREFETCH", "not a number")
     monkeypatch.setenv("GDAG_TRIM_NODES", "4096")
     monkeypatch.setenv("GDAG_RECORD_LOG", "2")
+    monkeypatch.setenv("GDAG_AUTO_GRAPH", "3")
     o = G.gdag_options_default()
     assert o.max_streams == 5 and o.timeout_ms == 1234 and o.prefetch == 1
-    assert o.trim_nodes == 4096 and o.record_log == 2
+    assert o.trim_nodes == 4096 and o.record_log == 2 and o.auto_graph == 3
 
 
 @pytest.mark.parametrize("fail_op,where", [(4, "wait"), (5, "launch"), (6, "event record")])
