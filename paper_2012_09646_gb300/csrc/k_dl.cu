@@ -102,6 +102,7 @@ constexpr size_t kConvSmemUsed = kOffBars + kNumBars * 8 + 16;
 // one CTA (holding all 512 tensor-memory columns) owns an SM
 constexpr size_t kConvSmem = 160 * 1024;
 static_assert(kConvSmemUsed <= kConvSmem, "conv shared memory");
+static_assert(kConvSmem < (size_t)(0x4000 << 4), "shared addresses fit a matrix descriptor's 14-bit start field");
 static_assert(2 * kConvN * kConvTaps + 4 * kConvN <= kStageBytes, "raw weights must fit one staging buffer");
 static_assert((2 * kConvN * (kConvK / 8)) % kEpiThreads == 0, "B rows split evenly over the epilogue");
 static_assert(kOffHalo % 128 == 0 && kHaloBoxStride % 128 == 0 && kHaloBytes % 128 == 0 && kOffStage % 128 == 0 &&
@@ -238,6 +239,7 @@ __global__ void __launch_bounds__(kConvThreads, 1)
         // the whole warp meets the epilogue warps, which staged the weights
         asm volatile("bar.sync 3, %0;" ::"n"(kCtlThreads + kEpiThreads) : "memory");
         if (lane == 0) {
+            const uint64_t a_desc0 = umma_desc(smem_addr(sa)), b_desc0 = umma_desc(smem_addr(sb));
             uint32_t it = 0;
             for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
                 const int s = it & 1;
@@ -258,13 +260,15 @@ __global__ void __launch_bounds__(kConvThreads, 1)
                     break;
                 }
                 asm volatile("tcgen05.fence::after_thread_sync;");
-                const unsigned char *As = sa + s * kOpASet;
+                // descriptors differ from the first one only in their start
+                // address field (no carry: shared addresses stay below 256 KB)
+                const uint64_t a_set = a_desc0 + (uint64_t)(s * (kOpASet >> 4));
 #pragma unroll
                 for (int a = 0; a < 4; ++a)
 #pragma unroll
                     for (int ks = 0; ks < kConvK / 16; ++ks) {
-                        const uint64_t ad = umma_desc(smem_addr(As + a * kOpABytes) + ks * 256);
-                        const uint64_t bd = umma_desc(smem_addr(sb + (a & 1) * kOpBBytes) + ks * 256);
+                        const uint64_t ad = a_set + (uint64_t)((a * kOpABytes + ks * 256) >> 4);
+                        const uint64_t bd = b_desc0 + (uint64_t)(((a & 1) * kOpBBytes + ks * 256) >> 4);
                         asm volatile("{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
                                      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(
                                          tmem + s * kAccCols + a * kConvN),
@@ -377,32 +381,39 @@ __global__ void __launch_bounds__(kConvThreads, 1)
             if (etid < kConvN) braw[etid] = bl;
             asm volatile("bar.sync 2, %0;" ::"n"(kEpiThreads) : "memory");
             // the two B operands in the K order from the raw copy, one 16-byte
-            // core-matrix row (eight K positions of one channel) per store
-            constexpr int kRows = 2 * kConvN * (kConvK / 8);
+            // core-matrix row (eight K positions of one channel) per store.
+            // Thread etid builds the rows of channel etid % 64 at K chunk
+            // etid / 64 (uniform over a warp) for both parities: the chunk
+            // is matched against compile-time values, so every tap index
+            // below is a constant
+            constexpr int kKc = kConvK / 8;
+            static_assert(kEpiThreads == kConvN * kKc, "one channel and K chunk per epilogue thread");
+            const int co = etid % kConvN, kq = etid / kConvN;
+            const float bb = braw[co];
+            const __nv_bfloat16 bhi = __float2bfloat16_rn(bb);
+            const uint32_t bias_hi = __bfloat16_as_ushort(bhi);
+            const uint32_t bias_lo = __bfloat16_as_ushort(__float2bfloat16_rn(bb - __bfloat162float(bhi)));
 #pragma unroll
-            for (int r = 0; r < kRows / kEpiThreads; ++r) {
-                const int i = etid + r * kEpiThreads;
-                const int p = i / (kConvN * (kConvK / 8)), co = (i / (kConvK / 8)) % kConvN, kc = i % (kConvK / 8);
-                uint32_t q[4];
+            for (int kc = 0; kc < kKc; ++kc) {
+                if (kc != kq) continue;
 #pragma unroll
-                for (int j = 0; j < 8; j += 2) {
-                    uint32_t two = 0;
+                for (int p = 0; p < 2; ++p) {
+                    uint32_t q[4];
 #pragma unroll
-                    for (int h2 = 0; h2 < 2; ++h2) {
-                        const int k = 8 * kc + j + h2, tap = conv_tap(p, k);
-                        uint32_t v = 0;
-                        if (tap >= 0) {
-                            v = wraw[co * kConvTaps + tap];
-                        } else if (k == 27 || k == 28) {
-                            const float bb = braw[co];
-                            const __nv_bfloat16 hi = __float2bfloat16_rn(bb);
-                            v = __bfloat16_as_ushort(k == 27 ? hi : __float2bfloat16_rn(bb - __bfloat162float(hi)));
+                    for (int j = 0; j < 8; j += 2) {
+                        uint32_t two = 0;
+#pragma unroll
+                        for (int h2 = 0; h2 < 2; ++h2) {
+                            const int k = 8 * kc + j + h2, tap = conv_tap(p, k);
+                            const uint32_t v = tap >= 0 ? (uint32_t)wraw[co * kConvTaps + tap]
+                                                        : (k == 27 ? bias_hi : (k == 28 ? bias_lo : 0u));
+                            two |= v << (16 * h2);
                         }
-                        two |= v << (16 * h2);
+                        q[j / 2] = two;
                     }
-                    q[j / 2] = two;
+                    *reinterpret_cast<uint4 *>(sb + p * kOpBBytes + umma_off(co, 8 * kc)) =
+                        make_uint4(q[0], q[1], q[2], q[3]);
                 }
-                *reinterpret_cast<uint4 *>(sb + p * kOpBBytes + umma_off(co, 8 * kc)) = make_uint4(q[0], q[1], q[2], q[3]);
             }
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // B: generic stores -> tensor-core reads
             asm volatile("bar.sync 3, %0;" ::"n"(kCtlThreads + kEpiThreads) : "memory");
@@ -412,6 +423,8 @@ __global__ void __launch_bounds__(kConvThreads, 1)
         uint32_t it = 0;
         for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
             const int s = it & 1;
+            int b, y0, x0;  // the tile's coordinates, computed while its MMAs may still run
+            conv_tile_coords(tile, tiles_x, rows2, b, y0, x0);
             const bool fok = mbar_wait_bounded(full_bar + 8 * s, (it >> 1) & 1, abort);
             asm volatile("tcgen05.fence::after_thread_sync;");
             unsigned char *sg = stage + s * kStageBytes;
@@ -463,8 +476,6 @@ __global__ void __launch_bounds__(kConvThreads, 1)
                 if (etid == 0) *abort = 1;
                 break;
             }
-            int b, y0, x0;
-            conv_tile_coords(tile, tiles_x, rows2, b, y0, x0);
             if (tma_store) {
                 // one TMA store of the 128 x 1 x 64 box at (x0/2, y0/2, 64b);
                 // the hardware drops the columns past the image edge

@@ -16,6 +16,16 @@ __device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)
 // second or once another thread has raised *abort
 __device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity, const volatile int *abort)
 {
+    {
+        // the common case, a phase that has already completed, costs one
+        // test (no clock read, no abort load)
+        uint32_t done;
+        asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+                     : "=r"(done)
+                     : "r"(bar), "r"(parity)
+                     : "memory");
+        if (done) return true;
+    }
     const long long t0 = clock64();
     while (true) {
         uint32_t done;
