@@ -36,10 +36,13 @@ def run(rows, feats, classes, seed, inputs=None, scores_only=False):
 # feats a multiple of 64 up to 1024 runs on the tensor cores, the others on
 # CUDA cores
 # 19457 and 40001 rows split over 152 CTAs leave each a partial last tile
-# (127 or 128 rows; 7 past two full tiles), copied in 8-row boxes
+# (127 or 128 rows; 7 past two full tiles), copied in 8-row boxes.  Up to 10
+# classes the table takes the 32-column layout (pieces 10 columns apart), from
+# 11 to 16 the 48-column one (16 apart)
 @pytest.mark.parametrize("rows,feats,classes", [(1, 32, 10), (7, 64, 3), (100, 1024, 10), (1001, 256, 12),
                                                 (333, 96, 1), (64, 32, 16), (129, 1024, 16), (300, 640, 1),
-                                                (19457, 1024, 10), (40001, 512, 10)])
+                                                (19457, 1024, 10), (40001, 512, 10), (2049, 1024, 11),
+                                                (5000, 1024, 9), (700, 192, 15)])
 def test_scores_bit_exact_with_dyadic_tables(rows, feats, classes):
     ctx, d, (X, T1, b1, T2, b2) = run(rows, feats, classes, seed=rows, scores_only=True)
     s1 = d.S1[:rows].cpu().numpy()
@@ -49,8 +52,9 @@ def test_scores_bit_exact_with_dyadic_tables(rows, feats, classes):
     ctx.close()
 
 
-def test_scores_general_tables_within_tolerance():
-    rows, feats, classes = 513, 1024, 10
+@pytest.mark.parametrize("classes", [10, 11])
+def test_scores_general_tables_within_tolerance(classes):
+    rows, feats = 513, 1024
     X, *_ = datagen.ml_inputs(rows, feats=feats, classes=classes, seed=7)
     g = np.random.default_rng(0)
     T = g.normal(0, 1, (feats, classes)).astype(np.float32)
@@ -63,12 +67,13 @@ def test_scores_general_tables_within_tolerance():
     ctx.close()
 
 
-def test_scores_out_of_bf16_range_rows_fall_back_exactly():
+@pytest.mark.parametrize("classes", [10, 13])
+def test_scores_out_of_bf16_range_rows_fall_back_exactly(classes):
     """Feature values beyond +-256 (not exact in bf16) send their tile (at
     most 128 rows) to the CUDA-core path: those rows meet the tolerance, and
     every row further than a tile from such a row stays bit-exact (dyadic
     tables)."""
-    rows, feats, classes = 1000, 1024, 10
+    rows, feats = 1000, 1024
     X, T1, b1, T2, b2 = datagen.ml_inputs(rows, feats=feats, classes=classes, seed=11)
     X = X.copy()
     X[5, 17] = 1000
